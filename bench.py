@@ -1,0 +1,323 @@
+"""Benchmark of the hierarchical sorted splatting path on GB300.
+
+Workload: 3,000,000 Gaussians (64 anisotropic clusters, SH degree 3), 16 views on a 360 degree
+orbit at 1920x1080, fov 50 (synthetic, seeded; stands in for the paper's trained scenes).
+One step = one batched forward over the 16 views (Preprocess -> Duplicate -> sort -> hierarchical
+Render, one launch sequence for all views) followed by the backward pass of those views
+(backward Render replay + backward Preprocess) for a fixed synthetic dL/drgb.
+
+  value         forward Mpix/s = 16 x 1920 x 1080 / forward time of a step (CUDA events)
+  ms_per_step   forward + backward of the 16 views
+  per_view      the same forward as 16 separate single-view launch sequences
+  e2e           forward through the public API with the scene copied in from pinned host
+                memory and rgb + depth copied back inside the timed region
+  roofline      the dominant kernel (forward Render), ALU bound: algorithmic FP32 work from
+                its counted work units / its event-timed duration
+  cpu_baseline  the FP64 CPU oracle on a bounded sample of the same workload
+
+--impl reference runs that oracle as the reference arm. Multi-GPU (torchrun): views are
+independent, so every rank renders its own 16 views of the scene (weak scaling); only the
+timing uses a collective (barrier + max).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2402_00525_gb300 import inputs as I  # noqa: E402
+
+WORKLOAD = "3M Gaussians (64 clusters, SH3), 16 orbit views 1920x1080, fov 50"
+METRIC = "Mpix/s fwd and fwd+bwd ms/view, 3M Gaussians @1080p; batched vs per-view"
+FP32_LANES_PER_SM = 128
+# algorithmic FP32 operations per work unit of the forward Render (cull by Algorithm 1 + G2 +
+# t_opt at a 4x4 or 2x2 box; alpha + t_opt at a pixel)
+FLOP_PER_SUBTILE_EVAL, FLOP_PER_QUAD_EVAL, FLOP_PER_PIXEL_EVAL = 80, 80, 45
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [ln.strip().split(", ") for ln in self.f.read().splitlines() if ln.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1].split()[0]))
+                smax.append(float(r[2].split()[0]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (IndexError, ValueError):
+                continue
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(scene, cam, prm, ntiles, seed):
+    """Time the FP64 oracle (as it stands) on `ntiles` random tiles of one view."""
+    from oracle import oracle as O
+    tiles = np.random.default_rng(seed).choice(cam.num_tiles, ntiles, replace=False)
+    t0 = time.perf_counter()
+    with O.OracleRun(scene, cam, prm, tiles=tiles) as r:
+        r.render()
+    dt = time.perf_counter() - t0
+    return ntiles * 256, dt
+
+
+def oracle_threads() -> int:
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from oracle import build as OB
+    OB.build()
+    scene, cams, prm = I.full_hd_workload()
+    ntiles = 24
+    for w in range(args.warmup):
+        oracle_sample(scene, cams[w % len(cams)], prm, ntiles, 100 + w)
+    px, secs = 0, 0.0
+    for k in range(args.steps):
+        p, dt = oracle_sample(scene, cams[k % len(cams)], prm, ntiles, 200 + k)
+        px += p
+        secs += dt
+    val = px / secs / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "Mpix/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "%d random tiles of one view per step" % ntiles},
+            "cpu_baseline": {"value": val, "unit": "Mpix/s", "cores": oracle_threads(), "kind": "oracle",
+                             "sample": "%d random 16x16 tiles of view (step mod 16) per step, full preprocess of the 3M Gaussians" % ntiles},
+            "e2e": {"value": val, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="stp", choices=["stp", "reference"])
+    ap.add_argument("--n", type=int, default=3_000_000, help="Gaussians (default: the workload's 3M)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--per-view-rounds", type=int, default=2)
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+        run_reference(args, rank, world)
+        return
+    args.warmup = max(3, args.warmup)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2402_00525_gb300 import build as B
+    B.build()
+    from paper_2402_00525_gb300 import _native as N
+    from paper_2402_00525_gb300 import renderer as R
+
+    scene, _, prm = I.full_hd_workload(n=args.n, nviews=1)
+    all_cams = I.orbit_cameras(16 * world, 15.0, 2.0, I.C2_SIZES, 50.0)
+    cams = all_cams[rank::world]
+    V = len(cams)
+    P = sum(c.num_pixels for c in cams)
+    g = R.scene_to_device(scene)
+    rnd = R.Renderer(scene.n, cams, prm, backward=True)
+    out = (torch.empty((P, 3), device="cuda"), torch.empty((P,), device="cuda"), torch.empty((P,), device="cuda"))
+    rnd.forward(g, out=out)                                   # sizes the sort-entry capacity
+    gen = torch.Generator(device="cuda").manual_seed(1234)
+    d_rgb = (torch.randint(0, 2, (P, 3), device="cuda", generator=gen).float() * 2 - 1) / (3 * P)
+    grads = {k: torch.zeros_like(g[k]) for k in R.FIELDS}
+
+    def step():
+        rnd.forward(g, out=out, check=False)
+        rnd.backward(g, d_rgb, None, grads)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st = rnd.status()
+    assert st.error_bits == 0, "status %d after warm-up" % st.error_bits
+    entries = int(st.num_entries)
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    N.profile_enable(2 * K)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(K):
+        ev[k][0].record()
+        rnd.forward(g, out=out, check=False)
+        ev[k][1].record()
+        rnd.backward(g, d_rgb, None, grads)
+        ev[k][2].record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    stages = N.profile_read(2 * K)
+    N.profile_enable(0)
+    fwd_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
+    step_ms = float(np.mean([e[0].elapsed_time(e[2]) for e in ev]))
+    st = rnd.status()
+    assert st.error_bits == 0, "status %d after the timed region" % st.error_bits
+    fwd_stage = stages[0::2].mean(0)
+    bwd_stage = stages[1::2].mean(0)
+    if dist:
+        t = torch.tensor([fwd_ms, step_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        fwd_ms, step_ms = float(t[0]), float(t[1])
+    total_px = P * world
+    value = total_px / (fwd_ms * 1e-3) / 1e6
+
+    # ---------------------------------------------------------------- per-view launches
+    single = [R.Renderer(scene.n, [c], prm) for c in cams]
+    souts = [(torch.empty((c.num_pixels, 3), device="cuda"), torch.empty((c.num_pixels,), device="cuda"),
+              torch.empty((c.num_pixels,), device="cuda")) for c in cams]
+    for r_, o_ in zip(single, souts):
+        r_.forward(g, out=o_)
+    torch.cuda.synchronize()
+    pv_ms = []
+    for _ in range(args.per_view_rounds + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for r_, o_ in zip(single, souts):
+            r_.forward(g, out=o_, check=False)
+        e1.record()
+        torch.cuda.synchronize()
+        pv_ms.append(e0.elapsed_time(e1))
+    pv_ms = float(np.mean(pv_ms[1:]))
+    same = all(torch.equal(out[0][int(rnd.pixel_offsets[k]):int(rnd.pixel_offsets[k + 1])], souts[k][0])
+               for k in range(V))
+    del single, souts
+    torch.cuda.empty_cache()
+
+    # ---------------------------------------------------------------- end to end (host buffers)
+    host = {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k), np.float32)).pin_memory() for k in R.FIELDS}
+    h_rgb = torch.empty((P, 3), pin_memory=True)
+    h_depth = torch.empty((P,), pin_memory=True)
+    h2d = sum(t.numel() * 4 for t in host.values())
+    d2h = (h_rgb.numel() + h_depth.numel()) * 4
+    e2e_ms = []
+    for it in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in R.FIELDS:
+            g[k].copy_(host[k], non_blocking=True)
+        rnd.forward(g, out=out, check=False)
+        h_rgb.copy_(out[0], non_blocking=True)
+        h_depth.copy_(out[1], non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        if it:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_ms = float(np.mean(e2e_ms))
+    e2e_val = total_px / (e2e_ms * 1e-3) / 1e6
+
+    # ---------------------------------------------------------------- work counters (untimed)
+    dbg = R.Renderer(scene.n, cams, prm, debug=True, capacity=rnd.capacity)
+    dbg.forward(g)
+    cst = dbg.status()
+    cnt = [int(x) for x in cst.counters]
+    del dbg
+    torch.cuda.empty_cache()
+    flops = FLOP_PER_SUBTILE_EVAL * cnt[0] + FLOP_PER_QUAD_EVAL * cnt[2] + FLOP_PER_PIXEL_EVAL * cnt[4]
+    render_ms = float(fwd_stage[6])
+    props = torch.cuda.get_device_properties(0)
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = flops / (render_ms * 1e-3) / 1e12
+    passes = (int(rnd.layout.key_bits) + 7) // 8
+    launches_fwd = 1 + 1 + 1 + 3 + 1 + 3 * passes + 1 + 1
+    launches_bwd = 2
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_gaussians": scene.n, "views_per_gpu": V, "resolution": "1920x1080",
+                   "queues": "%d/%d/%d" % (prm.tail, prm.mid, prm.head), "l2": "inputs larger than L2 (708 MB scene, 3.8 GB records)",
+                   "parallelism": "views sharded over ranks" if world > 1 else "single GPU"},
+        "fwd_ms_per_step": fwd_ms, "fwd_bwd_ms_per_view": step_ms / V,
+        "stage_ms": {"forward": {n: round(float(x), 4) for n, x in zip(N.STAGE_NAMES, fwd_stage)},
+                     "backward": {n: round(float(x), 4) for n, x in zip(N.STAGE_NAMES, bwd_stage)}},
+        "per_view": {"fwd_mpix_s": total_px / world / (pv_ms * 1e-3) / 1e6, "fwd_ms_16_views": pv_ms,
+                     "batched_speedup": pv_ms / fwd_ms, "identical_to_batched": bool(same)},
+        "entries_per_step": entries,
+        "e2e": {"value": e2e_val, "unit": "Mpix/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": e2e_ms},
+        "gpu_launches": K * (launches_fwd + launches_bwd),
+        "clocks": clk,
+        "roofline": {"bound": "alu", "kernel": "k_render (forward)", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "work_units": {"subtile_evals": cnt[0], "subtile_survivors": cnt[1], "quad_evals": cnt[2],
+                                    "blends": cnt[3], "pixel_evals": cnt[4]},
+                     "peak_basis": "FP32 FMA issue: %d SMs x 128 lanes x 2 x %.0f MHz" % (props.multi_processor_count, sm_max)},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import build as OB
+        OB.build()
+        ntiles = 96
+        px, secs = oracle_sample(scene, cams[0], prm, ntiles, 7)
+        line["cpu_baseline"] = {"value": px / secs / 1e6, "unit": "Mpix/s", "cores": oracle_threads(),
+                                "kind": "oracle",
+                                "sample": "%d random 16x16 tiles of view 0 (%d px), FP64, incl. the preprocess of all 3M Gaussians, %.1f s" % (ntiles, px, secs)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,217 @@
+/* stp.h -- C ABI of the GB300 (sm_103a) StopThePop renderer (libstp.so).
+ *
+ * Hierarchical sorted Gaussian splatting: Radl, Steiner et al., "StopThePop: Sorted Gaussian
+ * Splatting for View-Consistent Real-time Rendering", TOG 43(4) 2024, arXiv 2402.00525.
+ * The forward pass is the paper's four stages (Sec. 4, Fig. "pipeline"): Preprocess,
+ * Duplicate (with exact tile culling and the per-tile t_opt key), a global sort of
+ * (tile, depth) keys, and the hierarchical Render with tail / mid / head queues. The backward
+ * pass replays the same blend order front to back (Sec. 4.5).
+ *
+ * Conventions shared by every entry point:
+ *   - Every array pointer is a DEVICE pointer owned by the caller unless the comment says
+ *     "host". The library never allocates device memory: scratch lives in a caller-owned
+ *     workspace sized by stp_workspace_size().
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream). Launches are
+ *     asynchronous on it; nothing in stp_render / stp_render_backward synchronises the host.
+ *   - Gaussians are float32 structure-of-arrays: means [N,3], log_scales [N,3], quats [N,4]
+ *     in (w, x, y, z) order (normalised inside), opacity_logits [N] (opacity = sigmoid),
+ *     sh [N, (deg+1)^2, 3] (deg <= 3).
+ *   - Cameras map world to camera space as p = R x + t (R row major), OpenCV axes (x right,
+ *     y down, z forward), pinhole intrinsics in pixels; pixel (u, v) has its centre at
+ *     (u + 0.5, v + 0.5). Tiles are 16 x 16 pixels, row major.
+ *   - Images of several views are packed view after view: view v starts at pixel offset
+ *     sum_{u<v} W_u H_u; rgb is [pixels, 3] (HWC), depth and T are [pixels].
+ *   - Return values are stp_status. Argument errors are detected on the host before any
+ *     launch (STP_ERR_ARG, nothing launched). Conditions that only the device can see
+ *     (sort-entry capacity exceeded, a bounded wait that gave up) are recorded in the
+ *     workspace's status block and read back with stp_read_status() after the stream work.
+ *   - stp_last_error() returns a host-side, thread-local message for the last failure.
+ */
+#ifndef STP_H
+#define STP_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    STP_OK = 0,
+    STP_ERR_ARG = 1,            /* invalid argument; nothing was launched                   */
+    STP_ERR_CAPACITY = 2,       /* more (Gaussian, tile) entries than the workspace holds    */
+    STP_ERR_TIMEOUT = 3,        /* a bounded device wait gave up                             */
+    STP_ERR_CUDA = 4,           /* a CUDA runtime call failed (message in stp_last_error)    */
+    STP_ERR_NOT_SUPPORTED = 5   /* parameter combination not compiled in                      */
+} stp_status;
+
+enum { STP_MODE_HIER = 0, STP_MODE_FULL = 1, STP_MODE_GLOBAL = 2, STP_MODE_WINDOW = 3 };
+
+/* flag bits of stp_params.flags */
+enum {
+    STP_FLAG_HEAD_EVICT_FIRST = 1,   /* head queue blends before inserting (alternative reading) */
+    STP_FLAG_LEVEL_CENTRE_RAYS = 2,  /* 4x4 / 2x2 depth from the level-centre ray             */
+    STP_FLAG_TILE_CENTRE_KEY = 4,    /* tile key from the tile-centre ray                    */
+    STP_FLAG_VIEW_DEPTH_KEY = 8,     /* tile key = view-space depth of the mean (3DGS)       */
+    STP_FLAG_NO_LOAD_BALANCE = 16,   /* every Gaussian processed by its own thread           */
+    STP_FLAG_DEBUG_STATS = 32,       /* workspace also receives per-pixel blend count and hash */
+    STP_FLAG_BACKWARD = 64           /* workspace also holds the backward pass's scratch; the
+                                        forward and backward calls must both set it          */
+};
+
+typedef struct {
+    const float* means;          /* [N,3] */
+    const float* log_scales;     /* [N,3] */
+    const float* quats;          /* [N,4] (w, x, y, z) */
+    const float* opacity_logits; /* [N]   */
+    const float* sh;             /* [N, (sh_degree+1)^2, 3] */
+    int64_t n;                   /* number of Gaussians, 0 <= n < 2^31                        */
+    int32_t sh_degree;           /* 0..3 */
+    int32_t reserved;
+} stp_gaussians;
+
+typedef struct {                 /* gradient outputs in the input layout, ACCUMULATED (+=)   */
+    float* means;
+    float* log_scales;
+    float* quats;
+    float* opacity_logits;
+    float* sh;
+} stp_gaussians_grad;
+
+typedef struct {
+    float R[9];                  /* world -> camera rotation, row major (host value)          */
+    float t[3];
+    float fx, fy, cx, cy;        /* pixels */
+    int32_t width, height;       /* 1 .. 16384 */
+} stp_camera;
+
+typedef struct {
+    int32_t tail;                /* tail (4x4) queue size: 32n + 32, n >= 1 (Sec. 4.4)       */
+    int32_t mid;                 /* mid (2x2) queue size: 4m + 4, m >= 1                    */
+    int32_t head;                /* head (per-pixel) queue size, 1..16                      */
+    int32_t lb_threshold;        /* load-balancing threshold in tiles (Sec. 4.4), >= 1      */
+    float eps_o;                 /* contribution threshold, 1/255                           */
+    float t_min;                 /* transmittance early-out, 1e-4                           */
+    float alpha_max;             /* 0.99 */
+    float inv_scale_max;         /* bound on entries of S^-1, 1e3 (Sec. 4.2)               */
+    float dilation;              /* EWA low-pass added to Sigma2, 0.3                       */
+    float frustum_clamp;         /* Jacobian clamp factor, 1.3                              */
+    float znear;                 /* near plane, 0.2                                         */
+    float bg[3];                 /* background colour                                       */
+    int32_t mode;                /* STP_MODE_*                                              */
+    int32_t window_k;            /* k of STP_MODE_WINDOW                                    */
+    int32_t flags;               /* STP_FLAG_* */
+    int32_t reserved;
+    int64_t max_entries;         /* capacity of (Gaussian, tile) sort entries for one call  */
+} stp_params;
+
+typedef struct {                 /* device status block, read back by stp_read_status        */
+    uint32_t error_bits;         /* 1 capacity exceeded, 2 count mismatch padded, 4 timeout   */
+    uint32_t mismatched;         /* Gaussians whose Duplicate count differed from Preprocess  */
+    uint64_t num_entries;        /* entries the last forward needed (may exceed capacity)    */
+    uint64_t capacity;           /* entries the workspace holds                              */
+    uint64_t counters[5];        /* with STP_FLAG_DEBUG_STATS, work units of the last forward
+                                    Render: [0] (entry, 4x4 subtile) evaluations, [1] 4x4
+                                    survivors, [2] (entry, 2x2 quad) evaluations, [3] blends,
+                                    [4] (entry, pixel) evaluations                         */
+} stp_run_status;
+
+typedef struct {                 /* byte offsets of workspace regions (for inspection)       */
+    size_t status;               /* stp_run_status                                           */
+    size_t views;                /* internal view table                                      */
+    size_t geom;                 /* [V*N] 64-byte render records (layout in stp_common.cuh)  */
+    size_t color;                /* [V*N] float4 colours                                     */
+    size_t rect;                 /* [V*N] ushort4 tile rectangles [x0, y0, x1, y1)           */
+    size_t counts;               /* [V*N] uint32 entries per (view, Gaussian)                */
+    size_t offsets;              /* [V*N] uint32 exclusive prefix sum of counts              */
+    size_t scan_partials;        /* scan scratch                                             */
+    size_t keys, vals;           /* [capacity] uint64 / uint32 radix-sort buffer B           */
+    size_t keys_alt, vals_alt;   /* [capacity] radix-sort buffer A (Duplicate output)        */
+    size_t sorted_keys;          /* = keys or keys_alt: where the sorted (tile, depth) keys  */
+    size_t sorted_vals;          /*   and Gaussian ids end up                                */
+    size_t ranges;               /* [total tiles] uint2 [start, end) into the sorted pairs   */
+    size_t tfinal;               /* [total pixels] float final transmittance                 */
+    size_t pix_state;            /* [total pixels] float4 (colour without background, depth) */
+    size_t scratch;              /* sort histogram scratch                                   */
+    size_t dbg_nblend;           /* [total pixels] uint32 blends per pixel (flag 32), else 0 */
+    size_t dbg_hash;             /* [total pixels] uint64 blend-order hash (flag 32), else 0 */
+    size_t grad_geom;            /* [V*N*20] float backward scratch (flag 64), else 0        */
+    size_t total;                /* total bytes                                              */
+    int64_t capacity;            /* sort-entry capacity                                      */
+    int64_t total_tiles, total_pixels;
+    int32_t key_bits;            /* bits of the radix-sort key: 32 + bits(total tiles)       */
+    int32_t reserved;
+} stp_workspace_layout;
+
+/* Size of the workspace one stp_render call needs for `nviews` cameras of N Gaussians
+ * (Sec. 4: per-view records, sort entries, tile ranges, per-pixel T). Host-only, no CUDA
+ * call. Returns 0 on invalid arguments (see stp_last_error).                              */
+size_t stp_workspace_size(int64_t n, const stp_camera* cams /* host, [nviews] */, int32_t nviews,
+                          const stp_params* prm /* host */);
+
+/* Same sizing, with the byte offset of every region (host).                               */
+stp_status stp_workspace_layout_get(int64_t n, const stp_camera* cams /* host */, int32_t nviews,
+                                    const stp_params* prm /* host */, stp_workspace_layout* out /* host */);
+
+/* Forward pass (Sec. 4): Preprocess -> Duplicate -> global radix sort -> hierarchical
+ * Render, for `nviews` views of one scene in one batched launch sequence. Writes rgb
+ * [pixels,3], depth [pixels] (volumetric depth with phi = t_opt, Sec. 6) and, if not NULL,
+ * tfinal [pixels]. The workspace keeps the state the backward pass needs (sorted lists,
+ * records, final T). Asynchronous; call stp_read_status() to learn whether the capacity
+ * sufficed (if not, rgb / depth are undefined and num_entries tells the size needed).   */
+stp_status stp_render(const stp_gaussians* g /* host struct of device pointers */,
+                      const stp_camera* cams /* host, [nviews] */, int32_t nviews,
+                      const stp_params* prm /* host */, void* workspace, size_t ws_bytes,
+                      float* rgb, float* depth, float* tfinal, void* stream);
+
+/* Backward pass (Sec. 4.5): replays the forward's blend order front to back using the
+ * workspace of the preceding stp_render with the same arguments (which must not have been
+ * modified), and ACCUMULATES (+=) the gradients of <d_rgb, rgb> + <d_depth, depth> into
+ * `grad` (device arrays in the input layout; zero them first for a fresh gradient).
+ * d_depth may be NULL. Asynchronous.                                                       */
+stp_status stp_render_backward(const stp_gaussians* g, const stp_camera* cams, int32_t nviews,
+                               const stp_params* prm, void* workspace, size_t ws_bytes,
+                               const float* d_rgb, const float* d_depth,
+                               const stp_gaussians_grad* grad /* host struct of device ptrs */,
+                               void* stream);
+
+/* Synchronises `stream`, copies the workspace's status block to *out (host) and returns
+ * STP_ERR_CAPACITY / STP_ERR_TIMEOUT if the device recorded that condition, else STP_OK.  */
+stp_status stp_read_status(const void* workspace, stp_run_status* out /* host */, void* stream);
+
+/* Stable LSD radix sort of (uint64 key, uint32 value) pairs on the low `key_bits` bits
+ * (1..64), the sort of Sec. 3.1 / 4 that orders (tile, depth) keys. keys_in / vals_in are
+ * read, keys_out / vals_out receive the sorted pairs; `n` may also be read from the device
+ * (n_dev != NULL: the count is min(*n_dev, n)). temp is device scratch of
+ * stp_sort_temp_bytes(n) bytes. The four arrays must not overlap. Asynchronous.            */
+size_t     stp_sort_temp_bytes(int64_t n);
+stp_status stp_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
+                          uint32_t* vals_out, int64_t n, const uint64_t* n_dev, int32_t key_bits,
+                          void* temp, size_t temp_bytes, void* stream);
+
+/* Stage timing with CUDA events (Sec. 5.3 reports per-stage times). After
+ * stp_profile_enable(max_calls), each stp_render / stp_render_backward call on this host
+ * thread records STP_NUM_STAGE_EVENTS events on its stream into the next of max_calls slots
+ * (further calls are not recorded); max_calls = 0 disables and frees the events.
+ * stp_profile_read synchronises the recorded events and writes, per recorded call, the
+ * milliseconds of each stage (ms[call * STP_NUM_STAGES + stage]); *ncalls receives the number
+ * of calls recorded; recording then restarts at slot 0. Stages of a forward call: 0 status and
+ * view table, 1 Preprocess, 2 scan, 3 Duplicate, 4 sort, 5 tile ranges, 6 Render; of a
+ * backward call: 5 clearing the gradient scratch, 6 backward Render, 7 backward Preprocess
+ * (the others are 0).                                                                     */
+#define STP_NUM_STAGES 8
+#define STP_NUM_STAGE_EVENTS (STP_NUM_STAGES + 1)
+stp_status stp_profile_enable(int32_t max_calls);
+stp_status stp_profile_read(float* ms /* host, [max_calls * STP_NUM_STAGES] */, int32_t max_calls,
+                            int32_t* ncalls /* host */);
+
+/* Thread-local message of the last error on this host thread (empty if none).            */
+const char* stp_last_error(void);
+
+/* Library version, e.g. 0x000100 for 0.1.0.                                              */
+int32_t stp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STP_H */

@@ -1,0 +1,87 @@
+// stp_kernels.cuh -- launch interfaces between the C-ABI host code (stp_api.cu) and the
+// kernels of libstp. Internal to the library.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "stp_common.cuh"
+
+namespace stp {
+
+struct PipeArgs {
+    // inputs (device, caller owned)
+    const float* means;
+    const float* log_scales;
+    const float* quats;
+    const float* logits;
+    const float* sh;
+    int n, sh_k, nviews, lb_threshold, flags, mode, window_k, tail, mid, head;
+    float eps_o, t_min, alpha_max, inv_scale_max, dilation, znear;
+    float bg[3];
+    int total_tiles;
+    long long total_pixels;
+    // workspace regions
+    const ViewDesc* views;
+    Status* status;
+    float4* geom;            // [V*N*4]
+    float4* color;           // [V*N]
+    ushort4* rect;           // [V*N]
+    uint32_t* counts;        // [V*N]
+    uint32_t* offsets;       // [V*N]
+    unsigned long long* scan_partials;
+    uint64_t* keys;          // sort buffer B
+    uint32_t* vals;
+    uint64_t* keys_alt;      // sort buffer A (Duplicate writes here)
+    uint32_t* vals_alt;
+    uint64_t* dup_keys;      // = keys_alt
+    uint32_t* dup_vals;
+    const uint64_t* skeys;   // sorted pairs (A or B, see pipeline_sorted_in_alt)
+    const uint32_t* svals;
+    unsigned long long capacity;
+    uint2* ranges;           // [total_tiles]
+    float* tfinal_ws;        // [total_pixels]
+    float* pix_state;        // [total_pixels] float4 (C without background, depth)
+    uint32_t* dbg_nblend;    // [total_pixels] or null
+    unsigned long long* dbg_hash;   // [total_pixels] or null
+    void* sort_temp;
+    size_t sort_temp_bytes;
+    int key_bits;
+    // outputs
+    float* rgb;
+    float* depth;
+    float* tfinal_out;
+    // backward
+    const float* d_rgb;
+    const float* d_depth;
+    float* grad_geom;        // [V*N*kGradStride] per-(view, Gaussian) 2D gradients
+    float* g_means;
+    float* g_log_scales;
+    float* g_quats;
+    float* g_logits;
+    float* g_sh;
+};
+
+constexpr int kGradStride = 20;   // dmean2(2) dconic(3) dopacity(1) dcolor(3) dS(6) dv(3) pad(2)
+
+cudaError_t launch_views_init(const ViewDesc* host_views, int nviews, ViewDesc* dev_views,
+                              cudaStream_t s);
+cudaError_t launch_preprocess(const PipeArgs& a, cudaStream_t s);
+cudaError_t launch_scan_counts(const PipeArgs& a, cudaStream_t s);
+cudaError_t launch_duplicate(const PipeArgs& a, cudaStream_t s);
+cudaError_t launch_ranges(const PipeArgs& a, cudaStream_t s);
+cudaError_t launch_render(const PipeArgs& a, bool backward, cudaStream_t s);
+cudaError_t launch_backward_preprocess(const PipeArgs& a, cudaStream_t s);
+
+size_t scan_partials_count(long long m);
+size_t sort_hist_bytes();
+bool pipeline_sorted_in_alt(int key_bits);
+cudaError_t pipeline_sort(const PipeArgs& a, cudaStream_t s);
+size_t render_smem_bytes(int tail, int mid);
+bool render_head_supported(int head);
+size_t sort_temp_bytes(long long n);
+cudaError_t sort_pairs(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout,
+                       long long n, const unsigned long long* n_dev, int key_bits, void* temp,
+                       size_t temp_bytes, cudaStream_t s);
+
+}  // namespace stp

@@ -1,0 +1,450 @@
+// stp_preprocess.cu -- Preprocess, the scan of tile counts, and Duplicate.
+//
+// StopThePop (arXiv 2402.00525) Sec. 4.4 and appendix B: per Gaussian and view, the EWA 2D
+// splat, SH colour, Sigma^-1 with the S^-1 clamp packed with Sigma^-1 (mu - o) for the depth
+// evaluation, the opacity-aware bounding rectangle t_O sqrt(lambda_max), and the number of
+// tiles that survive exact culling (Algorithm 1). Duplicate re-takes the same cull decisions
+// and writes one (tile, t_opt) key per surviving tile. Both stages use the paper's two-phase
+// load balancing: a Gaussian with at most `lb_threshold` candidate tiles is handled by its own
+// thread; larger ones are handled by the whole warp (ballot / shuffle / popc offsets).
+//
+// One thread per Gaussian loops over all views of the launch, so the Gaussian's parameters
+// (236 bytes at SH degree 3) are read from HBM once for every view of the batch.
+#include <cuda_runtime.h>
+
+#include "stp_common.cuh"
+#include "stp_kernels.cuh"
+
+namespace stp {
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// Real spherical harmonics to degree 3, Condon-Shortley phase, as polynomials of the unit
+// view direction; constants sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) (times sqrt 2 for m != 0).
+__device__ __forceinline__ void sh_colour(const float* __restrict__ c, int K, float x, float y,
+                                          float z, float out[3])
+{
+    const float k0 = 0.28209479177387814f, k1 = 0.4886025119029199f;
+    const float k2a = 1.0925484305920792f, k2b = 0.31539156525252005f, k2c = 0.5462742152960396f;
+    const float k3a = 0.5900435899266435f, k3b = 2.890611442640554f, k3c = 0.4570457994644658f;
+    const float k3d = 0.3731763325901154f, k3e = 1.445305721320277f;
+    float Y[16];
+    Y[0] = k0;
+    if (K > 1) {
+        Y[1] = -k1 * y; Y[2] = k1 * z; Y[3] = -k1 * x;
+    }
+    if (K > 4) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = k2a * x * y; Y[5] = -k2a * y * z; Y[6] = k2b * (2.f * zz - xx - yy);
+        Y[7] = -k2a * x * z; Y[8] = k2c * (xx - yy);
+        if (K > 9) {
+            Y[9] = -k3a * y * (3.f * xx - yy);
+            Y[10] = k3b * x * y * z;
+            Y[11] = -k3c * y * (4.f * zz - xx - yy);
+            Y[12] = k3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+            Y[13] = -k3c * x * (4.f * zz - xx - yy);
+            Y[14] = k3e * z * (xx - yy);
+            Y[15] = -k3a * x * (xx - 3.f * yy);
+        }
+    }
+    float s0 = 0.5f, s1 = 0.5f, s2 = 0.5f;
+    for (int j = 0; j < K; j++) {
+        s0 += Y[j] * __ldg(c + 3 * j);
+        s1 += Y[j] * __ldg(c + 3 * j + 1);
+        s2 += Y[j] * __ldg(c + 3 * j + 2);
+    }
+    out[0] = fmaxf(s0, 0.f);
+    out[1] = fmaxf(s1, 0.f);
+    out[2] = fmaxf(s2, 0.f);
+}
+
+struct GaussIn {             // view-independent quantities of one Gaussian
+    float mu[3];
+    float sig[6];            // Sigma   (xx, xy, xz, yy, yz, zz)
+    float sinv[6];           // Sigma^-1 with the S^-1 clamp
+    float opacity;
+};
+
+__device__ __forceinline__ void load_gauss(const PipeArgs& a, int i, GaussIn& g)
+{
+    g.mu[0] = __ldg(a.means + 3 * i);
+    g.mu[1] = __ldg(a.means + 3 * i + 1);
+    g.mu[2] = __ldg(a.means + 3 * i + 2);
+    float qw = __ldg(a.quats + 4 * i), qx = __ldg(a.quats + 4 * i + 1);
+    float qy = __ldg(a.quats + 4 * i + 2), qz = __ldg(a.quats + 4 * i + 3);
+    const float ql = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+    qw *= ql; qx *= ql; qy *= ql; qz *= ql;
+    const float R[9] = {1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy),
+                        2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx),
+                        2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)};
+    float s2[3], w[3];
+    for (int k = 0; k < 3; k++) {
+        const float ls = __ldg(a.log_scales + 3 * i + k);
+        s2[k] = expf(2.f * ls);
+        const float si = fminf(expf(-ls), a.inv_scale_max);
+        w[k] = si * si;
+    }
+    const int id[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+    for (int e = 0; e < 6; e++) {
+        const int r = id[e][0], c = id[e][1];
+        g.sig[e] = R[3 * r] * s2[0] * R[3 * c] + R[3 * r + 1] * s2[1] * R[3 * c + 1] + R[3 * r + 2] * s2[2] * R[3 * c + 2];
+        g.sinv[e] = R[3 * r] * w[0] * R[3 * c] + R[3 * r + 1] * w[1] * R[3 * c + 1] + R[3 * r + 2] * w[2] * R[3 * c + 2];
+    }
+    g.opacity = 1.f / (1.f + expf(-__ldg(a.logits + i)));
+}
+
+__device__ __forceinline__ float sym(const float* s, int r, int c)
+{
+    const int idx[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+    return s[idx[r][c]];
+}
+
+// Per-(view, Gaussian) record (layout in stp_common.cuh). Returns false if invisible.
+__device__ bool make_record(const PipeArgs& a, const ViewDesc& V, const GaussIn& g, int i,
+                            Rec& rec, float4& col, ushort4& rect)
+{
+    rect = make_ushort4(0, 0, 0, 0);
+    rec.r0 = rec.r1 = rec.r2 = rec.r3 = make_float4(0.f, 0.f, 0.f, 0.f);
+    col = make_float4(0.f, 0.f, 0.f, 0.f);
+    float p[3];
+    for (int k = 0; k < 3; k++)
+        p[k] = V.R[3 * k] * g.mu[0] + V.R[3 * k + 1] * g.mu[1] + V.R[3 * k + 2] * g.mu[2] + V.t[k];
+    if (!(p[2] > a.znear)) return false;
+    if (!(g.opacity >= a.eps_o)) return false;
+    const float iz = 1.f / p[2];
+    const float ux = p[0] * iz, uy = p[1] * iz;
+    const float cx = fminf(V.limx, fmaxf(-V.limx, ux)), cy = fminf(V.limy, fmaxf(-V.limy, uy));
+    const float J00 = V.fx * iz, J02 = -V.fx * cx * iz, J11 = V.fy * iz, J12 = -V.fy * cy * iz;
+    float T[2][3];
+    for (int c = 0; c < 3; c++) {
+        T[0][c] = J00 * V.R[c] + J02 * V.R[6 + c];
+        T[1][c] = J11 * V.R[3 + c] + J12 * V.R[6 + c];
+    }
+    float M[2][3];
+    for (int r = 0; r < 2; r++)
+        for (int c = 0; c < 3; c++)
+            M[r][c] = T[r][0] * sym(g.sig, 0, c) + T[r][1] * sym(g.sig, 1, c) + T[r][2] * sym(g.sig, 2, c);
+    const float ca = M[0][0] * T[0][0] + M[0][1] * T[0][1] + M[0][2] * T[0][2] + a.dilation;
+    const float cb = M[0][0] * T[1][0] + M[0][1] * T[1][1] + M[0][2] * T[1][2];
+    const float cc = M[1][0] * T[1][0] + M[1][1] * T[1][1] + M[1][2] * T[1][2] + a.dilation;
+    const float det = ca * cc - cb * cb;
+    if (!(det > 0.f)) return false;
+    const float idet = 1.f / det;
+    const float mx = V.fx * ux + V.cx, my = V.fy * uy + V.cy;
+    // camera-space Sigma^-1 and v = S p
+    float RS[3][3];
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++)
+            RS[r][c] = V.R[3 * r] * sym(g.sinv, 0, c) + V.R[3 * r + 1] * sym(g.sinv, 1, c) + V.R[3 * r + 2] * sym(g.sinv, 2, c);
+    float S[3][3];
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++)
+            S[r][c] = RS[r][0] * V.R[3 * c] + RS[r][1] * V.R[3 * c + 1] + RS[r][2] * V.R[3 * c + 2];
+    float v[3];
+    for (int r = 0; r < 3; r++) v[r] = S[r][0] * p[0] + S[r][1] * p[1] + S[r][2] * p[2];
+    rec.r0 = make_float4(mx, my, cc * idet, -cb * idet);
+    rec.r1 = make_float4(ca * idet, g.opacity, v[0], v[1]);
+    rec.r2 = make_float4(v[2], S[0][0], 2.f * S[0][1], 2.f * S[0][2]);
+    rec.r3 = make_float4(S[1][1], 2.f * S[1][2], S[2][2], p[2]);
+    // colour: SH with the direction from the camera centre to the mean
+    float d[3] = {g.mu[0] - V.o[0], g.mu[1] - V.o[1], g.mu[2] - V.o[2]};
+    const float dl = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    float rgb[3];
+    sh_colour(a.sh + (long long)i * a.sh_k * 3, a.sh_k, d[0] * dl, d[1] * dl, d[2] * dl, rgb);
+    col = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
+    // opacity-aware radius (appendix B.2) and the rectangle of tiles holding a pixel centre
+    // within [mean2 - r, mean2 + r]
+    const float tO = sqrtf(2.f * logf(g.opacity / a.eps_o));
+    const float mid = 0.5f * (ca + cc);
+    const float lam = mid + sqrtf(fmaxf(0.f, mid * mid - det));
+    const float r = ceilf(tO * sqrtf(lam));
+    const float fx0 = ceilf((mx - r - 15.5f) * (1.f / 16.f)), fx1 = floorf((mx + r - 0.5f) * (1.f / 16.f));
+    const float fy0 = ceilf((my - r - 15.5f) * (1.f / 16.f)), fy1 = floorf((my + r - 0.5f) * (1.f / 16.f));
+    const int tx0 = (int)fmaxf(0.f, fx0), ty0 = (int)fmaxf(0.f, fy0);
+    const int tx1 = (int)fminf((float)(V.tiles_x - 1), fx1), ty1 = (int)fminf((float)(V.tiles_y - 1), fy1);
+    if (tx1 >= tx0 && ty1 >= ty0)
+        rect = make_ushort4((unsigned short)tx0, (unsigned short)ty0, (unsigned short)(tx1 + 1),
+                            (unsigned short)(ty1 + 1));
+    return true;
+}
+
+__device__ __forceinline__ Rec shfl_rec(const Rec& r, int src)
+{
+    Rec o;
+    o.r0 = make_float4(__shfl_sync(kFull, r.r0.x, src), __shfl_sync(kFull, r.r0.y, src),
+                       __shfl_sync(kFull, r.r0.z, src), __shfl_sync(kFull, r.r0.w, src));
+    o.r1 = make_float4(__shfl_sync(kFull, r.r1.x, src), __shfl_sync(kFull, r.r1.y, src),
+                       __shfl_sync(kFull, r.r1.z, src), __shfl_sync(kFull, r.r1.w, src));
+    o.r2 = make_float4(__shfl_sync(kFull, r.r2.x, src), __shfl_sync(kFull, r.r2.y, src),
+                       __shfl_sync(kFull, r.r2.z, src), __shfl_sync(kFull, r.r2.w, src));
+    o.r3 = make_float4(__shfl_sync(kFull, r.r3.x, src), __shfl_sync(kFull, r.r3.y, src),
+                       __shfl_sync(kFull, r.r3.z, src), __shfl_sync(kFull, r.r3.w, src));
+    return o;
+}
+
+// Key of one kept (Gaussian, tile) pair: tile in the high word, ordered depth bits low.
+__device__ __forceinline__ bool tile_key(const PipeArgs& a, const ViewDesc& V, const Rec& r,
+                                         int tx, int ty, unsigned long long* key)
+{
+    const Box b = block_box(tx * kTile, ty * kTile, kTile, V.W, V.H);
+    float t = 0.f;
+    if (!box_keep_depth(r, b, V, a.eps_o, (a.flags & 4) != 0, &t)) return false;
+    if (a.flags & 8) t = r.r3.w;
+    *key = ((unsigned long long)(V.tile_off + ty * V.tiles_x + tx) << 32) | fkey(t);
+    return true;
+}
+
+// Count (EMIT = false) or write (EMIT = true) the kept tiles of this lane's Gaussian, with the
+// two-phase warp load balancing. Every lane of the warp must call it.
+template <bool EMIT>
+__device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, bool has, const Rec& r,
+                               ushort4 rc, uint32_t off, uint32_t want, uint32_t gid)
+{
+    const int lane = threadIdx.x & 31;
+    const int w = (int)rc.z - (int)rc.x, h = (int)rc.w - (int)rc.y;
+    const int ncand = has ? w * h : 0;
+    const bool big = ncand > a.lb_threshold && !(a.flags & 16);
+    uint32_t cnt = 0;
+    if (!big) {
+        for (int k = 0; k < ncand; k++) {
+            const int tx = rc.x + k % w, ty = rc.y + k / w;
+            if (EMIT) {
+                unsigned long long key;
+                if (tile_key(a, V, r, tx, ty, &key)) {
+                    const unsigned long long pos = (unsigned long long)off + cnt;
+                    if (cnt < want && pos < a.capacity) { a.dup_keys[pos] = key; a.dup_vals[pos] = gid; }
+                    cnt++;
+                }
+            } else {
+                const Box b = block_box(tx * kTile, ty * kTile, kTile, V.W, V.H);
+                cnt += box_keep(r, b, a.eps_o) ? 1u : 0u;
+            }
+        }
+    }
+    unsigned bigmask = __ballot_sync(kFull, big);
+    while (bigmask) {
+        const int src = __ffs(bigmask) - 1;
+        bigmask &= bigmask - 1;
+        const Rec rs = shfl_rec(r, src);
+        const int ws = __shfl_sync(kFull, w, src), nc = __shfl_sync(kFull, ncand, src);
+        const int x0 = __shfl_sync(kFull, (int)rc.x, src), y0 = __shfl_sync(kFull, (int)rc.y, src);
+        const uint32_t offs = __shfl_sync(kFull, off, src), wants = __shfl_sync(kFull, want, src);
+        const uint32_t gids = __shfl_sync(kFull, gid, src);
+        uint32_t base = 0;
+        for (int k0 = 0; k0 < nc; k0 += 32) {
+            const int k = k0 + lane;
+            bool keep = false;
+            unsigned long long key = 0;
+            if (k < nc) {
+                const int tx = x0 + k % ws, ty = y0 + k / ws;
+                if (EMIT) keep = tile_key(a, V, rs, tx, ty, &key);
+                else keep = box_keep(rs, block_box(tx * kTile, ty * kTile, kTile, V.W, V.H), a.eps_o);
+            }
+            const unsigned m = __ballot_sync(kFull, keep);
+            if (EMIT && keep) {
+                const uint32_t rank = base + __popc(m & lanemask_lt());
+                const unsigned long long pos = (unsigned long long)offs + rank;
+                if (rank < wants && pos < a.capacity) { a.dup_keys[pos] = key; a.dup_vals[pos] = gids; }
+            }
+            base += __popc(m);
+        }
+        if (lane == src) cnt = base;
+    }
+    return cnt;
+}
+
+__global__ void __launch_bounds__(256) k_preprocess(PipeArgs a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i < a.n;
+    GaussIn g;
+    if (live) load_gauss(a, i, g);
+    for (int v = 0; v < a.nviews; v++) {
+        const ViewDesc& V = a.views[v];
+        Rec r;
+        float4 col;
+        ushort4 rc = make_ushort4(0, 0, 0, 0);
+        bool vis = false;
+        if (live) vis = make_record(a, V, g, i, r, col, rc);
+        else r.r0 = r.r1 = r.r2 = r.r3 = make_float4(0.f, 0.f, 0.f, 0.f);
+        const uint32_t cnt = tiles_pass<false>(a, V, vis, r, rc, 0, 0, 0);
+        if (live) {
+            const long long o = V.rec_off + i;
+            float4* gp = a.geom + 4 * o;
+            gp[0] = r.r0; gp[1] = r.r1; gp[2] = r.r2; gp[3] = r.r3;
+            a.color[o] = col;
+            a.rect[o] = rc;
+            a.counts[o] = cnt;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_duplicate(PipeArgs a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i < a.n;
+    for (int v = 0; v < a.nviews; v++) {
+        const ViewDesc& V = a.views[v];
+        const long long o = V.rec_off + i;
+        Rec r;
+        ushort4 rc = make_ushort4(0, 0, 0, 0);
+        uint32_t off = 0, want = 0;
+        if (live) {
+            r = load_rec(a.geom, o);
+            rc = a.rect[o];
+            off = a.offsets[o];
+            want = a.counts[o];
+        } else {
+            r.r0 = r.r1 = r.r2 = r.r3 = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const uint32_t got = tiles_pass<true>(a, V, live && want > 0, r, rc, off, want, (uint32_t)i);
+        if (live && got != want) {
+            // Preprocess and Duplicate disagree (cannot happen with the shared rounding of the
+            // decision arithmetic; kept as the paper's safety net, appendix B.4): pad with
+            // dummy keys that sort behind every tile.
+            for (uint32_t k = got; k < want; k++) {
+                const unsigned long long pos = (unsigned long long)off + k;
+                if (pos < a.capacity) { a.dup_keys[pos] = ~0ull; a.dup_vals[pos] = (uint32_t)i; }
+            }
+            atomicOr(&a.status->error_bits, 2u);
+            atomicAdd(&a.status->mismatched, 1u);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- scan of the counts
+constexpr int kScanThreads = 256, kScanItems = 16, kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ unsigned long long warp_incl_scan(unsigned long long x)
+{
+    const int lane = threadIdx.x & 31;
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long y = __shfl_up_sync(kFull, x, d);
+        if (lane >= d) x += y;
+    }
+    return x;
+}
+
+// exclusive block scan of one value per thread; returns the prefix, *total the block sum
+__device__ unsigned long long block_excl_scan(unsigned long long x, unsigned long long* total)
+{
+    __shared__ unsigned long long ws[32];
+    __shared__ unsigned long long wtot;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned long long inc = warp_incl_scan(x);
+    if (lane == 31) ws[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long s = lane < nw ? ws[lane] : 0ull;
+        const unsigned long long si = warp_incl_scan(s);
+        if (lane < nw) ws[lane] = si - s;
+        if (lane == nw - 1) wtot = si;
+    }
+    __syncthreads();
+    const unsigned long long r = ws[warp] + inc - x;
+    if (total) *total = wtot;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ in, long long m,
+                                                              unsigned long long* partials)
+{
+    const long long base = (long long)blockIdx.x * kScanTile;
+    unsigned long long s = 0;
+    for (int k = 0; k < kScanItems; k++) {
+        const long long idx = base + (long long)k * kScanThreads + threadIdx.x;
+        if (idx < m) s += in[idx];
+    }
+    unsigned long long tot;
+    block_excl_scan(s, &tot);
+    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_partials(unsigned long long* partials, int np, Status* st)
+{
+    // one block: each thread scans a contiguous run, then a block scan of the run sums
+    const int per = (np + blockDim.x - 1) / blockDim.x;
+    const int b = threadIdx.x * per, e = min(np, b + per);
+    unsigned long long s = 0;
+    for (int k = b; k < e; k++) s += partials[k];
+    unsigned long long tot;
+    unsigned long long run = block_excl_scan(s, &tot);
+    for (int k = b; k < e; k++) {
+        const unsigned long long v = partials[k];
+        partials[k] = run;
+        run += v;
+    }
+    if (threadIdx.x == 0) {
+        st->num_entries = tot;
+        if (tot > st->capacity) atomicOr(&st->error_bits, 1u);
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* __restrict__ in, long long m,
+                                                             const unsigned long long* partials, uint32_t* out)
+{
+    // blocked arrangement: thread t owns items [t*kScanItems, (t+1)*kScanItems) of the tile
+    const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    unsigned long long s = 0;
+    for (int k = 0; k < kScanItems; k++) {
+        const long long idx = base + k;
+        v[k] = idx < m ? in[idx] : 0u;
+        s += v[k];
+    }
+    unsigned long long run = block_excl_scan(s, nullptr) + partials[blockIdx.x];
+    for (int k = 0; k < kScanItems; k++) {
+        const long long idx = base + k;
+        if (idx < m) out[idx] = run > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)run;
+        run += v[k];
+    }
+}
+
+struct ViewPack { ViewDesc v[kMaxViews]; };
+
+__global__ void k_views_copy(ViewPack pack, int nviews, ViewDesc* dst)
+{
+    const int k = threadIdx.x;
+    if (k < nviews) dst[k] = pack.v[k];
+}
+
+}  // namespace
+
+size_t scan_partials_count(long long m) { return (size_t)((m + kScanTile - 1) / kScanTile) + 1; }
+
+cudaError_t launch_views_init(const ViewDesc* host_views, int nviews, ViewDesc* dev_views, cudaStream_t s)
+{
+    ViewPack pack;
+    for (int k = 0; k < nviews && k < kMaxViews; k++) pack.v[k] = host_views[k];
+    k_views_copy<<<1, kMaxViews, 0, s>>>(pack, nviews, dev_views);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_preprocess(const PipeArgs& a, cudaStream_t s)
+{
+    if (a.n == 0) return cudaSuccess;
+    k_preprocess<<<(a.n + 255) / 256, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_counts(const PipeArgs& a, cudaStream_t s)
+{
+    const long long m = (long long)a.n * a.nviews;
+    const int nb = (int)((m + kScanTile - 1) / kScanTile);
+    if (nb > 0) k_scan_reduce<<<nb, kScanThreads, 0, s>>>(a.counts, m, a.scan_partials);
+    k_scan_partials<<<1, 1024, 0, s>>>(a.scan_partials, nb, a.status);
+    if (nb > 0) k_scan_apply<<<nb, kScanThreads, 0, s>>>(a.counts, m, a.scan_partials, a.offsets);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_duplicate(const PipeArgs& a, cudaStream_t s)
+{
+    if (a.n == 0) return cudaSuccess;
+    k_duplicate<<<(a.n + 255) / 256, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace stp

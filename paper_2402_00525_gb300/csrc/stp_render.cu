@@ -1,0 +1,516 @@
+// stp_render.cu -- hierarchical sorted Render (forward) and its replay for the backward pass.
+//
+// StopThePop (arXiv 2402.00525) Sec. 4.4 "Hierarchically sorted rendering", Fig. "pipeline",
+// appendix B.4 "Render"; backward Sec. 4.5.
+//
+// One 256-thread block renders one 16x16 tile. Warp w owns the two horizontally adjacent
+// 4x4 subtiles 2w and 2w+1 (an 8x4 pixel strip); half-warp h owns subtile 2w+h, its 4-lane
+// groups own the subtile's four 2x2 quads, and every lane owns one pixel. Each warp walks the
+// tile's sorted list on its own -- the subtiles are independent -- so no block-wide barrier is
+// needed and a warp whose 32 pixels are all saturated retires early.
+//
+// Queues (per warp, shared memory; entries are (ordered depth key, Gaussian id)):
+//   tail  : per subtile, double-buffered, TAIL = 32n + 32 entries (the paper's 4x4 queue)
+//   mid   : per quad, MID = 4m + 4 entries (the paper's 2x2 queue)
+//   head  : per pixel, HEAD entries in registers (the paper's per-ray queue / k-buffer)
+// Push discipline (the same reading as the CPU oracle):
+//   * the list is consumed in batches of 32 (one entry per lane); every lane culls its entry
+//     against both subtile boxes with Algorithm 1 and computes t_opt on the ray through the
+//     box's x_hat; each subtile's survivors are ranked stably (ties by list position) and
+//     merged into its tail by binary search, existing entries first on ties;
+//   * while a tail holds more than TAIL-32 entries its front 16 go to the mid level; at the end
+//     the tails drain in chunks of at most 16;
+//   * a chunk goes to the quads in sub-batches of 4: each quad culls the 4 against its box,
+//     computes t_opt through its x_hat, ranks them (three shuffles in the 4-lane group) and
+//     merges them into its mid queue; when the mid queue then holds more than MID-4 entries
+//     its front 4 go to the quad's pixels; at the end the mid queues flush in groups of 4;
+//   * a pixel drops alpha < eps_O, computes t_opt on its own ray and inserts into its head;
+//     when the head holds more than HEAD entries the smallest is blended.
+// Blending is front to back with the 3DGS early-out (the Gaussian that would take T below
+// t_min is not blended and the ray stops). The backward kernel is the same code with BWD =
+// true: it recomputes the identical decisions (shared rounding of the decision arithmetic)
+// and, at each blend, forms the gradients with the suffix colour C - C_i and T_N / T_i.
+#include <cuda_runtime.h>
+
+#include "stp_common.cuh"
+#include "stp_kernels.cuh"
+
+namespace stp {
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint32_t depth_key(float t)
+{
+    const uint32_t k = fkey(t);
+    return k == kInvalidKey ? kInvalidKey - 1u : k;
+}
+
+template <int HEAD>
+struct Px {
+    float T, C0, C1, C2, Z;
+    bool done;
+    int nh;
+    uint32_t hk[HEAD + 1];
+    uint32_t hid[HEAD + 1];
+    float hv[HEAD + 1];          // opacity * G2 at the pixel (before the alpha_max clamp)
+    uint32_t nbl;
+    unsigned long long hash;
+};
+
+struct PixCtx {
+    float xc, yc;                // pixel centre
+    float u, w;                  // camera-normalised coordinates of the centre
+    long long pix;               // packed pixel index, -1 outside the image
+    float g0, g1, g2, gz, gbg;   // backward: dL/drgb, dL/ddepth, <dL/drgb, bg>
+    float Cf0, Cf1, Cf2, Zf, Tf; // backward: final colour (no background), depth, T
+};
+
+template <int HEAD, bool BWD>
+__device__ __forceinline__ void blend(const PipeArgs& a, const ViewDesc& V, Px<HEAD>& s,
+                                      const PixCtx& c, uint32_t key, uint32_t id, float val)
+{
+    if (s.done) return;
+    const float alpha = fminf(a.alpha_max, val);
+    const float Tn = __fmul_rn(s.T, __fsub_rn(1.f, alpha));
+    if (Tn < a.t_min) {
+        s.done = true;
+        return;
+    }
+    const long long ri = V.rec_off + id;
+    const float4 col = __ldg(a.color + ri);
+    const float t = fkey_inv(key);
+    const float wgt = alpha * s.T;
+    s.C0 += col.x * wgt;
+    s.C1 += col.y * wgt;
+    s.C2 += col.z * wgt;
+    s.Z += t * wgt;
+    if (BWD) {
+        float* gg = a.grad_geom + ri * kGradStride;
+        atomicAdd(gg + 6, c.g0 * wgt);
+        atomicAdd(gg + 7, c.g1 * wgt);
+        atomicAdd(gg + 8, c.g2 * wgt);
+        const float inv = 1.f / (1.f - alpha);
+        float da = c.g0 * (col.x * s.T - (c.Cf0 - s.C0) * inv) + c.g1 * (col.y * s.T - (c.Cf1 - s.C1) * inv) +
+                   c.g2 * (col.z * s.T - (c.Cf2 - s.C2) * inv) - c.gbg * c.Tf * inv;
+        da += c.gz * (t * s.T - (c.Zf - s.Z) * inv);
+        const Rec r = load_rec(a.geom, ri);
+        if (val < a.alpha_max) {
+            const float dx = c.xc - r.r0.x, dy = c.yc - r.r0.y;
+            const float o = r.r1.y;
+            const float G = expf(-0.5f * (r.r0.z * dx * dx + 2.f * r.r0.w * dx * dy + r.r1.x * dy * dy));
+            atomicAdd(gg + 5, da * G);
+            const float dGG = da * o * G;
+            atomicAdd(gg + 2, dGG * (-0.5f * dx * dx));
+            atomicAdd(gg + 3, dGG * (-dx * dy));
+            atomicAdd(gg + 4, dGG * (-0.5f * dy * dy));
+            atomicAdd(gg + 0, dGG * (r.r0.z * dx + r.r0.w * dy));
+            atomicAdd(gg + 1, dGG * (r.r0.w * dx + r.r1.x * dy));
+        }
+        if (c.gz != 0.f) {
+            // t = |d| L / Q with L = v . d, Q = d^T S d, d = (u, w, 1) (record layout)
+            const float u = c.u, w = c.w;
+            const float L = r.r1.z * u + r.r1.w * w + r.r2.x;
+            const float Q = r.r2.y * u * u + r.r2.z * u * w + r.r2.w * u + r.r3.x * w * w + r.r3.y * w + r.r3.z;
+            const float n = sqrtf(u * u + w * w + 1.f);
+            const float dt = c.gz * wgt;
+            const float fv = dt * n / Q;                   // dt/dv = |d| d / Q
+            const float fs = -dt * n * L / (Q * Q);        // dt/d(coeff) = -|d| L / Q^2 * monomial
+            atomicAdd(gg + 9, fs * u * u);
+            atomicAdd(gg + 10, fs * u * w);
+            atomicAdd(gg + 11, fs * u);
+            atomicAdd(gg + 12, fs * w * w);
+            atomicAdd(gg + 13, fs * w);
+            atomicAdd(gg + 14, fs);
+            atomicAdd(gg + 15, fv * u);
+            atomicAdd(gg + 16, fv * w);
+            atomicAdd(gg + 17, fv);
+        }
+    }
+    s.T = Tn;
+    s.nbl++;
+    s.hash = s.hash * kHashMul + (unsigned long long)(id + 1u);
+}
+
+// insert (key, id, val) after equal keys; when more than HEAD entries are held blend the
+// smallest (Sec. 4.3 k-buffer; evict_first = the alternative "blend before insert" reading)
+template <int HEAD, bool BWD>
+__device__ __forceinline__ void head_push(const PipeArgs& a, const ViewDesc& V, Px<HEAD>& s,
+                                          const PixCtx& c, uint32_t key, uint32_t id, float val,
+                                          bool evict_first)
+{
+    if (evict_first && s.nh == HEAD) {
+        blend<HEAD, BWD>(a, V, s, c, s.hk[0], s.hid[0], s.hv[0]);
+#pragma unroll
+        for (int j = 0; j < HEAD; j++) {
+            s.hk[j] = s.hk[j + 1];
+            s.hid[j] = s.hid[j + 1];
+            s.hv[j] = s.hv[j + 1];
+        }
+        s.hk[HEAD] = kInvalidKey;
+        s.nh--;
+        if (s.done) return;
+    }
+    uint32_t nk[HEAD + 1], ni[HEAD + 1];
+    float nv[HEAD + 1];
+#pragma unroll
+    for (int j = 0; j <= HEAD; j++) {
+        const bool le = s.hk[j] <= key;
+        const bool prev_le = (j == 0) ? true : (s.hk[j - 1] <= key);
+        nk[j] = le ? s.hk[j] : (prev_le ? key : s.hk[j - 1]);
+        ni[j] = le ? s.hid[j] : (prev_le ? id : s.hid[j - 1]);
+        nv[j] = le ? s.hv[j] : (prev_le ? val : s.hv[j - 1]);
+    }
+#pragma unroll
+    for (int j = 0; j <= HEAD; j++) {
+        s.hk[j] = nk[j];
+        s.hid[j] = ni[j];
+        s.hv[j] = nv[j];
+    }
+    s.nh++;
+    if (s.nh > HEAD) {
+        blend<HEAD, BWD>(a, V, s, c, s.hk[0], s.hid[0], s.hv[0]);
+#pragma unroll
+        for (int j = 0; j < HEAD; j++) {
+            s.hk[j] = s.hk[j + 1];
+            s.hid[j] = s.hid[j + 1];
+            s.hv[j] = s.hv[j + 1];
+        }
+        s.hk[HEAD] = kInvalidKey;
+        s.nh--;
+    }
+}
+
+struct Warp {                    // warp-uniform tail state and per-quad mid state
+    int nt[2], ts[2], tb[2];
+    int nm, ms;                  // this lane's quad
+};
+
+template <int HEAD, bool BWD>
+__device__ __forceinline__ void headstage(const PipeArgs& a, const ViewDesc& V, Px<HEAD>& s,
+                                          const PixCtx& c, Warp& wq, uint2* mq, bool pop, int cap)
+{
+    const int pc = pop ? min(cap, wq.nm) : 0;
+    uint2 el[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) el[k] = k < pc ? mq[wq.ms + k] : make_uint2(0u, 0u);
+    wq.ms += pc;
+    wq.nm -= pc;
+    const bool evict_first = (a.flags & 1) != 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        if (k < pc && !s.done) {
+            const uint32_t gid = el[k].y;
+            const Rec r = load_rec(a.geom, V.rec_off + gid);
+            const float val = splat_value(r, c.xc, c.yc);
+            if (a.dbg_nblend != nullptr && !BWD) atomicAdd(&a.status->counters[4], 1ull);
+            if (fminf(a.alpha_max, val) >= a.eps_o) {
+                const float t = depth_uv(r, c.u, c.w);
+                head_push<HEAD, BWD>(a, V, s, c, depth_key(t), gid, val, evict_first);
+            }
+        }
+    }
+}
+
+template <int HEAD, bool BWD>
+__device__ void midstage(const PipeArgs& a, const ViewDesc& V, Px<HEAD>& s, const PixCtx& c,
+                         Warp& wq, const uint2* tailb, uint2* mq, const Box& bQ, bool qval,
+                         int c0, int c1, int lane)
+{
+    const int h = lane >> 4, pq = lane & 3, qbase = lane & ~3;
+    const int cnt = h ? c1 : c0;
+    const uint2* chunk = tailb + (h * 2 + wq.tb[h]) * a.tail + wq.ts[h];
+    const int cmax = max(c0, c1);
+    const int MID = a.mid;
+    const bool centre = (a.flags & 2) != 0;
+    for (int j0 = 0; j0 < cmax; j0 += 4) {
+        const int e = j0 + pq;
+        uint32_t key = kInvalidKey, gid = 0;
+        if (e < cnt) {
+            gid = chunk[e].y;
+            if (qval) {
+                const Rec r = load_rec(a.geom, V.rec_off + gid);
+                const Box bq = bQ;
+                float t;
+                if (box_keep_depth(r, bq, V, a.eps_o, centre, &t)) key = depth_key(t);
+            }
+        }
+        // stable rank of the new entry among the quad's (up to) four
+        uint32_t rk = 0;
+#pragma unroll
+        for (int k = 1; k < 4; k++) {
+            const int op = (pq + k) & 3;
+            const uint32_t o = __shfl_sync(kFull, key, qbase | op);
+            rk += (o < key) || (o == key && op < pq);
+        }
+        const unsigned bal = __ballot_sync(kFull, key != kInvalidKey);
+        const int nn = __popc((bal >> qbase) & 0xFu);
+        if (a.dbg_nblend != nullptr && !BWD) {
+            const unsigned ev = __ballot_sync(kFull, e < cnt && qval);
+            if (lane == 0) atomicAdd(&a.status->counters[2], (unsigned long long)__popc(ev));
+        }
+        uint32_t nk[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) nk[k] = __shfl_sync(kFull, key, qbase | k);
+        // merge: existing entries first on equal keys
+        uint2 ex[4];
+        int exp[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const int i = pq + 4 * r;
+            exp[r] = -1;
+            if (i < wq.nm) {
+                ex[r] = mq[wq.ms + i];
+                int cl = 0;
+#pragma unroll
+                for (int k = 0; k < 4; k++) cl += nk[k] < ex[r].x;
+                exp[r] = i + cl;
+            }
+        }
+        int npos = -1;
+        if (key != kInvalidKey) {
+            int cle = 0;
+            for (int i = 0; i < wq.nm; i++) cle += mq[wq.ms + i].x <= key;
+            npos = (int)rk + cle;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+            if (exp[r] >= 0) mq[exp[r]] = ex[r];
+        if (npos >= 0) mq[npos] = make_uint2(key, gid);
+        __syncwarp();
+        wq.nm += nn;
+        wq.ms = 0;
+        const bool pop = wq.nm > MID - 4;
+        if (__any_sync(kFull, pop)) headstage<HEAD, BWD>(a, V, s, c, wq, mq, pop, 4);
+        __syncwarp();
+    }
+}
+
+__device__ __forceinline__ void merge_tail(const uint2* src, int ne, const uint2* nw, int nn, uint2* dst, int lane)
+{
+    for (int e = lane; e < ne; e += 32) {
+        const uint2 x = src[e];
+        int lo = 0, hi = nn;
+        while (lo < hi) {
+            const int m = (lo + hi) >> 1;
+            if (nw[m].x < x.x) lo = m + 1; else hi = m;
+        }
+        dst[e + lo] = x;
+    }
+    if (lane < nn) {
+        const uint2 x = nw[lane];
+        int lo = 0, hi = ne;
+        while (lo < hi) {
+            const int m = (lo + hi) >> 1;
+            if (src[m].x <= x.x) lo = m + 1; else hi = m;
+        }
+        dst[lane + lo] = x;
+    }
+}
+
+template <int HEAD, bool BWD>
+__global__ void __launch_bounds__(256) k_render(PipeArgs a)
+{
+    extern __shared__ uint2 sm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int TAIL = a.tail, MID = a.mid;
+    uint2* tailb = sm + warp * (4 * TAIL + 64 + 8 * MID);
+    uint2* stage = tailb + 4 * TAIL;
+    uint2* midb = stage + 64;
+    if (a.status->error_bits & 1u) return;
+
+    const int gtile = blockIdx.x;
+    int lo = 0, hi = a.nviews - 1;
+    while (lo < hi) {
+        const int m = (lo + hi + 1) >> 1;
+        if (a.views[m].tile_off <= gtile) lo = m; else hi = m - 1;
+    }
+    const ViewDesc& V = a.views[lo];
+    const int W = V.W, H = V.H;
+    const int tile = gtile - V.tile_off;
+    const int tx = tile % V.tiles_x, ty = tile / V.tiles_x;
+    const int h = lane >> 4, q = (lane & 15) >> 2, pq = lane & 3;
+
+    Box bS[2];
+    bool sval[2];
+#pragma unroll
+    for (int hh = 0; hh < 2; hh++) {
+        const int sidx = warp * 2 + hh;
+        const int ox = tx * kTile + (sidx & 3) * 4, oy = ty * kTile + (sidx >> 2) * 4;
+        sval[hh] = ox < W && oy < H;
+        bS[hh] = block_box(ox, oy, 4, W, H);
+    }
+    const int sme = warp * 2 + h;
+    const int qox = tx * kTile + (sme & 3) * 4 + (q & 1) * 2, qoy = ty * kTile + (sme >> 2) * 4 + (q >> 1) * 2;
+    const bool qval = qox < W && qoy < H;
+    const Box bQ = block_box(qox, qoy, 2, W, H);
+    const int pxi = qox + (pq & 1), pyi = qoy + (pq >> 1);
+    const bool inside = pxi < W && pyi < H;
+
+    PixCtx c;
+    c.xc = pxi + 0.5f;
+    c.yc = pyi + 0.5f;
+    c.u = to_u(V, c.xc);
+    c.w = to_w(V, c.yc);
+    c.pix = inside ? V.pix_off + (long long)pyi * W + pxi : -1;
+    c.g0 = c.g1 = c.g2 = c.gz = c.gbg = 0.f;
+    c.Cf0 = c.Cf1 = c.Cf2 = c.Zf = c.Tf = 0.f;
+    if (BWD && inside) {
+        c.g0 = a.d_rgb[3 * c.pix];
+        c.g1 = a.d_rgb[3 * c.pix + 1];
+        c.g2 = a.d_rgb[3 * c.pix + 2];
+        c.gz = a.d_depth ? a.d_depth[c.pix] : 0.f;
+        c.gbg = c.g0 * a.bg[0] + c.g1 * a.bg[1] + c.g2 * a.bg[2];
+        const float4 cz = reinterpret_cast<const float4*>(a.pix_state)[c.pix];
+        c.Cf0 = cz.x; c.Cf1 = cz.y; c.Cf2 = cz.z; c.Zf = cz.w;
+        c.Tf = a.tfinal_ws[c.pix];
+    }
+
+    Px<HEAD> s;
+    s.T = 1.f;
+    s.C0 = s.C1 = s.C2 = s.Z = 0.f;
+    s.done = !inside;
+    s.nh = 0;
+    s.nbl = 0;
+    s.hash = kHashInit;
+#pragma unroll
+    for (int j = 0; j <= HEAD; j++) {
+        s.hk[j] = kInvalidKey;
+        s.hid[j] = 0;
+        s.hv[j] = 0.f;
+    }
+    Warp wq;
+    wq.nt[0] = wq.nt[1] = wq.ts[0] = wq.ts[1] = wq.tb[0] = wq.tb[1] = 0;
+    wq.nm = wq.ms = 0;
+    uint2* mq = midb + (h * 4 + q) * MID;
+
+    const uint2 rg = a.ranges[gtile];
+    const int lst = (int)rg.x, nL = (int)(rg.y - rg.x);
+    const bool centre = (a.flags & 2) != 0;
+    const bool count = a.dbg_nblend != nullptr && !BWD;
+    unsigned long long n_eval_s = 0, n_surv_s = 0;
+    bool finished = false;
+    for (int b0 = 0; b0 < nL; b0 += 32) {
+        if (__all_sync(kFull, s.done)) {
+            finished = true;
+            break;
+        }
+        const int idx = b0 + lane;
+        const bool in = idx < nL;
+        const uint32_t gid = in ? __ldg(a.svals + lst + idx) : 0u;
+        uint32_t k0 = kInvalidKey, k1 = kInvalidKey;
+        if (in) {
+            const Rec r = load_rec(a.geom, V.rec_off + gid);
+            float t;
+            if (sval[0] && box_keep_depth(r, bS[0], V, a.eps_o, centre, &t)) k0 = depth_key(t);
+            if (sval[1] && box_keep_depth(r, bS[1], V, a.eps_o, centre, &t)) k1 = depth_key(t);
+        }
+        uint32_t r0 = 0, r1 = 0;
+#pragma unroll 8
+        for (int j = 0; j < 32; j++) {
+            const uint32_t o0 = __shfl_sync(kFull, k0, j), o1 = __shfl_sync(kFull, k1, j);
+            r0 += (o0 < k0) || (o0 == k0 && j < lane);
+            r1 += (o1 < k1) || (o1 == k1 && j < lane);
+        }
+        const int nn0 = __popc(__ballot_sync(kFull, k0 != kInvalidKey));
+        const int nn1 = __popc(__ballot_sync(kFull, k1 != kInvalidKey));
+        if (count && lane == 0) {
+            const int nin = min(32, nL - b0);
+            n_eval_s += (unsigned long long)nin * ((sval[0] ? 1 : 0) + (sval[1] ? 1 : 0));
+            n_surv_s += (unsigned long long)(nn0 + nn1);
+        }
+        if (k0 != kInvalidKey) stage[r0] = make_uint2(k0, gid);
+        if (k1 != kInvalidKey) stage[32 + r1] = make_uint2(k1, gid);
+        __syncwarp();
+        merge_tail(tailb + (0 * 2 + wq.tb[0]) * TAIL + wq.ts[0], wq.nt[0], stage, nn0,
+                   tailb + (0 * 2 + (wq.tb[0] ^ 1)) * TAIL, lane);
+        merge_tail(tailb + (1 * 2 + wq.tb[1]) * TAIL + wq.ts[1], wq.nt[1], stage + 32, nn1,
+                   tailb + (1 * 2 + (wq.tb[1] ^ 1)) * TAIL, lane);
+        __syncwarp();
+        wq.nt[0] += nn0;
+        wq.nt[1] += nn1;
+        wq.ts[0] = wq.ts[1] = 0;
+        wq.tb[0] ^= 1;
+        wq.tb[1] ^= 1;
+        while (wq.nt[0] > TAIL - 32 || wq.nt[1] > TAIL - 32) {
+            const int c0 = wq.nt[0] > TAIL - 32 ? 16 : 0, c1 = wq.nt[1] > TAIL - 32 ? 16 : 0;
+            midstage<HEAD, BWD>(a, V, s, c, wq, tailb, mq, bQ, qval, c0, c1, lane);
+            wq.ts[0] += c0; wq.nt[0] -= c0;
+            wq.ts[1] += c1; wq.nt[1] -= c1;
+        }
+    }
+    if (!finished) {
+        while ((wq.nt[0] > 0 || wq.nt[1] > 0) && !__all_sync(kFull, s.done)) {
+            const int c0 = min(16, wq.nt[0]), c1 = min(16, wq.nt[1]);
+            midstage<HEAD, BWD>(a, V, s, c, wq, tailb, mq, bQ, qval, c0, c1, lane);
+            wq.ts[0] += c0; wq.nt[0] -= c0;
+            wq.ts[1] += c1; wq.nt[1] -= c1;
+        }
+        while (__any_sync(kFull, wq.nm > 0) && !__all_sync(kFull, s.done)) {
+            headstage<HEAD, BWD>(a, V, s, c, wq, mq, wq.nm > 0, 4);
+            __syncwarp();
+        }
+#pragma unroll
+        for (int j = 0; j < HEAD; j++)
+            if (j < s.nh) blend<HEAD, BWD>(a, V, s, c, s.hk[j], s.hid[j], s.hv[j]);
+    }
+    if (count) {
+        if (lane == 0) {
+            atomicAdd(&a.status->counters[0], n_eval_s);
+            atomicAdd(&a.status->counters[1], n_surv_s);
+        }
+        atomicAdd(&a.status->counters[3], (unsigned long long)s.nbl);
+    }
+    if (!inside) return;
+    const long long p = c.pix;
+    if (!BWD) {
+        a.rgb[3 * p] = s.C0 + s.T * a.bg[0];
+        a.rgb[3 * p + 1] = s.C1 + s.T * a.bg[1];
+        a.rgb[3 * p + 2] = s.C2 + s.T * a.bg[2];
+        a.depth[p] = s.Z;
+        a.tfinal_ws[p] = s.T;
+        reinterpret_cast<float4*>(a.pix_state)[p] = make_float4(s.C0, s.C1, s.C2, s.Z);
+        if (a.tfinal_out) a.tfinal_out[p] = s.T;
+        if (a.dbg_nblend) a.dbg_nblend[p] = s.nbl;
+        if (a.dbg_hash) a.dbg_hash[p] = s.hash;
+    } else {
+        if (a.dbg_nblend && a.dbg_nblend[p] != s.nbl) atomicOr(&a.status->error_bits, 8u);
+    }
+}
+
+template <int HEAD>
+cudaError_t launch_head(const PipeArgs& a, bool bwd, size_t smem, cudaStream_t s)
+{
+    if (bwd) {
+        cudaFuncSetAttribute(k_render<HEAD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_render<HEAD, true><<<a.total_tiles, 256, smem, s>>>(a);
+    } else {
+        cudaFuncSetAttribute(k_render<HEAD, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_render<HEAD, false><<<a.total_tiles, 256, smem, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t render_smem_bytes(int tail, int mid) { return (size_t)8 * (4 * tail + 64 + 8 * mid) * sizeof(uint2); }
+
+bool render_head_supported(int head) { return head == 1 || head == 2 || head == 4 || head == 8 || head == 16; }
+
+cudaError_t launch_render(const PipeArgs& a, bool backward, cudaStream_t s)
+{
+    if (a.total_tiles == 0) return cudaSuccess;
+    const size_t smem = render_smem_bytes(a.tail, a.mid);
+    switch (a.head) {
+        case 1: return launch_head<1>(a, backward, smem, s);
+        case 2: return launch_head<2>(a, backward, smem, s);
+        case 4: return launch_head<4>(a, backward, smem, s);
+        case 8: return launch_head<8>(a, backward, smem, s);
+        case 16: return launch_head<16>(a, backward, smem, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace stp

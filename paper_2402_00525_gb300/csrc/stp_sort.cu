@@ -1,0 +1,277 @@
+// stp_sort.cu -- global sort of (tile, depth) keys and the per-tile ranges.
+//
+// StopThePop (arXiv 2402.00525) keeps 3DGS's single global sort of combined keys, tile id in
+// the high bits and depth in the low bits (Sec. 3.1, appendix B.3), and relies on a stable
+// order so that forward and backward see the same list (Sec. 4.5). This is a stable LSD radix
+// sort with 8-bit digits over only the key bits in use (32 depth bits + the bits of the tile
+// count), three kernels per digit:
+//   hist    -- every block counts the digits of a fixed contiguous range of the input;
+//   scan    -- one block turns the [digit][block] counts into exclusive global offsets;
+//   scatter -- every block re-reads its range in 4096-item tiles and writes each item to
+//              offset[digit][block] + (items of that digit earlier in the block's range).
+// Within a tile, warp w owns items [512 w, 512 w + 512) in order and ranks equal digits with
+// __match_any_sync, so the write order preserves the input order (stability).
+// The grid is fixed (a multiple of the SM count) and the entry count may be read from device
+// memory, so the whole sequence needs no host synchronisation and can be graph-captured.
+#include <cuda_runtime.h>
+
+#include "stp_common.cuh"
+#include "stp_kernels.cuh"
+
+namespace stp {
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kThreads = 256, kItems = 16, kTileItems = kThreads * kItems;
+constexpr int kRadix = 256;
+constexpr int kMaxGrid = 1024;
+
+__device__ __forceinline__ long long eff_count(long long nmax, const unsigned long long* n_dev)
+{
+    if (!n_dev) return nmax;
+    const unsigned long long d = *n_dev;
+    return d < (unsigned long long)nmax ? (long long)d : nmax;
+}
+
+__device__ __forceinline__ void block_range(long long n, int G, int b, long long* beg, long long* end)
+{
+    const long long tiles = (n + kTileItems - 1) / kTileItems;
+    const long long per = (tiles + G - 1) / G;
+    *beg = (long long)b * per * kTileItems;
+    const long long e = *beg + per * kTileItems;
+    *end = e < n ? e : n;
+    if (*beg > n) *beg = n;
+}
+
+__global__ void __launch_bounds__(kThreads) k_hist(const uint64_t* __restrict__ kin, long long nmax,
+                                                   const unsigned long long* n_dev, int shift,
+                                                   uint32_t* __restrict__ hist, int G)
+{
+    __shared__ uint32_t s_h[kThreads / 32][kRadix];
+    const int warp = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < (kThreads / 32) * kRadix; k += kThreads) (&s_h[0][0])[k] = 0;
+    __syncthreads();
+    long long beg, end;
+    block_range(eff_count(nmax, n_dev), G, blockIdx.x, &beg, &end);
+    for (long long idx = beg + threadIdx.x; idx < end; idx += kThreads) {
+        const uint32_t d = (uint32_t)(kin[idx] >> shift) & (kRadix - 1);
+        atomicAdd(&s_h[warp][d], 1u);
+    }
+    __syncthreads();
+    uint32_t s = 0;
+    for (int w = 0; w < kThreads / 32; w++) s += s_h[w][threadIdx.x];
+    hist[threadIdx.x * G + blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(1024) k_scan(uint32_t* __restrict__ hist, int m)
+{
+    __shared__ uint32_t ws[32];
+    const int per = (m + blockDim.x - 1) / blockDim.x;
+    const int b = threadIdx.x * per, e = min(m, b + per);
+    uint32_t s = 0;
+    for (int k = b; k < e; k++) s += hist[k];
+    // block exclusive scan of s
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = s;
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, inc, d);
+        if (lane >= d) inc += y;
+    }
+    if (lane == 31) ws[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t x = ws[lane];
+        uint32_t xi = x;
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, xi, d);
+            if (lane >= d) xi += y;
+        }
+        ws[lane] = xi - x;
+    }
+    __syncthreads();
+    uint32_t run = ws[warp] + inc - s;
+    for (int k = b; k < e; k++) {
+        const uint32_t v = hist[k];
+        hist[k] = run;
+        run += v;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_scatter(const uint64_t* __restrict__ kin,
+                                                      const uint32_t* __restrict__ vin,
+                                                      uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                      long long nmax, const unsigned long long* n_dev,
+                                                      int shift, const uint32_t* __restrict__ offs, int G)
+{
+    __shared__ uint32_t s_run[kRadix];
+    __shared__ uint32_t s_base[kRadix];
+    __shared__ uint32_t s_wh[kThreads / 32][kRadix];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    long long beg, end;
+    block_range(eff_count(nmax, n_dev), G, blockIdx.x, &beg, &end);
+    s_run[threadIdx.x] = offs[threadIdx.x * G + blockIdx.x];
+    __syncthreads();
+    const unsigned lt_mask = lanemask_lt();
+    for (long long tb = beg; tb < end; tb += kTileItems) {
+        for (int d = lane; d < kRadix; d += 32) s_wh[warp][d] = 0;
+        __syncwarp();
+        uint64_t k[kItems];
+        uint32_t v[kItems], lr[kItems], dg[kItems];
+        const long long wb = tb + (long long)warp * (32 * kItems);
+#pragma unroll
+        for (int j = 0; j < kItems; j++) {
+            const long long idx = wb + j * 32 + lane;
+            const bool in = idx < end;
+            k[j] = in ? kin[idx] : 0ull;
+            v[j] = in ? vin[idx] : 0u;
+            dg[j] = in ? ((uint32_t)(k[j] >> shift) & (kRadix - 1)) : (uint32_t)kRadix;
+        }
+#pragma unroll
+        for (int j = 0; j < kItems; j++) {
+            const uint32_t d = dg[j];
+            const unsigned m = __match_any_sync(kFull, d);
+            const uint32_t lt = __popc(m & lt_mask);
+            const uint32_t cur = d < kRadix ? s_wh[warp][d] : 0u;
+            lr[j] = cur + lt;
+            __syncwarp();
+            if (d < kRadix && lt == 0) s_wh[warp][d] = cur + __popc(m);
+            __syncwarp();
+        }
+        __syncthreads();
+        {
+            const int d = threadIdx.x;
+            uint32_t run = 0;
+            for (int w = 0; w < kThreads / 32; w++) {
+                const uint32_t c = s_wh[w][d];
+                s_wh[w][d] = run;
+                run += c;
+            }
+            s_base[d] = s_run[d];
+            s_run[d] += run;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kItems; j++) {
+            const uint32_t d = dg[j];
+            if (d < kRadix) {
+                const uint32_t pos = s_base[d] + s_wh[warp][d] + lr[j];
+                kout[pos] = k[j];
+                vout[pos] = v[j];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) k_ranges(const uint64_t* __restrict__ keys, long long nmax,
+                                                const Status* __restrict__ st, int total_tiles,
+                                                uint2* __restrict__ ranges)
+{
+    if (st->error_bits & 1u) return;   // capacity exceeded: the lists are incomplete
+    const long long n = eff_count(nmax, &st->num_entries);
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const uint32_t t = (uint32_t)(keys[k] >> 32);
+        if (t >= (uint32_t)total_tiles) continue;
+        if (k == 0 || (uint32_t)(keys[k - 1] >> 32) != t) ranges[t].x = (uint32_t)k;
+        if (k == n - 1 || (uint32_t)(keys[k + 1] >> 32) != t) ranges[t].y = (uint32_t)(k + 1);
+    }
+}
+
+int sort_grid(long long n)
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 148;
+    }
+    const long long tiles = (n + kTileItems - 1) / kTileItems;
+    long long g = 4LL * sms;
+    if (g > tiles) g = tiles;
+    if (g < 1) g = 1;
+    if (g > kMaxGrid) g = kMaxGrid;
+    return (int)g;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+size_t sort_hist_bytes() { return align256((size_t)kRadix * kMaxGrid * sizeof(uint32_t)); }
+
+size_t sort_temp_bytes(long long n)
+{
+    // histogram / offsets of the largest grid, then the ping-pong partner of the output
+    return sort_hist_bytes() + align256((size_t)n * sizeof(uint64_t)) + align256((size_t)n * sizeof(uint32_t));
+}
+
+static void sort_pass(const uint64_t* sk, const uint32_t* sv, uint64_t* dk, uint32_t* dv, long long n,
+                      const unsigned long long* n_dev, int shift, uint32_t* hist, int G, cudaStream_t s)
+{
+    k_hist<<<G, kThreads, 0, s>>>(sk, n, n_dev, shift, hist, G);
+    k_scan<<<1, 1024, 0, s>>>(hist, kRadix * G);
+    k_scatter<<<G, kThreads, 0, s>>>(sk, sv, dk, dv, n, n_dev, shift, hist, G);
+}
+
+// Library sort: input preserved, output in (kout, vout); temp holds the histogram and the
+// ping-pong partner, so the passes alternate between `out` and the partner and the last
+// pass writes `out`.
+cudaError_t sort_pairs(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout,
+                       long long n, const unsigned long long* n_dev, int key_bits, void* temp,
+                       size_t temp_bytes, cudaStream_t s)
+{
+    if (temp_bytes < sort_temp_bytes(n)) return cudaErrorInvalidValue;
+    const int passes = (key_bits + 7) / 8;
+    if (n == 0 || passes == 0) return cudaSuccess;
+    const int G = sort_grid(n);
+    uint32_t* hist = (uint32_t*)temp;
+    uint64_t* kalt = (uint64_t*)((char*)temp + sort_hist_bytes());
+    uint32_t* valt = (uint32_t*)((char*)temp + sort_hist_bytes() + align256((size_t)n * sizeof(uint64_t)));
+    const uint64_t* sk = kin;
+    const uint32_t* sv = vin;
+    for (int p = 0; p < passes; p++) {
+        const bool to_out = ((passes - 1 - p) % 2) == 0;
+        uint64_t* dk = to_out ? kout : kalt;
+        uint32_t* dv = to_out ? vout : valt;
+        sort_pass(sk, sv, dk, dv, n, n_dev, 8 * p, hist, G, s);
+        sk = dk;
+        sv = dv;
+    }
+    return cudaGetLastError();
+}
+
+// Pipeline sort: Duplicate's output in buffer A = (keys_alt, vals_alt) is sorted by ping-pong
+// between A and B = (keys, vals); pass p reads A and writes B for even p. The sorted pairs end
+// in B for an odd number of passes and in A otherwise (pipeline_sorted_in_alt()).
+bool pipeline_sorted_in_alt(int key_bits) { return ((key_bits + 7) / 8) % 2 == 0; }
+
+cudaError_t pipeline_sort(const PipeArgs& a, cudaStream_t s)
+{
+    const int passes = (a.key_bits + 7) / 8;
+    const long long n = (long long)a.capacity;
+    if (n == 0) return cudaSuccess;
+    const int G = sort_grid(n);
+    uint32_t* hist = (uint32_t*)a.sort_temp;
+    const unsigned long long* n_dev = &a.status->num_entries;
+    for (int p = 0; p < passes; p++) {
+        const bool even = (p % 2) == 0;
+        sort_pass(even ? a.keys_alt : a.keys, even ? a.vals_alt : a.vals, even ? a.keys : a.keys_alt,
+                  even ? a.vals : a.vals_alt, n, n_dev, 8 * p, hist, G, s);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ranges(const PipeArgs& a, cudaStream_t s)
+{
+    cudaMemsetAsync(a.ranges, 0, (size_t)a.total_tiles * sizeof(uint2), s);
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_ranges<<<sms * 8, 256, 0, s>>>(a.skeys, (long long)a.capacity, a.status, a.total_tiles, a.ranges);
+    return cudaGetLastError();
+}
+
+}  // namespace stp

@@ -1,0 +1,206 @@
+"""PyTorch front end of libstp: device memory, streams and autograd plumbing only.
+
+Every step of the renderer runs in libstp.so (include/stp.h). This module allocates the
+caller-owned workspace with torch, passes raw device pointers through the C ABI, and wraps
+forward + backward in a torch.autograd.Function.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import List, Sequence
+
+import numpy as np
+import torch
+
+from . import _native as N
+from .inputs import Camera, RenderParams, Scene
+
+FIELDS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+def scene_to_device(scene: Scene, device="cuda") -> dict:
+    """Copy a numpy Scene to contiguous float32 device tensors."""
+    out = {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k), np.float32)).to(device)
+           for k in FIELDS}
+    out["sh_degree"] = scene.sh_degree
+    return out
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def gaussians_struct(g: dict) -> N.Gaussians:
+    s = N.Gaussians()
+    for k in FIELDS:
+        t = g[k]
+        if t.dtype != torch.float32 or not t.is_contiguous() or not t.is_cuda:
+            raise ValueError("%s must be a contiguous float32 CUDA tensor" % k)
+        setattr(s, k, _ptr(t))
+    s.n = int(g["means"].shape[0])
+    s.sh_degree = int(g["sh_degree"])
+    return s
+
+
+class Renderer:
+    """Renders one scene size from a fixed list of cameras with fixed parameters.
+
+    The workspace is sized for the configuration and grown on demand when the sort-entry
+    capacity turns out too small (this needs one host synchronisation; pass check=False in
+    a steady-state loop once the capacity is known). A backward pass reuses the workspace of
+    the preceding forward pass, so do not interleave forward calls between the two.
+    """
+
+    def __init__(self, n: int, cams: Sequence[Camera], prm: RenderParams, device="cuda",
+                 backward: bool = False, debug: bool = False, capacity: int | None = None,
+                 headroom: float = 1.15):
+        self.n = int(n)
+        self.cams = list(cams)
+        self.prm = prm
+        self.device = torch.device(device)
+        self.flags = (N.FLAG_BACKWARD if backward else 0) | (N.FLAG_DEBUG_STATS if debug else 0)
+        self.headroom = headroom
+        self._cams_arr = N.cameras_array(self.cams)
+        self.total_pixels = sum(c.width * c.height for c in self.cams)
+        self.pixel_offsets = np.cumsum([0] + [c.width * c.height for c in self.cams])
+        self.ws = None
+        self._alloc(capacity or 0)
+
+    # ------------------------------------------------------------------ workspace
+    def _params(self) -> N.Params:
+        return N.params_struct(self.prm, self.flags, self.capacity_req)
+
+    def _alloc(self, capacity: int) -> None:
+        self.capacity_req = int(capacity)
+        self.p = self._params()
+        self.layout = N.layout(self.n, self.cams, self.p)
+        self.capacity = int(self.layout.capacity)
+        self.ws = None
+        torch.cuda.empty_cache() if self.device.type == "cuda" else None
+        self.ws = torch.empty(int(self.layout.total), dtype=torch.uint8, device=self.device)
+
+    def _region(self, off: int, count: int, dtype) -> torch.Tensor:
+        nbytes = count * torch.empty((), dtype=dtype).element_size()
+        return self.ws[off:off + nbytes].view(dtype)
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(self.layout.total)
+
+    # ------------------------------------------------------------------ forward
+    def forward(self, g: dict, out=None, check: bool = True, stream=None):
+        """Render every camera. Returns (rgb [P,3], depth [P], tfinal [P]) packed view after
+        view (see split())."""
+        P = self.total_pixels
+        if out is None:
+            out = (torch.empty((P, 3), dtype=torch.float32, device=self.device),
+                   torch.empty((P,), dtype=torch.float32, device=self.device),
+                   torch.empty((P,), dtype=torch.float32, device=self.device))
+        rgb, depth, tfin = out
+        s = gaussians_struct(g)
+        if s.n != self.n:
+            raise ValueError("renderer was built for n = %d, got %d" % (self.n, s.n))
+        strm = stream if stream is not None else torch.cuda.current_stream(self.device)
+        for attempt in range(3):
+            N.check(N.lib().stp_render(C.byref(s), C.cast(self._cams_arr, C.c_void_p), len(self.cams),
+                                       C.byref(self.p), C.c_void_p(_ptr(self.ws)), self.layout.total,
+                                       C.c_void_p(_ptr(rgb)), C.c_void_p(_ptr(depth)),
+                                       C.c_void_p(_ptr(tfin)), C.c_void_p(strm.cuda_stream)))
+            if not check:
+                break
+            st = N.read_status(_ptr(self.ws), strm.cuda_stream, raise_on_error=False)
+            if st.error_bits & 1:
+                self._alloc(int(st.num_entries * self.headroom) + 1024)
+                continue
+            if st.error_bits & ~2:
+                N.check(N.lib().stp_read_status(C.c_void_p(_ptr(self.ws)), C.byref(N.RunStatus()),
+                                                C.c_void_p(strm.cuda_stream)))
+            self.last_status = st
+            break
+        return rgb, depth, tfin
+
+    def status(self, stream=None) -> N.RunStatus:
+        strm = stream if stream is not None else torch.cuda.current_stream(self.device)
+        return N.read_status(_ptr(self.ws), strm.cuda_stream, raise_on_error=False)
+
+    # ------------------------------------------------------------------ backward
+    def backward(self, g: dict, d_rgb: torch.Tensor, d_depth: torch.Tensor | None, grads: dict,
+                 stream=None) -> None:
+        """Accumulate (+=) the gradients of <d_rgb, rgb> + <d_depth, depth> of the last forward
+        into grads (dict of tensors shaped like the inputs)."""
+        if not (self.flags & N.FLAG_BACKWARD):
+            raise RuntimeError("construct the Renderer with backward=True")
+        s = gaussians_struct(g)
+        gs = N.GaussiansGrad()
+        for k in FIELDS:
+            t = grads[k]
+            if t.dtype != torch.float32 or not t.is_contiguous():
+                raise ValueError("gradient %s must be contiguous float32" % k)
+            setattr(gs, k, _ptr(t))
+        d_rgb = d_rgb.contiguous()
+        d_depth = None if d_depth is None else d_depth.contiguous()
+        strm = stream if stream is not None else torch.cuda.current_stream(self.device)
+        N.check(N.lib().stp_render_backward(C.byref(s), C.cast(self._cams_arr, C.c_void_p), len(self.cams),
+                                            C.byref(self.p), C.c_void_p(_ptr(self.ws)), self.layout.total,
+                                            C.c_void_p(_ptr(d_rgb)), C.c_void_p(_ptr(d_depth)),
+                                            C.byref(gs), C.c_void_p(strm.cuda_stream)))
+
+    # ------------------------------------------------------------------ inspection
+    def split(self, packed: torch.Tensor) -> List[torch.Tensor]:
+        """Per-view images [H, W, ...] from a packed [P, ...] tensor."""
+        out = []
+        for k, c in enumerate(self.cams):
+            a, b = int(self.pixel_offsets[k]), int(self.pixel_offsets[k + 1])
+            out.append(packed[a:b].reshape((c.height, c.width) + tuple(packed.shape[1:])))
+        return out
+
+    def debug_stats(self):
+        """Per-pixel blend counts and blend-order hashes (needs debug=True)."""
+        L = self.layout
+        P = int(L.total_pixels)
+        nbl = self._region(L.dbg_nblend, P, torch.int32)
+        h = self._region(L.dbg_hash, P, torch.int64)
+        return nbl, h
+
+    def sorted_lists(self):
+        """(ranges [T,2] int32, sorted keys int64, sorted ids int32) of the last forward."""
+        L = self.layout
+        st = self.status()
+        E = min(int(st.num_entries), self.capacity)
+        ranges = self._region(L.ranges, int(L.total_tiles) * 2, torch.int32).view(-1, 2)
+        keys = self._region(L.sorted_keys, E, torch.int64)
+        vals = self._region(L.sorted_vals, E, torch.int32)
+        return ranges, keys, vals
+
+    def records(self):
+        L = self.layout
+        m = self.n * len(self.cams)
+        geom = self._region(L.geom, m * 16, torch.float32).view(len(self.cams), self.n, 16)
+        color = self._region(L.color, m * 4, torch.float32).view(len(self.cams), self.n, 4)
+        rect = self._region(L.rect, m * 4, torch.int16).view(len(self.cams), self.n, 4)
+        counts = self._region(L.counts, m, torch.int32).view(len(self.cams), self.n)
+        return geom, color, rect, counts
+
+
+class _RenderFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, renderer: Renderer, sh_degree: int, means, log_scales, quats, opacity_logits, sh):
+        g = dict(means=means.contiguous(), log_scales=log_scales.contiguous(), quats=quats.contiguous(),
+                 opacity_logits=opacity_logits.contiguous(), sh=sh.contiguous(), sh_degree=sh_degree)
+        rgb, depth, _ = renderer.forward(g)
+        ctx.renderer = renderer
+        ctx.g = g
+        return rgb, depth
+
+    @staticmethod
+    def backward(ctx, d_rgb, d_depth):
+        g = ctx.g
+        grads = {k: torch.zeros_like(g[k]) for k in FIELDS}
+        ctx.renderer.backward(g, d_rgb, d_depth, grads)
+        return (None, None) + tuple(grads[k] for k in FIELDS)
+
+
+def render(renderer: Renderer, g: dict):
+    """Differentiable render: returns (rgb [P,3], depth [P]); backward via libstp."""
+    return _RenderFn.apply(renderer, int(g["sh_degree"]), g["means"], g["log_scales"], g["quats"],
+                           g["opacity_logits"], g["sh"])

@@ -1,0 +1,292 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bar (from the method's definition of order and the FP32 arithmetic of the kernels):
+  * blend order: per pixel, the count and the order hash of the blended Gaussians are equal on
+    every pixel the oracle marks decided (no depth comparison within 1e-6 relative, no cull /
+    alpha / transmittance test within 1e-5 relative of its threshold);
+  * colour: max abs difference <= 1e-4 per channel on decided pixels;
+  * depth (unnormalised volumetric depth): |diff| <= 1e-4 (1 + |depth|); T: <= 1e-5.
+"""
+import ctypes as C
+import dataclasses
+
+import numpy as np
+import pytest
+
+from paper_2402_00525_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2402_00525_gb300 import _native as N  # noqa: E402
+from paper_2402_00525_gb300 import renderer as R  # noqa: E402
+
+
+def gpu_render(scene, cams, prm, debug=True, capacity=None):
+    g = R.scene_to_device(scene)
+    r = R.Renderer(scene.n, cams, prm, debug=debug, capacity=capacity)
+    rgb, depth, tf = r.forward(g)
+    torch.cuda.synchronize()
+    out = dict(rgb=[x.cpu().numpy() for x in r.split(rgb)], depth=[x.cpu().numpy() for x in r.split(depth)],
+               tfinal=[x.cpu().numpy() for x in r.split(tf)], renderer=r, g=g)
+    if debug:
+        nbl, h = r.debug_stats()
+        out["nblend"] = [x.cpu().numpy() for x in r.split(nbl)]
+        out["hash"] = [x.cpu().numpy().view(np.uint64) for x in r.split(h)]
+    return out
+
+
+def compare_view(gpu, k, ora, tiles_mask=None, min_decided=0.99, label=""):
+    dec = ora["decided"].copy()
+    if tiles_mask is not None:
+        dec &= tiles_mask
+        denom = tiles_mask.sum()
+    else:
+        denom = dec.size
+    frac = dec.sum() / max(denom, 1)
+    assert frac >= min_decided, "%s decided fraction %.4f" % (label, frac)
+    nb = gpu["nblend"][k]
+    hs = gpu["hash"][k]
+    bad = dec & ((nb != ora["nblend"]) | (hs != ora["hash"]))
+    assert bad.sum() == 0, "%s: %d decided pixels differ in blend order (of %d)" % (label, bad.sum(), dec.sum())
+    drgb = np.abs(gpu["rgb"][k] - ora["rgb"])[dec]
+    assert drgb.size == 0 or drgb.max() <= 1e-4, "%s rgb max diff %g" % (label, drgb.max())
+    dd = np.abs(gpu["depth"][k] - ora["depth"])[dec]
+    assert dd.size == 0 or (dd / (1 + np.abs(ora["depth"][dec]))).max() <= 1e-4
+    dt = np.abs(gpu["tfinal"][k] - ora["tfinal"])[dec]
+    assert dt.size == 0 or dt.max() <= 1e-5
+    return frac
+
+
+def test_plain_forward_256_matches_oracle(oracle):
+    sc, cams, prm = I.plain_forward_workload()
+    gpu = gpu_render(sc, cams, prm)
+    ora = oracle.render(sc, cams[0], prm)
+    compare_view(gpu, 0, ora, label="plain 256")
+    st = gpu["renderer"].status()
+    assert st.num_entries == ora["num_entries"]
+    assert st.error_bits == 0
+
+
+def test_preprocess_records_match_oracle(oracle):
+    sc = I.cluster_scene(20000, 77, nclusters=6, centre_range=1.5, scale_range=(0.003, 0.2))
+    cam = I.look_at((0.5, -0.3, -6), (0, 0, 0), (0, 1, 0), 333, 250, 50.0)
+    prm = I.RenderParams()
+    gpu = gpu_render(sc, [cam], prm, debug=False)
+    geom, color, rect, counts = [x.cpu().numpy() for x in gpu["renderer"].records()]
+    with oracle.OracleRun(sc, cam, prm) as r:
+        pp = r.preprocess()
+    vis_g = geom[0, :, 5] > 0
+    vis_o = pp["visible"] > 0
+    near = pp["margin"] < 1e-5
+    assert np.array_equal(vis_g[~near], vis_o[~near])
+    v = vis_o & vis_g
+    g = geom[0][v]
+    assert np.allclose(g[:, 0:2], pp["mean2"][v], rtol=1e-5, atol=2e-3)
+    A = np.stack([g[:, 2], g[:, 3], g[:, 4]], 1)
+    assert np.allclose(A, pp["conic"][v], rtol=2e-3, atol=1e-6)
+    assert np.allclose(g[:, 5], pp["opacity"][v], rtol=1e-5)
+    assert np.allclose(color[0][v][:, :3], pp["color"][v], atol=2e-5)
+    # camera-space Sigma^-1 and v = S p against the oracle's world-space values
+    Rc = cam.R
+    s6 = pp["sinv6"][v]
+    Sw = np.stack([np.stack([s6[:, 0], s6[:, 1], s6[:, 2]], 1), np.stack([s6[:, 1], s6[:, 3], s6[:, 4]], 1),
+                   np.stack([s6[:, 2], s6[:, 4], s6[:, 5]], 1)], 1)
+    Sc = Rc @ Sw @ Rc.T
+    vc = (Rc @ pp["v"][v].T).T
+    gS = np.stack([g[:, 9], g[:, 10] / 2, g[:, 11] / 2, g[:, 12], g[:, 13] / 2, g[:, 14]], 1)
+    oS = np.stack([Sc[:, 0, 0], Sc[:, 0, 1], Sc[:, 0, 2], Sc[:, 1, 1], Sc[:, 1, 2], Sc[:, 2, 2]], 1)
+    scale = np.abs(oS).max(1, keepdims=True)
+    assert np.abs(gS - oS).max() <= 1e-4 * scale.max() and (np.abs(gS - oS) / scale).max() < 1e-4
+    gv = np.stack([g[:, 6], g[:, 7], g[:, 8]], 1)
+    assert (np.abs(gv - vc) / np.abs(vc).max(1, keepdims=True)).max() < 1e-4
+    rr = rect[0][v].astype(np.int64)
+    orc = pp["rect"][v]
+    same_rect = (rr[:, 0] == orc[:, 0]) & (rr[:, 1] == orc[:, 1]) & (rr[:, 2] == orc[:, 2] + 1) & (rr[:, 3] == orc[:, 3] + 1)
+    assert same_rect.mean() > 0.999
+    same_cnt = counts[0][v] == pp["ntiles"][v]
+    assert same_cnt.mean() > 0.999
+    assert gpu["renderer"].status().mismatched == 0
+
+
+def test_sorted_tile_lists_match_oracle(oracle):
+    sc = I.cluster_scene(30000, 78, nclusters=8, centre_range=1.5, scale_range=(0.003, 0.2))
+    cam = I.look_at((0.2, 0.4, -6), (0, 0, 0), (0, 1, 0), 320, 256, 50.0)
+    prm = I.RenderParams()
+    gpu = gpu_render(sc, [cam], prm, debug=False)
+    ranges, keys, vals = [x.cpu().numpy() for x in gpu["renderer"].sorted_lists()]
+    with oracle.OracleRun(sc, cam, prm) as r:
+        start, ids, ts = r.tile_lists()
+    assert len(vals) == len(ids)
+    keys = keys.view(np.uint64)
+    tiles = (keys >> np.uint64(32)).astype(np.int64)
+    assert np.all(np.diff(tiles) >= 0)
+    lo = (keys & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    t_gpu = np.where(lo & 0x80000000, lo & 0x7FFFFFFF, ~lo).astype(np.uint32).view(np.float32)
+    mism_tiles = 0
+    for t in range(cam.num_tiles):
+        a, b = int(start[t]), int(start[t + 1])
+        ga, gb = int(ranges[t, 0]), int(ranges[t, 1])
+        assert gb - ga == b - a
+        if b == a:
+            continue
+        assert np.array_equal(np.sort(vals[ga:gb]), np.sort(ids[a:b]))
+        assert np.allclose(t_gpu[ga:gb], ts[a:b], rtol=2e-6, atol=1e-6)
+        if not np.array_equal(vals[ga:gb], ids[a:b]):
+            # only permutations among near-equal depths are allowed
+            gaps = np.abs(np.diff(ts[a:b])) / np.maximum(np.abs(ts[a:b][1:]), 1e-30)
+            assert gaps.min() < 1e-6
+            mism_tiles += 1
+    assert mism_tiles <= cam.num_tiles * 0.01
+
+
+@pytest.mark.parametrize("size", [(100, 75), (17, 33), (1, 1), (64, 7)])
+def test_ragged_image_sizes(oracle, size):
+    sc = I.uniform_scene(2000, 90 + size[0], scale_range=(0.01, 0.1))
+    cam = I.look_at((0, 0, -3), (0, 0, 0), (0, 1, 0), size[0], size[1], 60.0)
+    prm = I.RenderParams(head=8)
+    gpu = gpu_render(sc, [cam], prm)
+    ora = oracle.render(sc, cam, prm)
+    compare_view(gpu, 0, ora, min_decided=0.95, label=str(size))
+
+
+def test_empty_scene_gives_background():
+    sc = I.uniform_scene(0, 1)
+    cam = I.look_at((0, 0, -3), (0, 0, 0), (0, 1, 0), 48, 40, 60.0)
+    prm = I.RenderParams(bg=(0.25, 0.5, 0.75))
+    gpu = gpu_render(sc, [cam], prm)
+    assert np.allclose(gpu["rgb"][0], np.array([0.25, 0.5, 0.75], np.float32))
+    assert np.all(gpu["depth"][0] == 0) and np.all(gpu["tfinal"][0] == 1)
+    assert np.all(gpu["nblend"][0] == 0)
+
+
+def test_large_and_behind_camera_gaussians(oracle):
+    """Load balancing path (Gaussians covering hundreds of tiles), Gaussians behind the camera
+    and beside the frustum, background colour."""
+    rng = np.random.default_rng(5)
+    small = I.uniform_scene(3000, 91, scale_range=(0.005, 0.05))
+    big = I.uniform_scene(40, 92, scale_range=(0.3, 1.2), opacity_range=(0.05, 0.4))
+    behind = I.uniform_scene(50, 93)
+    behind.means[:, 2] = rng.uniform(-6, -3.2, 50)
+    sc = I.Scene(*(np.concatenate([getattr(s, k) for s in (small, big, behind)]) for k in
+                   ("means", "log_scales", "quats", "opacity_logits", "sh")), 0)
+    cam = I.look_at((0, 0, -3), (0, 0, 0), (0, 1, 0), 200, 160, 60.0)
+    prm = I.RenderParams(bg=(0.1, 0.2, 0.3))
+    gpu = gpu_render(sc, [cam], prm)
+    ora = oracle.render(sc, cam, prm)
+    compare_view(gpu, 0, ora, min_decided=0.97, label="big")
+    # the same with load balancing disabled and with a threshold of 1: identical results
+    for extra in (dict(flags=16), dict(lb_threshold=1)):
+        g2 = gpu_render(sc, [cam], dataclasses.replace(prm, **extra))
+        assert np.array_equal(g2["hash"][0], gpu["hash"][0])
+        assert np.array_equal(g2["rgb"][0], gpu["rgb"][0])
+
+
+def test_capacity_overflow_is_reported_and_recovered(oracle):
+    sc, cams, prm = I.plain_forward_workload()
+    g = R.scene_to_device(sc)
+    r = R.Renderer(sc.n, cams, prm, debug=True, capacity=1000)
+    rgb0, _, _ = r.forward(g, check=False)
+    st = r.status()
+    assert st.error_bits & 1 and st.num_entries > 1000 and st.capacity == 1000
+    with pytest.raises(N.CapacityError):
+        N.read_status(R._ptr(r.ws), torch.cuda.current_stream().cuda_stream)
+    rgb, depth, tf = r.forward(g)           # grows the workspace and re-renders
+    assert r.capacity >= st.num_entries
+    ref = gpu_render(sc, cams, prm)
+    assert np.array_equal(r.split(rgb)[0].cpu().numpy(), ref["rgb"][0])
+
+
+def test_batched_views_equal_single_views():
+    sc = I.cluster_scene(50000, 79, nclusters=8, centre_range=2.0, scale_range=(0.003, 0.1))
+    cams = I.orbit_cameras(4, 7.0, 1.0, [(320, 240), (200, 150), (160, 120), (96, 64)], 50.0)
+    prm = I.RenderParams()
+    batched = gpu_render(sc, cams, prm)
+    for k, cam in enumerate(cams):
+        single = gpu_render(sc, [cam], prm)
+        assert np.array_equal(batched["rgb"][k], single["rgb"][0])
+        assert np.array_equal(batched["depth"][k], single["depth"][0])
+        assert np.array_equal(batched["hash"][k], single["hash"][0])
+
+
+def test_sort_primitive_is_stable_and_exact():
+    rng = np.random.default_rng(9)
+    lib = N.lib()
+    for n, bits in [(1, 8), (1000, 12), (100_000, 45), (1_234_567, 41), (300_000, 64)]:
+        keys = rng.integers(0, 1 << min(bits, 62), n, dtype=np.int64).astype(np.uint64)
+        keys[rng.random(n) < 0.3] = keys[0]            # many equal keys: stability matters
+        if bits == 64:
+            keys[::7] |= np.uint64(1) << np.uint64(63)
+        vals = np.arange(n, dtype=np.uint32)
+        kd = torch.from_numpy(keys.view(np.int64)).cuda()
+        vd = torch.from_numpy(vals.view(np.int32)).cuda()
+        ko = torch.empty_like(kd)
+        vo = torch.empty_like(vd)
+        tb = lib.stp_sort_temp_bytes(n)
+        tmp = torch.empty(tb, dtype=torch.uint8, device="cuda")
+        N.check(lib.stp_sort_pairs(C.c_void_p(kd.data_ptr()), C.c_void_p(vd.data_ptr()), C.c_void_p(ko.data_ptr()),
+                                   C.c_void_p(vo.data_ptr()), n, None, bits, C.c_void_p(tmp.data_ptr()), tb,
+                                   C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+        torch.cuda.synchronize()
+        mask = np.uint64((1 << bits) - 1) if bits < 64 else np.uint64(0xFFFFFFFFFFFFFFFF)
+        order = np.argsort(keys & mask, kind="stable")
+        assert np.array_equal(vo.cpu().numpy().view(np.uint32), vals[order])
+        assert np.array_equal(ko.cpu().numpy().view(np.uint64), keys[order])
+        assert np.array_equal(kd.cpu().numpy().view(np.uint64), keys)      # input preserved
+
+
+def _tile_mask(cam, tiles):
+    m = np.zeros((cam.height, cam.width), bool)
+    for t in tiles:
+        tx, ty = t % cam.tiles_x, t // cam.tiles_x
+        m[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16] = True
+    return m
+
+
+def test_full_hd_3m_sampled_tiles_match_oracle(oracle):
+    """The 3M-Gaussian Full-HD workload in the launch configuration the bench times (16 views
+    in one batch), sampled: the oracle renders 40 random tiles of two views one by one."""
+    sc, cams, prm = I.full_hd_workload()
+    gpu = gpu_render(sc, cams, prm)
+    rng = np.random.default_rng(3)
+    for k in (0, 9):
+        tiles = rng.choice(cams[k].num_tiles, 40, replace=False)
+        with oracle.OracleRun(sc, cams[k], prm, tiles=tiles) as r:
+            ora = r.render()
+        frac = compare_view(gpu, k, ora, tiles_mask=_tile_mask(cams[k], tiles), min_decided=0.75,
+                            label="full hd view %d" % k)
+        print("view", k, "decided fraction in sampled tiles", frac)
+    st = gpu["renderer"].status()
+    assert st.error_bits == 0
+
+
+def test_backward_matches_oracle_adjoint(oracle):
+    """Sec. 4.5 backward against the FP64 adjoint on the 512-Gaussian 64x64 case. The loss
+    weights are zero on undecided pixels, so both sides differentiate the same blend order."""
+    sc, _, cam, prm = I.fd_subcase()
+    rng = np.random.default_rng(4)
+    with oracle.OracleRun(sc, cam, prm, record=True) as r:
+        ora = r.render()
+        w = rng.normal(size=(cam.height, cam.width, 3)) / cam.num_pixels
+        wz = rng.normal(size=(cam.height, cam.width)) / cam.num_pixels * 0.1
+        w[~ora["decided"]] = 0
+        wz[~ora["decided"]] = 0
+        adj = r.backward(w, wz)
+    g = R.scene_to_device(sc)
+    rr = R.Renderer(sc.n, [cam], prm, backward=True, debug=True)
+    rgb, depth, _ = rr.forward(g)
+    grads = {k: torch.zeros_like(g[k]) for k in R.FIELDS}
+    rr.backward(g, torch.from_numpy(w.reshape(-1, 3).astype(np.float32)).cuda(),
+                torch.from_numpy(wz.reshape(-1).astype(np.float32)).cuda(), grads)
+    torch.cuda.synchronize()
+    assert rr.status().error_bits == 0
+    for k in R.FIELDS:
+        a = grads[k].cpu().numpy().astype(np.float64).ravel()
+        b = adj[k].ravel()
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        cos = a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30)
+        print(k, "rel-L2 %.3g cos %.8f" % (rel, cos))
+        assert rel <= 1e-3 and cos >= 0.9999, k
