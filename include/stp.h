@@ -55,9 +55,12 @@ enum {
     STP_FLAG_VIEW_DEPTH_KEY = 8,     /* tile key = view-space depth of the mean (3DGS)       */
     STP_FLAG_NO_LOAD_BALANCE = 16,   /* every Gaussian processed by its own thread           */
     STP_FLAG_DEBUG_STATS = 32,       /* workspace also receives per-pixel blend count and hash */
-    STP_FLAG_BACKWARD = 64           /* workspace also holds the backward pass's scratch; the
+    STP_FLAG_BACKWARD = 64,          /* workspace also holds the backward pass's scratch; the
                                         forward and backward calls must both set it          */
+    STP_FLAG_DEBUG_TRACE = 128       /* workspace also receives, per pixel, the ids of the first
+                                        STP_TRACE_LEN blended Gaussians (-1 padded)          */
 };
+#define STP_TRACE_LEN 64
 
 typedef struct {
     const float* means;          /* [N,3] */
@@ -119,7 +122,7 @@ typedef struct {                 /* device status block, read back by stp_read_s
 typedef struct {                 /* byte offsets of workspace regions (for inspection)       */
     size_t status;               /* stp_run_status                                           */
     size_t views;                /* internal view table                                      */
-    size_t geom;                 /* [V*N] 64-byte render records (layout in stp_common.cuh)  */
+    size_t geom;                 /* [V*N] 96-byte render records (layout in stp_common.cuh)  */
     size_t color;                /* [V*N] float4 colours                                     */
     size_t rect;                 /* [V*N] ushort4 tile rectangles [x0, y0, x1, y1)           */
     size_t counts;               /* [V*N] uint32 entries per (view, Gaussian)                */
@@ -135,7 +138,8 @@ typedef struct {                 /* byte offsets of workspace regions (for inspe
     size_t scratch;              /* sort histogram scratch                                   */
     size_t dbg_nblend;           /* [total pixels] uint32 blends per pixel (flag 32), else 0 */
     size_t dbg_hash;             /* [total pixels] uint64 blend-order hash (flag 32), else 0 */
-    size_t grad_geom;            /* [V*N*20] float backward scratch (flag 64), else 0        */
+    size_t grad_geom;            /* [V*N*24] float backward scratch (flag 64), else 0        */
+    size_t dbg_trace;            /* [total pixels][STP_TRACE_LEN] int32 blend ids (flag 128)  */
     size_t total;                /* total bytes                                              */
     int64_t capacity;            /* sort-entry capacity                                      */
     int64_t total_tiles, total_pixels;

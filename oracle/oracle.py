@@ -92,10 +92,13 @@ def _ptr(a):
 
 
 def cam_struct(cam: Camera) -> _Cam:
+    """The camera as the renderer receives it: every value rounded to float32 (the C ABI's
+    camera is float32), then widened exactly to FP64, so both sides see the same camera."""
+    f32 = lambda v: float(np.float32(v))  # noqa: E731
     c = _Cam()
-    c.R[:] = [float(v) for v in np.asarray(cam.R, np.float64).reshape(9)]
-    c.t[:] = [float(v) for v in np.asarray(cam.t, np.float64).reshape(3)]
-    c.fx, c.fy, c.cx, c.cy = cam.fx, cam.fy, cam.cx, cam.cy
+    c.R[:] = [f32(v) for v in np.asarray(cam.R, np.float64).reshape(9)]
+    c.t[:] = [f32(v) for v in np.asarray(cam.t, np.float64).reshape(3)]
+    c.fx, c.fy, c.cx, c.cy = f32(cam.fx), f32(cam.fy), f32(cam.cx), f32(cam.cy)
     c.width, c.height = cam.width, cam.height
     return c
 

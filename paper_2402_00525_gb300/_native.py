@@ -18,6 +18,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libstp.so")
 STP_OK, STP_ERR_ARG, STP_ERR_CAPACITY, STP_ERR_TIMEOUT, STP_ERR_CUDA, STP_ERR_NOT_SUPPORTED = range(6)
 FLAG_DEBUG_STATS = 32
 FLAG_BACKWARD = 64
+FLAG_DEBUG_TRACE = 128
+TRACE_LEN = 64
 
 
 class StpError(RuntimeError):
@@ -64,7 +66,7 @@ class RunStatus(C.Structure):
 _LAYOUT_SIZE_FIELDS = ["status", "views", "geom", "color", "rect", "counts", "offsets",
                        "scan_partials", "keys", "vals", "keys_alt", "vals_alt", "sorted_keys",
                        "sorted_vals", "ranges", "tfinal", "pix_state", "scratch", "dbg_nblend",
-                       "dbg_hash", "grad_geom", "total"]
+                       "dbg_hash", "grad_geom", "dbg_trace", "total"]
 
 
 class Layout(C.Structure):

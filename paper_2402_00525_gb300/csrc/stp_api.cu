@@ -62,6 +62,7 @@ stp_status cuda_fail(cudaError_t e, const char* where)
 
 constexpr int kFlagDebug = 32;      // per-pixel blend count / hash written to the workspace
 constexpr int kFlagBackward = 64;   // workspace also holds the backward pass's scratch
+constexpr int kFlagTrace = 128;     // per-pixel ids of the first kTraceLen blended Gaussians
 
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -149,7 +150,7 @@ void make_plan(int64_t n, const stp_camera* cams, int32_t nviews, const stp_para
     auto take = [&](size_t bytes) { size_t r = o; o += al(bytes); return r; };
     L.status = take(sizeof(stp::Status));
     L.views = take(sizeof(stp::ViewDesc) * nviews);
-    L.geom = take((size_t)P.m * 64);
+    L.geom = take((size_t)P.m * 16 * stp::kRecFloat4);
     L.color = take((size_t)P.m * 16);
     L.rect = take((size_t)P.m * 8);
     L.counts = take((size_t)P.m * 4);
@@ -173,6 +174,8 @@ void make_plan(int64_t n, const stp_camera* cams, int32_t nviews, const stp_para
     L.sorted_vals = in_alt ? L.vals_alt : L.vals;
     L.grad_geom = 0;
     if (p->flags & kFlagBackward) L.grad_geom = take((size_t)P.m * stp::kGradStride * 4);
+    L.dbg_trace = 0;
+    if (p->flags & kFlagTrace) L.dbg_trace = take((size_t)pixels * stp::kTraceLen * 4);
     L.total = o;
 }
 
@@ -220,6 +223,7 @@ stp::PipeArgs make_args(const stp_gaussians* g, const stp_params* p, const Plan&
     a.sort_temp_bytes = stp::sort_hist_bytes();
     a.key_bits = L.key_bits;
     a.grad_geom = L.grad_geom ? (float*)(b + L.grad_geom) : nullptr;
+    a.dbg_trace = L.dbg_trace ? (int*)(b + L.dbg_trace) : nullptr;
     return a;
 }
 
@@ -302,6 +306,8 @@ stp_status stp_render(const stp_gaussians* g, const stp_camera* cams, int32_t nv
     if ((e = stp::pipeline_sort(a, s)) != cudaSuccess) return cuda_fail(e, "sort");
     prof_mark(5, s);
     if ((e = stp::launch_ranges(a, s)) != cudaSuccess) return cuda_fail(e, "ranges");
+    if (a.dbg_trace && (e = cudaMemsetAsync(a.dbg_trace, 0xFF, (size_t)a.total_pixels * stp::kTraceLen * 4, s)) != cudaSuccess)
+        return cuda_fail(e, "clear trace");
     prof_mark(6, s);
     if ((e = stp::launch_render(a, false, s)) != cudaSuccess) return cuda_fail(e, "render");
     prof_mark(7, s);

@@ -2,13 +2,13 @@
 //
 // StopThePop (arXiv 2402.00525) Sec. 4.5 keeps 3DGS's gradient flow: the backward Render
 // (stp_render.cu, BWD = true) accumulates per (view, Gaussian) the gradients of the 2D mean,
-// the conic, the opacity, the colour and -- when a depth gradient is given -- of the camera-
-// space depth coefficients (S, v) of the record; this kernel chains them back to the inputs:
+// the conic, the opacity, the colour and -- when a depth gradient is given -- of the depth
+// factors (m_k, c_k) of the record; this kernel chains them back to the inputs:
 //   colour  -> SH coefficients, and through the view direction -> mean
 //   opacity -> logit
 //   conic   -> Sigma2 -> (Sigma, J) -> (scale, rotation) and the camera-space mean -> mean
 //   mean2   -> camera-space mean -> mean
-//   S, v    -> Sigma^-1 (S^-1 clamp respected) and the camera-space mean
+//   m_k,c_k -> rotation, clamped inverse scales (S^-1 clamp respected), camera-space mean
 // One thread per Gaussian loops over the views of the launch and adds once into the caller's
 // gradient arrays, so gradients of several views of one scene need no atomics.
 #include <cuda_runtime.h>
@@ -72,25 +72,20 @@ __global__ void __launch_bounds__(128) k_backward_pre(PipeArgs a)
     const float Rq[3][3] = {{1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy)},
                             {2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx)},
                             {2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)}};
-    float sc[3], w[3];
+    float sc[3], si[3];
     bool unclamped[3];
     for (int k = 0; k < 3; k++) {
         const float ls = a.log_scales[3 * i + k];
         sc[k] = expf(ls);
-        const float si = expf(-ls);
-        unclamped[k] = si < a.inv_scale_max;
-        const float sic = fminf(si, a.inv_scale_max);
-        w[k] = sic * sic;
+        const float s_inv = expf(-ls);
+        unclamped[k] = s_inv < a.inv_scale_max;
+        si[k] = fminf(s_inv, a.inv_scale_max);
     }
-    float Sig[3][3], Sinv[3][3];
+    float Sig[3][3];
     for (int r = 0; r < 3; r++)
         for (int c = 0; c < 3; c++) {
             Sig[r][c] = 0.f;
-            Sinv[r][c] = 0.f;
-            for (int k = 0; k < 3; k++) {
-                Sig[r][c] += Rq[r][k] * sc[k] * sc[k] * Rq[c][k];
-                Sinv[r][c] += Rq[r][k] * w[k] * Rq[c][k];
-            }
+            for (int k = 0; k < 3; k++) Sig[r][c] += Rq[r][k] * sc[k] * sc[k] * Rq[c][k];
         }
     const float opac = 1.f / (1.f + expf(-a.logits[i]));
     const float* shc = a.sh + (long long)i * K * 3;
@@ -98,7 +93,7 @@ __global__ void __launch_bounds__(128) k_backward_pre(PipeArgs a)
     float dmu[3] = {0.f, 0.f, 0.f}, dls[3] = {0.f, 0.f, 0.f}, dlogit = 0.f;
     float dRq[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
     float dSig[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-    float dSinv[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    float dsi[3] = {0.f, 0.f, 0.f};
     float dsh[48];
     for (int k = 0; k < 48; k++) dsh[k] = 0.f;
     bool any = false;
@@ -106,11 +101,11 @@ __global__ void __launch_bounds__(128) k_backward_pre(PipeArgs a)
     for (int v = 0; v < a.nviews; v++) {
         const ViewDesc& V = a.views[v];
         const long long ri = V.rec_off + i;
-        if (a.geom[4 * ri + 1].y == 0.f) continue;      // invisible in this view
+        if (a.geom[kRecFloat4 * ri + 2].x == 0.f) continue;      // invisible in this view
         const float* gg = a.grad_geom + ri * kGradStride;
-        float g[18];
+        float g[21];
         bool nz = false;
-        for (int k = 0; k < 18; k++) {
+        for (int k = 0; k < 21; k++) {
             g[k] = gg[k];
             nz |= g[k] != 0.f;
         }
@@ -154,10 +149,19 @@ __global__ void __launch_bounds__(128) k_backward_pre(PipeArgs a)
         float TS[2][3];
         for (int r = 0; r < 2; r++)
             for (int c = 0; c < 3; c++) TS[r][c] = T[r][0] * Sig[0][c] + T[r][1] * Sig[1][c] + T[r][2] * Sig[2][c];
-        const float ca = TS[0][0] * T[0][0] + TS[0][1] * T[0][1] + TS[0][2] * T[0][2] + a.dilation;
-        const float cb = TS[0][0] * T[1][0] + TS[0][1] * T[1][1] + TS[0][2] * T[1][2];
-        const float cc = TS[1][0] * T[1][0] + TS[1][1] * T[1][1] + TS[1][2] * T[1][2] + a.dilation;
-        const float idet = 1.f / (ca * cc - cb * cb);
+        // Sigma2 = B B^T + dil I with B = T Rq diag(s); det from |b0 x b1|^2 (no cancellation)
+        float B[2][3];
+        for (int r = 0; r < 2; r++)
+            for (int k = 0; k < 3; k++) B[r][k] = (T[r][0] * Rq[0][k] + T[r][1] * Rq[1][k] + T[r][2] * Rq[2][k]) * sc[k];
+        const float n0 = B[0][0] * B[0][0] + B[0][1] * B[0][1] + B[0][2] * B[0][2];
+        const float n1 = B[1][0] * B[1][0] + B[1][1] * B[1][1] + B[1][2] * B[1][2];
+        const float cb = B[0][0] * B[1][0] + B[0][1] * B[1][1] + B[0][2] * B[1][2];
+        const float x0 = B[0][1] * B[1][2] - B[0][2] * B[1][1];
+        const float x1 = B[0][2] * B[1][0] - B[0][0] * B[1][2];
+        const float x2 = B[0][0] * B[1][1] - B[0][1] * B[1][0];
+        const float ca = n0 + a.dilation, cc = n1 + a.dilation;
+        const float det = (x0 * x0 + x1 * x1 + x2 * x2) + a.dilation * (n0 + n1) + a.dilation * a.dilation;
+        const float idet = 1.f / det;
         const float A[2][2] = {{cc * idet, -cb * idet}, {-cb * idet, ca * idet}};
         const float Ab[2][2] = {{g[2], 0.5f * g[3]}, {0.5f * g[3], g[4]}};
         float tmp[2][2], S2b[2][2];
@@ -188,25 +192,25 @@ __global__ void __launch_bounds__(128) k_backward_pre(PipeArgs a)
         dp[0] += g[0] * V.fx * iz;
         dp[1] += g[1] * V.fy * iz;
         dp[2] -= (g[0] * V.fx * p[0] + g[1] * V.fy * p[1]) * iz2;
-        // depth coefficients: S = R Sigma^-1 R^T (camera space), v = S p
-        if (g[9] != 0.f || g[10] != 0.f || g[11] != 0.f || g[12] != 0.f || g[13] != 0.f || g[14] != 0.f ||
-            g[15] != 0.f || g[16] != 0.f || g[17] != 0.f) {
-            float RS[3][3], S[3][3];
-            for (int r = 0; r < 3; r++)
-                for (int c = 0; c < 3; c++) RS[r][c] = V.R[3 * r] * Sinv[0][c] + V.R[3 * r + 1] * Sinv[1][c] + V.R[3 * r + 2] * Sinv[2][c];
-            for (int r = 0; r < 3; r++)
-                for (int c = 0; c < 3; c++) S[r][c] = RS[r][0] * V.R[3 * c] + RS[r][1] * V.R[3 * c + 1] + RS[r][2] * V.R[3 * c + 2];
-            float GS[3][3] = {{g[9], g[10], g[11]}, {g[10], g[12], g[13]}, {g[11], g[13], g[14]}};
-            const float gv[3] = {g[15], g[16], g[17]};
-            for (int r = 0; r < 3; r++)
-                for (int c = 0; c < 3; c++) GS[r][c] += gv[r] * p[c];
-            for (int r = 0; r < 3; r++) dp[r] += S[0][r] * gv[0] + S[1][r] * gv[1] + S[2][r] * gv[2];
-            // world Sigma^-1 gradient R^T GS R
-            float t1[3][3];
-            for (int r = 0; r < 3; r++)
-                for (int c = 0; c < 3; c++) t1[r][c] = V.R[r] * GS[0][c] + V.R[3 + r] * GS[1][c] + V.R[6 + r] * GS[2][c];
-            for (int r = 0; r < 3; r++)
-                for (int c = 0; c < 3; c++) dSinv[r][c] += t1[r][0] * V.R[c] + t1[r][1] * V.R[3 + c] + t1[r][2] * V.R[6 + c];
+        // depth factors: m_k = si_k R_c Rq e_k, c_k = m_k . p
+        bool depth_nz = false;
+        for (int k = 9; k < 21; k++) depth_nz |= g[k] != 0.f;
+        if (depth_nz) {
+            for (int k = 0; k < 3; k++) {
+                float mk[3];   // camera-space axis k (unscaled)
+                for (int r = 0; r < 3; r++) mk[r] = V.R[3 * r] * Rq[0][k] + V.R[3 * r + 1] * Rq[1][k] + V.R[3 * r + 2] * Rq[2][k];
+                const float dc = g[18 + k];
+                float dm[3];
+                for (int r = 0; r < 3; r++) {
+                    dp[r] += dc * si[k] * mk[r];
+                    dm[r] = g[9 + 3 * k + r] + dc * p[r];
+                }
+                // world-space gradient of the unscaled axis and of the scale factor
+                float gw[3];
+                for (int r = 0; r < 3; r++) gw[r] = V.R[r] * dm[0] + V.R[3 + r] * dm[1] + V.R[6 + r] * dm[2];
+                for (int r = 0; r < 3; r++) dRq[r][k] += si[k] * gw[r];
+                dsi[k] += Rq[0][k] * gw[0] + Rq[1][k] * gw[1] + Rq[2][k] * gw[2];
+            }
         }
         for (int k = 0; k < 3; k++) dmu[k] += V.R[k] * dp[0] + V.R[3 + k] * dp[1] + V.R[6 + k] * dp[2];
     }
@@ -219,19 +223,9 @@ __global__ void __launch_bounds__(128) k_backward_pre(PipeArgs a)
             dls[k] += mb * Rq[r][k] * sc[k];
             dRq[r][k] += mb * sc[k];
         }
-    // Sigma^-1 = Rq diag(w) Rq^T
-    for (int r = 0; r < 3; r++)
-        for (int k = 0; k < 3; k++) {
-            float s = 0.f;
-            for (int j = 0; j < 3; j++) s += (dSinv[r][j] + dSinv[j][r]) * Rq[j][k];
-            dRq[r][k] += s * w[k];
-        }
-    for (int k = 0; k < 3; k++) {
-        float dw = 0.f;
-        for (int r = 0; r < 3; r++)
-            for (int j = 0; j < 3; j++) dw += Rq[r][k] * dSinv[r][j] * Rq[j][k];
-        if (unclamped[k]) dls[k] += dw * (-2.f * w[k]);
-    }
+    // clamped inverse scales si_k = min(exp(-log s_k), inv_scale_max)
+    for (int k = 0; k < 3; k++)
+        if (unclamped[k]) dls[k] += dsi[k] * (-si[k]);
     // rotation -> normalised quaternion -> raw quaternion
     const float(*R)[3] = dRq;
     float gq[4];

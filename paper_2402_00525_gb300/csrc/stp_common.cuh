@@ -43,27 +43,42 @@ struct ViewDesc {
 };
 
 // ---------------------------------------------------------------- render record
-// 64-byte per-(view, Gaussian) record written by Preprocess:
-//   r0 = (mean2.x, mean2.y, A00, A01)       conic A = Sigma2^-1
-//   r1 = (A11, opacity, v.x, v.y)           v = S p (camera space, p = mean in camera space)
-//   r2 = (v.z, S00, 2 S01, 2 S02)           S = R_c Sigma^-1 R_c^T (camera space, clamped)
-//   r3 = (S11, 2 S12, S22, p.z)
-// so that t_opt on the ray through pixel-space point x is
-//   t(x) = |d| (v . d) / (d^T S d),  d = ((x - cx) / fx, (y - cy) / fy, 1)   (Eq. "dopt")
+// 96-byte per-(view, Gaussian) record written by Preprocess:
+//   r0 = (mean2.x hi, mean2.y hi, mean2.x lo, mean2.y lo)   mean2 = hi + lo (FP64 projection)
+//   r1 = (e.x, e.y, 1/lambda_max, 1/lambda_min)             conic A = Sigma2^-1 in eigen form
+//   r2 = (opacity, c0, c1, c2)
+//   r3 = (m0.x, m0.y, m0.z, m1.x)
+//   r4 = (m1.y, m1.z, m2.x, m2.y)
+//   r5 = (m2.z, p.z, 0, 0)
+// The conic is kept as its unit major axis e and inverse eigenvalues, so the 2D Mahalanobis
+// form q(D) = (e.D)^2 / lambda_max + (e_perp.D)^2 / lambda_min is a sum of non-negative terms,
+// and the mean as an unevaluated float pair, so D = x - mean2 keeps its relative accuracy:
+// both matter for the cull and alpha decisions of long, thin splats (aspect up to ~2000:1).
+// m_k = s_k^-1 (R_c R_q) e_k are the camera-space axes of the Gaussian scaled by the clamped
+// inverse scales (Sigma^-1 = R S^-1 S^-1 R^T, appendix A; S^-1 entries <= 1e3, Sec. 4.2) and
+// c_k = m_k . p with p the mean in camera space. For the ray through pixel-space point x,
+// d = ((x - cx) / fx, (y - cy) / fy, 1), a_k = m_k . d and (Eq. "dopt")
+//   t_opt(x) = |d| (sum_k a_k c_k) / (sum_k a_k^2),
+// again a sum of per-axis terms without cancellation between eigen-directions.
 struct Rec {
-    float4 r0, r1, r2, r3;
+    float4 r0, r1, r2, r3, r4, r5;
 };
+constexpr int kRecFloat4 = 6;
 
 __device__ __forceinline__ Rec load_rec(const float4* __restrict__ geom, long long i)
 {
     Rec r;
-    const float4* p = geom + 4 * i;
+    const float4* p = geom + kRecFloat4 * i;
     r.r0 = __ldg(p);
     r.r1 = __ldg(p + 1);
     r.r2 = __ldg(p + 2);
     r.r3 = __ldg(p + 3);
+    r.r4 = __ldg(p + 4);
+    r.r5 = __ldg(p + 5);
     return r;
 }
+
+__device__ __forceinline__ float rec_opacity(const Rec& r) { return r.r2.x; }
 
 // order-preserving map float -> uint32 (total order on non-NaN floats)
 __device__ __forceinline__ uint32_t fkey(float f)
@@ -77,54 +92,73 @@ __device__ __forceinline__ float fkey_inv(uint32_t k)
     return __uint_as_float(u);
 }
 
-// ---------------------------------------------------------------- Algorithm 1
-// Point of the box [x0,x1] x [y0,y1] where the 2D Gaussian (mx, my, conic a, b, c) is
-// largest: the mean if inside; else a clamped line search along the edge(s) leaving the
-// corner nearest to the mean (appendix B.1). Exactly one of the two searches can move off
-// the corner for a positive-definite conic.
-__device__ __forceinline__ float2 box_max_point(float mx, float my, float a, float b, float c,
-                                                float x0, float x1, float y0, float y1)
+// offset of pixel-space coordinate x from the mean, x - (hi + lo)
+__device__ __forceinline__ float off_x(const Rec& r, float x) { return __fsub_rn(__fsub_rn(x, r.r0.x), r.r0.z); }
+__device__ __forceinline__ float off_y(const Rec& r, float y) { return __fsub_rn(__fsub_rn(y, r.r0.y), r.r0.w); }
+
+// q(D) = D^T Sigma2^-1 D in the eigen form
+__device__ __forceinline__ float quad_form(const Rec& r, float dx, float dy)
 {
-    const bool inx = (mx >= x0) && (mx <= x1);
-    const bool iny = (my >= y0) && (my <= y1);
-    if (inx && iny) return make_float2(mx, my);
-    const float px = mx < x0 ? x0 : (mx > x1 ? x1 : (__fsub_rn(mx, x0) <= __fsub_rn(x1, mx) ? x0 : x1));
-    const float py = my < y0 ? y0 : (my > y1 ? y1 : (__fsub_rn(my, y0) <= __fsub_rn(y1, my) ? y0 : y1));
-    const float ex = __fsub_rn(px == x0 ? x1 : x0, px);   // edge vector along x
-    const float ey = __fsub_rn(py == y0 ? y1 : y0, py);   // edge vector along y
-    const float dx = __fsub_rn(mx, px), dy = __fsub_rn(my, py);
-    float tx = 0.f, ty = 0.f;
-    if (!inx) {     // search along the y-edge x = px
-        const float num = __fmul_rn(ey, __fmaf_rn(b, dx, __fmul_rn(c, dy)));
-        const float den = __fmul_rn(__fmul_rn(ey, ey), c);
-        ty = den > 0.f ? fminf(1.f, fmaxf(0.f, __fdiv_rn(num, den))) : 0.f;
-    }
-    if (!iny) {     // search along the x-edge y = py
-        const float num = __fmul_rn(ex, __fmaf_rn(a, dx, __fmul_rn(b, dy)));
-        const float den = __fmul_rn(__fmul_rn(ex, ex), a);
-        tx = den > 0.f ? fminf(1.f, fmaxf(0.f, __fdiv_rn(num, den))) : 0.f;
-    }
-    return make_float2(__fmaf_rn(tx, ex, px), __fmaf_rn(ty, ey, py));
+    const float pe = __fmaf_rn(r.r1.x, dx, __fmul_rn(r.r1.y, dy));
+    const float pp = __fmaf_rn(r.r1.x, dy, -__fmul_rn(r.r1.y, dx));
+    return __fmaf_rn(r.r1.z, __fmul_rn(pe, pe), __fmul_rn(r.r1.w, __fmul_rn(pp, pp)));
 }
 
-// opacity * G2(x) (Sec. 3.1: alpha = opacity times the 2D splat)
+// opacity * G2 at offset D (Sec. 3.1: alpha = opacity times the 2D splat)
+__device__ __forceinline__ float splat_at(const Rec& r, float dx, float dy)
+{
+    return __fmul_rn(rec_opacity(r), expf(__fmul_rn(-0.5f, quad_form(r, dx, dy))));
+}
 __device__ __forceinline__ float splat_value(const Rec& r, float x, float y)
 {
-    const float dx = __fsub_rn(x, r.r0.x), dy = __fsub_rn(y, r.r0.y);
-    const float q = __fmaf_rn(r.r0.z, __fmul_rn(dx, dx),
-                              __fmaf_rn(r.r1.x, __fmul_rn(dy, dy),
-                                        __fmul_rn(2.f, __fmul_rn(r.r0.w, __fmul_rn(dx, dy)))));
-    return __fmul_rn(r.r1.y, expf(__fmul_rn(-0.5f, q)));
+    return splat_at(r, off_x(r, x), off_y(r, y));
+}
+
+// ---------------------------------------------------------------- Algorithm 1
+// Point of the box [x0,x1] x [y0,y1] where the 2D Gaussian is largest (appendix B.1): the
+// mean if inside; otherwise a clamped line search along the edge(s) leaving the corner nearest
+// to the mean (exactly one of the two searches can move off the corner for a positive-definite
+// conic). Computed in mean-relative coordinates; returns the offset D = x_hat - mean2.
+__device__ __forceinline__ float2 box_max_offset(const Rec& r, float x0, float x1, float y0, float y1)
+{
+    const float bx0 = off_x(r, x0), bx1 = off_x(r, x1), by0 = off_y(r, y0), by1 = off_y(r, y1);
+    const bool inx = (bx0 <= 0.f) && (bx1 >= 0.f);
+    const bool iny = (by0 <= 0.f) && (by1 >= 0.f);
+    if (inx && iny) return make_float2(0.f, 0.f);
+    const float px = bx0 > 0.f ? bx0 : (bx1 < 0.f ? bx1 : (-bx0 <= bx1 ? bx0 : bx1));
+    const float py = by0 > 0.f ? by0 : (by1 < 0.f ? by1 : (-by0 <= by1 ? by0 : by1));
+    const float ex = __fsub_rn(px == bx0 ? bx1 : bx0, px);   // edge vector along x
+    const float ey = __fsub_rn(py == by0 ? by1 : by0, py);   // edge vector along y
+    // A p_hat with A = Sigma2^-1 in eigen form
+    const float pe = __fmaf_rn(r.r1.x, px, __fmul_rn(r.r1.y, py));
+    const float pp = __fmaf_rn(r.r1.x, py, -__fmul_rn(r.r1.y, px));
+    const float se = __fmul_rn(r.r1.z, pe), sp = __fmul_rn(r.r1.w, pp);
+    const float Apx = __fmaf_rn(se, r.r1.x, -__fmul_rn(sp, r.r1.y));
+    const float Apy = __fmaf_rn(se, r.r1.y, __fmul_rn(sp, r.r1.x));
+    float tx = 0.f, ty = 0.f;
+    if (!inx) {     // search along the y-edge x = px: minimise q(p + t (0, ey))
+        const float Ayy = __fmaf_rn(r.r1.z, __fmul_rn(r.r1.y, r.r1.y), __fmul_rn(r.r1.w, __fmul_rn(r.r1.x, r.r1.x)));
+        const float den = __fmul_rn(ey, Ayy);
+        ty = den != 0.f ? fminf(1.f, fmaxf(0.f, __fdiv_rn(-Apy, den))) : 0.f;
+    }
+    if (!iny) {     // search along the x-edge y = py
+        const float Axx = __fmaf_rn(r.r1.z, __fmul_rn(r.r1.x, r.r1.x), __fmul_rn(r.r1.w, __fmul_rn(r.r1.y, r.r1.y)));
+        const float den = __fmul_rn(ex, Axx);
+        tx = den != 0.f ? fminf(1.f, fmaxf(0.f, __fdiv_rn(-Apx, den))) : 0.f;
+    }
+    return make_float2(__fmaf_rn(tx, ex, px), __fmaf_rn(ty, ey, py));
 }
 
 // t_opt on the ray through camera-normalised coordinates (u, w) = ((x-cx)/fx, (y-cy)/fy)
 __device__ __forceinline__ float depth_uv(const Rec& r, float u, float w)
 {
-    const float L = __fmaf_rn(r.r1.z, u, __fmaf_rn(r.r1.w, w, r.r2.x));
-    const float Q = __fmaf_rn(u, __fmaf_rn(r.r2.y, u, __fmaf_rn(r.r2.z, w, r.r2.w)),
-                              __fmaf_rn(w, __fmaf_rn(r.r3.x, w, r.r3.y), r.r3.z));
+    const float a0 = __fmaf_rn(r.r3.x, u, __fmaf_rn(r.r3.y, w, r.r3.z));
+    const float a1 = __fmaf_rn(r.r3.w, u, __fmaf_rn(r.r4.x, w, r.r4.y));
+    const float a2 = __fmaf_rn(r.r4.z, u, __fmaf_rn(r.r4.w, w, r.r5.x));
+    const float num = __fmaf_rn(a0, r.r2.y, __fmaf_rn(a1, r.r2.z, __fmul_rn(a2, r.r2.w)));
+    const float den = __fmaf_rn(a0, a0, __fmaf_rn(a1, a1, __fmul_rn(a2, a2)));
     const float n = __fsqrt_rn(__fmaf_rn(u, u, __fmaf_rn(w, w, 1.f)));
-    return __fmul_rn(n, __fdiv_rn(L, Q));
+    return __fmul_rn(n, __fdiv_rn(num, den));
 }
 
 __device__ __forceinline__ float to_u(const ViewDesc& V, float x) { return __fmul_rn(__fsub_rn(x, V.cx), V.ifx); }
@@ -142,16 +176,16 @@ __device__ __forceinline__ Box block_box(int ox, int oy, int s, int W, int H)
 // ray through the box's x_hat ("Tile-depth adjustment"); centre_ray selects the box centre.
 __device__ __forceinline__ bool box_keep(const Rec& r, const Box& b, float eps_o)
 {
-    const float2 xh = box_max_point(r.r0.x, r.r0.y, r.r0.z, r.r0.w, r.r1.x, b.x0, b.x1, b.y0, b.y1);
-    return splat_value(r, xh.x, xh.y) >= eps_o;
+    const float2 d = box_max_offset(r, b.x0, b.x1, b.y0, b.y1);
+    return splat_at(r, d.x, d.y) >= eps_o;
 }
 __device__ __forceinline__ bool box_keep_depth(const Rec& r, const Box& b, const ViewDesc& V,
                                                float eps_o, bool centre_ray, float* t)
 {
-    const float2 xh = box_max_point(r.r0.x, r.r0.y, r.r0.z, r.r0.w, r.r1.x, b.x0, b.x1, b.y0, b.y1);
-    if (!(splat_value(r, xh.x, xh.y) >= eps_o)) return false;
-    const float x = centre_ray ? __fmul_rn(0.5f, __fadd_rn(b.x0, b.x1)) : xh.x;
-    const float y = centre_ray ? __fmul_rn(0.5f, __fadd_rn(b.y0, b.y1)) : xh.y;
+    const float2 d = box_max_offset(r, b.x0, b.x1, b.y0, b.y1);
+    if (!(splat_at(r, d.x, d.y) >= eps_o)) return false;
+    const float x = centre_ray ? __fmul_rn(0.5f, __fadd_rn(b.x0, b.x1)) : __fadd_rn(r.r0.x, __fadd_rn(r.r0.z, d.x));
+    const float y = centre_ray ? __fmul_rn(0.5f, __fadd_rn(b.y0, b.y1)) : __fadd_rn(r.r0.y, __fadd_rn(r.r0.w, d.y));
     *t = depth_uv(r, to_u(V, x), to_w(V, y));
     return true;
 }

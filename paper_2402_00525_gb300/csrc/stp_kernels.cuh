@@ -24,7 +24,7 @@ struct PipeArgs {
     // workspace regions
     const ViewDesc* views;
     Status* status;
-    float4* geom;            // [V*N*4]
+    float4* geom;            // [V*N*kRecFloat4]
     float4* color;           // [V*N]
     ushort4* rect;           // [V*N]
     uint32_t* counts;        // [V*N]
@@ -44,6 +44,7 @@ struct PipeArgs {
     float* pix_state;        // [total_pixels] float4 (C without background, depth)
     uint32_t* dbg_nblend;    // [total_pixels] or null
     unsigned long long* dbg_hash;   // [total_pixels] or null
+    int* dbg_trace;          // [total_pixels][kTraceLen] or null
     void* sort_temp;
     size_t sort_temp_bytes;
     int key_bits;
@@ -62,7 +63,8 @@ struct PipeArgs {
     float* g_sh;
 };
 
-constexpr int kGradStride = 20;   // dmean2(2) dconic(3) dopacity(1) dcolor(3) dS(6) dv(3) pad(2)
+constexpr int kTraceLen = 64;
+constexpr int kGradStride = 24;   // dmean2(2) dconic(3) dopacity(1) dcolor(3) dm(9) dc(3) pad(3)
 
 cudaError_t launch_views_init(const ViewDesc* host_views, int nviews, ViewDesc* dev_views,
                               cudaStream_t s);

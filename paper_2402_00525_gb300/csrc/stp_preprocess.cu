@@ -62,8 +62,9 @@ __device__ __forceinline__ void sh_colour(const float* __restrict__ c, int K, fl
 
 struct GaussIn {             // view-independent quantities of one Gaussian
     float mu[3];
-    float sig[6];            // Sigma   (xx, xy, xz, yy, yz, zz)
-    float sinv[6];           // Sigma^-1 with the S^-1 clamp
+    float s[3];              // scales
+    float Rq[9];             // rotation of the normalised quaternion (row major)
+    float si[3];             // clamped inverse scales min(1/s, inv_scale_max)
     float opacity;
 };
 
@@ -79,42 +80,38 @@ __device__ __forceinline__ void load_gauss(const PipeArgs& a, int i, GaussIn& g)
     const float R[9] = {1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy),
                         2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx),
                         2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)};
-    float s2[3], w[3];
     for (int k = 0; k < 3; k++) {
         const float ls = __ldg(a.log_scales + 3 * i + k);
-        s2[k] = expf(2.f * ls);
-        const float si = fminf(expf(-ls), a.inv_scale_max);
-        w[k] = si * si;
+        g.s[k] = expf(ls);
+        g.si[k] = fminf(expf(-ls), a.inv_scale_max);
     }
-    const int id[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
-    for (int e = 0; e < 6; e++) {
-        const int r = id[e][0], c = id[e][1];
-        g.sig[e] = R[3 * r] * s2[0] * R[3 * c] + R[3 * r + 1] * s2[1] * R[3 * c + 1] + R[3 * r + 2] * s2[2] * R[3 * c + 2];
-        g.sinv[e] = R[3 * r] * w[0] * R[3 * c] + R[3 * r + 1] * w[1] * R[3 * c + 1] + R[3 * r + 2] * w[2] * R[3 * c + 2];
-    }
+    for (int k = 0; k < 9; k++) g.Rq[k] = R[k];
     g.opacity = 1.f / (1.f + expf(-__ldg(a.logits + i)));
 }
 
-__device__ __forceinline__ float sym(const float* s, int r, int c)
-{
-    const int idx[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
-    return s[idx[r][c]];
-}
-
 // Per-(view, Gaussian) record (layout in stp_common.cuh). Returns false if invisible.
+// The camera-space mean and its projection are evaluated in FP64 (a handful of operations per
+// Gaussian and view): mean2 is ~1e3 px, where an FP32 rounding of 6e-5 px would move the alpha
+// of a sub-pixel-wide splat by ~1e-3 relative. Sigma2 = B B^T + dilation I with B = T M
+// (M = R_q diag(s), Sigma = M M^T), so det Sigma2 = |b0 x b1|^2 + dil (|b0|^2 + |b1|^2) + dil^2
+// is a sum of non-negative terms instead of the cancelling a c - b^2.
 __device__ bool make_record(const PipeArgs& a, const ViewDesc& V, const GaussIn& g, int i,
                             Rec& rec, float4& col, ushort4& rect)
 {
     rect = make_ushort4(0, 0, 0, 0);
-    rec.r0 = rec.r1 = rec.r2 = rec.r3 = make_float4(0.f, 0.f, 0.f, 0.f);
+    rec.r0 = rec.r1 = rec.r2 = rec.r3 = rec.r4 = rec.r5 = make_float4(0.f, 0.f, 0.f, 0.f);
     col = make_float4(0.f, 0.f, 0.f, 0.f);
-    float p[3];
+    double pd[3];
     for (int k = 0; k < 3; k++)
-        p[k] = V.R[3 * k] * g.mu[0] + V.R[3 * k + 1] * g.mu[1] + V.R[3 * k + 2] * g.mu[2] + V.t[k];
-    if (!(p[2] > a.znear)) return false;
+        pd[k] = (double)V.R[3 * k] * g.mu[0] + (double)V.R[3 * k + 1] * g.mu[1] + (double)V.R[3 * k + 2] * g.mu[2] +
+                (double)V.t[k];
+    if (!(pd[2] > (double)a.znear)) return false;
     if (!(g.opacity >= a.eps_o)) return false;
+    const double uxd = pd[0] / pd[2], uyd = pd[1] / pd[2];
+    const double mxd = (double)V.fx * uxd + (double)V.cx, myd = (double)V.fy * uyd + (double)V.cy;
+    const float p[3] = {(float)pd[0], (float)pd[1], (float)pd[2]};
     const float iz = 1.f / p[2];
-    const float ux = p[0] * iz, uy = p[1] * iz;
+    const float ux = (float)uxd, uy = (float)uyd;
     const float cx = fminf(V.limx, fmaxf(-V.limx, ux)), cy = fminf(V.limy, fmaxf(-V.limy, uy));
     const float J00 = V.fx * iz, J02 = -V.fx * cx * iz, J11 = V.fy * iz, J12 = -V.fy * cy * iz;
     float T[2][3];
@@ -122,32 +119,52 @@ __device__ bool make_record(const PipeArgs& a, const ViewDesc& V, const GaussIn&
         T[0][c] = J00 * V.R[c] + J02 * V.R[6 + c];
         T[1][c] = J11 * V.R[3 + c] + J12 * V.R[6 + c];
     }
-    float M[2][3];
+    // B = T R_q diag(s): rows b0, b1
+    float B[2][3];
     for (int r = 0; r < 2; r++)
-        for (int c = 0; c < 3; c++)
-            M[r][c] = T[r][0] * sym(g.sig, 0, c) + T[r][1] * sym(g.sig, 1, c) + T[r][2] * sym(g.sig, 2, c);
-    const float ca = M[0][0] * T[0][0] + M[0][1] * T[0][1] + M[0][2] * T[0][2] + a.dilation;
-    const float cb = M[0][0] * T[1][0] + M[0][1] * T[1][1] + M[0][2] * T[1][2];
-    const float cc = M[1][0] * T[1][0] + M[1][1] * T[1][1] + M[1][2] * T[1][2] + a.dilation;
-    const float det = ca * cc - cb * cb;
+        for (int k = 0; k < 3; k++)
+            B[r][k] = (T[r][0] * g.Rq[k] + T[r][1] * g.Rq[3 + k] + T[r][2] * g.Rq[6 + k]) * g.s[k];
+    const float n0 = B[0][0] * B[0][0] + B[0][1] * B[0][1] + B[0][2] * B[0][2];
+    const float n1 = B[1][0] * B[1][0] + B[1][1] * B[1][1] + B[1][2] * B[1][2];
+    const float cb = B[0][0] * B[1][0] + B[0][1] * B[1][1] + B[0][2] * B[1][2];
+    const float x0 = B[0][1] * B[1][2] - B[0][2] * B[1][1];
+    const float x1 = B[0][2] * B[1][0] - B[0][0] * B[1][2];
+    const float x2 = B[0][0] * B[1][1] - B[0][1] * B[1][0];
+    const float dil = a.dilation;
+    const float ca = n0 + dil, cc = n1 + dil;
+    const float det = (x0 * x0 + x1 * x1 + x2 * x2) + dil * (n0 + n1) + dil * dil;
     if (!(det > 0.f)) return false;
-    const float idet = 1.f / det;
-    const float mx = V.fx * ux + V.cx, my = V.fy * uy + V.cy;
-    // camera-space Sigma^-1 and v = S p
-    float RS[3][3];
-    for (int r = 0; r < 3; r++)
-        for (int c = 0; c < 3; c++)
-            RS[r][c] = V.R[3 * r] * sym(g.sinv, 0, c) + V.R[3 * r + 1] * sym(g.sinv, 1, c) + V.R[3 * r + 2] * sym(g.sinv, 2, c);
-    float S[3][3];
-    for (int r = 0; r < 3; r++)
-        for (int c = 0; c < 3; c++)
-            S[r][c] = RS[r][0] * V.R[3 * c] + RS[r][1] * V.R[3 * c + 1] + RS[r][2] * V.R[3 * c + 2];
-    float v[3];
-    for (int r = 0; r < 3; r++) v[r] = S[r][0] * p[0] + S[r][1] * p[1] + S[r][2] * p[2];
-    rec.r0 = make_float4(mx, my, cc * idet, -cb * idet);
-    rec.r1 = make_float4(ca * idet, g.opacity, v[0], v[1]);
-    rec.r2 = make_float4(v[2], S[0][0], 2.f * S[0][1], 2.f * S[0][2]);
-    rec.r3 = make_float4(S[1][1], 2.f * S[1][2], S[2][2], p[2]);
+    // eigen form of Sigma2: lambda_max = mean + sqrt(half-difference^2 + b^2), lambda_min = det/lambda_max
+    const float hd = 0.5f * (ca - cc);
+    const float lmax = 0.5f * (ca + cc) + sqrtf(hd * hd + cb * cb);
+    const float lmin = det / lmax;
+    float ex = cb, ey = lmax - ca;                 // (Sigma2 - lmax I) v = 0
+    const float fx2 = lmax - cc, fy2 = cb;
+    if (fx2 * fx2 + fy2 * fy2 > ex * ex + ey * ey) { ex = fx2; ey = fy2; }
+    const float en = ex * ex + ey * ey;
+    if (en > 0.f) {
+        const float inv = rsqrtf(en);
+        ex *= inv;
+        ey *= inv;
+    } else {
+        ex = 1.f;
+        ey = 0.f;
+    }
+    const float mx_hi = (float)mxd, my_hi = (float)myd;
+    const float mx_lo = (float)(mxd - (double)mx_hi), my_lo = (float)(myd - (double)my_hi);
+    // camera-space axes scaled by the clamped inverse scales, and their projections of p
+    float m[3][3], c[3];
+    for (int k = 0; k < 3; k++) {
+        for (int r = 0; r < 3; r++)
+            m[k][r] = g.si[k] * (V.R[3 * r] * g.Rq[k] + V.R[3 * r + 1] * g.Rq[3 + k] + V.R[3 * r + 2] * g.Rq[6 + k]);
+        c[k] = (float)((double)m[k][0] * pd[0] + (double)m[k][1] * pd[1] + (double)m[k][2] * pd[2]);
+    }
+    rec.r0 = make_float4(mx_hi, my_hi, mx_lo, my_lo);
+    rec.r1 = make_float4(ex, ey, 1.f / lmax, 1.f / lmin);
+    rec.r2 = make_float4(g.opacity, c[0], c[1], c[2]);
+    rec.r3 = make_float4(m[0][0], m[0][1], m[0][2], m[1][0]);
+    rec.r4 = make_float4(m[1][1], m[1][2], m[2][0], m[2][1]);
+    rec.r5 = make_float4(m[2][2], p[2], 0.f, 0.f);
     // colour: SH with the direction from the camera centre to the mean
     float d[3] = {g.mu[0] - V.o[0], g.mu[1] - V.o[1], g.mu[2] - V.o[2]};
     const float dl = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
@@ -157,11 +174,10 @@ __device__ bool make_record(const PipeArgs& a, const ViewDesc& V, const GaussIn&
     // opacity-aware radius (appendix B.2) and the rectangle of tiles holding a pixel centre
     // within [mean2 - r, mean2 + r]
     const float tO = sqrtf(2.f * logf(g.opacity / a.eps_o));
-    const float mid = 0.5f * (ca + cc);
-    const float lam = mid + sqrtf(fmaxf(0.f, mid * mid - det));
-    const float r = ceilf(tO * sqrtf(lam));
-    const float fx0 = ceilf((mx - r - 15.5f) * (1.f / 16.f)), fx1 = floorf((mx + r - 0.5f) * (1.f / 16.f));
-    const float fy0 = ceilf((my - r - 15.5f) * (1.f / 16.f)), fy1 = floorf((my + r - 0.5f) * (1.f / 16.f));
+    const float rad = ceilf(tO * sqrtf(lmax));
+    const float mx = (float)mxd, my = (float)myd;
+    const float fx0 = ceilf((mx - rad - 15.5f) * (1.f / 16.f)), fx1 = floorf((mx + rad - 0.5f) * (1.f / 16.f));
+    const float fy0 = ceilf((my - rad - 15.5f) * (1.f / 16.f)), fy1 = floorf((my + rad - 0.5f) * (1.f / 16.f));
     const int tx0 = (int)fmaxf(0.f, fx0), ty0 = (int)fmaxf(0.f, fy0);
     const int tx1 = (int)fminf((float)(V.tiles_x - 1), fx1), ty1 = (int)fminf((float)(V.tiles_y - 1), fy1);
     if (tx1 >= tx0 && ty1 >= ty0)
@@ -181,6 +197,9 @@ __device__ __forceinline__ Rec shfl_rec(const Rec& r, int src)
                        __shfl_sync(kFull, r.r2.z, src), __shfl_sync(kFull, r.r2.w, src));
     o.r3 = make_float4(__shfl_sync(kFull, r.r3.x, src), __shfl_sync(kFull, r.r3.y, src),
                        __shfl_sync(kFull, r.r3.z, src), __shfl_sync(kFull, r.r3.w, src));
+    o.r4 = make_float4(__shfl_sync(kFull, r.r4.x, src), __shfl_sync(kFull, r.r4.y, src),
+                       __shfl_sync(kFull, r.r4.z, src), __shfl_sync(kFull, r.r4.w, src));
+    o.r5 = make_float4(__shfl_sync(kFull, r.r5.x, src), __shfl_sync(kFull, r.r5.y, src), 0.f, 0.f);
     return o;
 }
 
@@ -191,7 +210,7 @@ __device__ __forceinline__ bool tile_key(const PipeArgs& a, const ViewDesc& V, c
     const Box b = block_box(tx * kTile, ty * kTile, kTile, V.W, V.H);
     float t = 0.f;
     if (!box_keep_depth(r, b, V, a.eps_o, (a.flags & 4) != 0, &t)) return false;
-    if (a.flags & 8) t = r.r3.w;
+    if (a.flags & 8) t = r.r5.y;
     *key = ((unsigned long long)(V.tile_off + ty * V.tiles_x + tx) << 32) | fkey(t);
     return true;
 }
@@ -268,12 +287,12 @@ __global__ void __launch_bounds__(256) k_preprocess(PipeArgs a)
         ushort4 rc = make_ushort4(0, 0, 0, 0);
         bool vis = false;
         if (live) vis = make_record(a, V, g, i, r, col, rc);
-        else r.r0 = r.r1 = r.r2 = r.r3 = make_float4(0.f, 0.f, 0.f, 0.f);
+        else r.r0 = r.r1 = r.r2 = r.r3 = r.r4 = r.r5 = make_float4(0.f, 0.f, 0.f, 0.f);
         const uint32_t cnt = tiles_pass<false>(a, V, vis, r, rc, 0, 0, 0);
         if (live) {
             const long long o = V.rec_off + i;
-            float4* gp = a.geom + 4 * o;
-            gp[0] = r.r0; gp[1] = r.r1; gp[2] = r.r2; gp[3] = r.r3;
+            float4* gp = a.geom + kRecFloat4 * o;
+            gp[0] = r.r0; gp[1] = r.r1; gp[2] = r.r2; gp[3] = r.r3; gp[4] = r.r4; gp[5] = r.r5;
             a.color[o] = col;
             a.rect[o] = rc;
             a.counts[o] = cnt;
@@ -297,7 +316,7 @@ __global__ void __launch_bounds__(256) k_duplicate(PipeArgs a)
             off = a.offsets[o];
             want = a.counts[o];
         } else {
-            r.r0 = r.r1 = r.r2 = r.r3 = make_float4(0.f, 0.f, 0.f, 0.f);
+            r.r0 = r.r1 = r.r2 = r.r3 = r.r4 = r.r5 = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         const uint32_t got = tiles_pass<true>(a, V, live && want > 0, r, rc, off, want, (uint32_t)i);
         if (live && got != want) {

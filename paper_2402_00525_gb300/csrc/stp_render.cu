@@ -97,37 +97,42 @@ __device__ __forceinline__ void blend(const PipeArgs& a, const ViewDesc& V, Px<H
         da += c.gz * (t * s.T - (c.Zf - s.Z) * inv);
         const Rec r = load_rec(a.geom, ri);
         if (val < a.alpha_max) {
-            const float dx = c.xc - r.r0.x, dy = c.yc - r.r0.y;
-            const float o = r.r1.y;
-            const float G = expf(-0.5f * (r.r0.z * dx * dx + 2.f * r.r0.w * dx * dy + r.r1.x * dy * dy));
+            const float dx = off_x(r, c.xc), dy = off_y(r, c.yc);
+            const float o = rec_opacity(r);
+            const float G = expf(-0.5f * quad_form(r, dx, dy));
+            // conic entries (A00, A01, A11) from the eigen form
+            const float ex = r.r1.x, ey = r.r1.y, l0 = r.r1.z, l1 = r.r1.w;
+            const float A00 = l0 * ex * ex + l1 * ey * ey, A01 = (l0 - l1) * ex * ey, A11 = l0 * ey * ey + l1 * ex * ex;
             atomicAdd(gg + 5, da * G);
             const float dGG = da * o * G;
             atomicAdd(gg + 2, dGG * (-0.5f * dx * dx));
             atomicAdd(gg + 3, dGG * (-dx * dy));
             atomicAdd(gg + 4, dGG * (-0.5f * dy * dy));
-            atomicAdd(gg + 0, dGG * (r.r0.z * dx + r.r0.w * dy));
-            atomicAdd(gg + 1, dGG * (r.r0.w * dx + r.r1.x * dy));
+            atomicAdd(gg + 0, dGG * (A00 * dx + A01 * dy));
+            atomicAdd(gg + 1, dGG * (A01 * dx + A11 * dy));
         }
         if (c.gz != 0.f) {
-            // t = |d| L / Q with L = v . d, Q = d^T S d, d = (u, w, 1) (record layout)
+            // t = |d| N / D with a_k = m_k . d, N = sum a_k c_k, D = sum a_k^2 (record layout)
             const float u = c.u, w = c.w;
-            const float L = r.r1.z * u + r.r1.w * w + r.r2.x;
-            const float Q = r.r2.y * u * u + r.r2.z * u * w + r.r2.w * u + r.r3.x * w * w + r.r3.y * w + r.r3.z;
+            const float m[3][3] = {{r.r3.x, r.r3.y, r.r3.z}, {r.r3.w, r.r4.x, r.r4.y}, {r.r4.z, r.r4.w, r.r5.x}};
+            const float cc[3] = {r.r2.y, r.r2.z, r.r2.w};
+            float ak[3];
+            for (int k = 0; k < 3; k++) ak[k] = m[k][0] * u + m[k][1] * w + m[k][2];
+            const float num = ak[0] * cc[0] + ak[1] * cc[1] + ak[2] * cc[2];
+            const float den = ak[0] * ak[0] + ak[1] * ak[1] + ak[2] * ak[2];
             const float n = sqrtf(u * u + w * w + 1.f);
             const float dt = c.gz * wgt;
-            const float fv = dt * n / Q;                   // dt/dv = |d| d / Q
-            const float fs = -dt * n * L / (Q * Q);        // dt/d(coeff) = -|d| L / Q^2 * monomial
-            atomicAdd(gg + 9, fs * u * u);
-            atomicAdd(gg + 10, fs * u * w);
-            atomicAdd(gg + 11, fs * u);
-            atomicAdd(gg + 12, fs * w * w);
-            atomicAdd(gg + 13, fs * w);
-            atomicAdd(gg + 14, fs);
-            atomicAdd(gg + 15, fv * u);
-            atomicAdd(gg + 16, fv * w);
-            atomicAdd(gg + 17, fv);
+            const float tq = num / den;
+            for (int k = 0; k < 3; k++) {
+                const float da_k = dt * n * (cc[k] - 2.f * tq * ak[k]) / den;   // dt/da_k
+                atomicAdd(gg + 9 + 3 * k, da_k * u);
+                atomicAdd(gg + 10 + 3 * k, da_k * w);
+                atomicAdd(gg + 11 + 3 * k, da_k);
+                atomicAdd(gg + 18 + k, dt * n * ak[k] / den);                    // dt/dc_k
+            }
         }
     }
+    if (!BWD && a.dbg_trace && s.nbl < (uint32_t)kTraceLen) a.dbg_trace[c.pix * kTraceLen + s.nbl] = (int)id;
     s.T = Tn;
     s.nbl++;
     s.hash = s.hash * kHashMul + (unsigned long long)(id + 1u);

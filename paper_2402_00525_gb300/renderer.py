@@ -53,12 +53,13 @@ class Renderer:
 
     def __init__(self, n: int, cams: Sequence[Camera], prm: RenderParams, device="cuda",
                  backward: bool = False, debug: bool = False, capacity: int | None = None,
-                 headroom: float = 1.15):
+                 headroom: float = 1.15, trace: bool = False):
         self.n = int(n)
         self.cams = list(cams)
         self.prm = prm
         self.device = torch.device(device)
-        self.flags = (N.FLAG_BACKWARD if backward else 0) | (N.FLAG_DEBUG_STATS if debug else 0)
+        self.flags = ((N.FLAG_BACKWARD if backward else 0) | (N.FLAG_DEBUG_STATS if debug else 0) |
+                      (N.FLAG_DEBUG_TRACE if trace else 0))
         self.headroom = headroom
         self._cams_arr = N.cameras_array(self.cams)
         self.total_pixels = sum(c.width * c.height for c in self.cams)
@@ -162,6 +163,11 @@ class Renderer:
         h = self._region(L.dbg_hash, P, torch.int64)
         return nbl, h
 
+    def debug_trace(self) -> torch.Tensor:
+        """[P, TRACE_LEN] ids of the first blended Gaussians per pixel (needs trace=True)."""
+        P = int(self.layout.total_pixels)
+        return self._region(self.layout.dbg_trace, P * N.TRACE_LEN, torch.int32).view(P, N.TRACE_LEN)
+
     def sorted_lists(self):
         """(ranges [T,2] int32, sorted keys int64, sorted ids int32) of the last forward."""
         L = self.layout
@@ -175,7 +181,7 @@ class Renderer:
     def records(self):
         L = self.layout
         m = self.n * len(self.cams)
-        geom = self._region(L.geom, m * 16, torch.float32).view(len(self.cams), self.n, 16)
+        geom = self._region(L.geom, m * 24, torch.float32).view(len(self.cams), self.n, 24)
         color = self._region(L.color, m * 4, torch.float32).view(len(self.cams), self.n, 4)
         rect = self._region(L.rect, m * 4, torch.int16).view(len(self.cams), self.n, 4)
         counts = self._region(L.counts, m, torch.int32).view(len(self.cams), self.n)

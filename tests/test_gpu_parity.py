@@ -79,30 +79,49 @@ def test_preprocess_records_match_oracle(oracle):
     geom, color, rect, counts = [x.cpu().numpy() for x in gpu["renderer"].records()]
     with oracle.OracleRun(sc, cam, prm) as r:
         pp = r.preprocess()
-    vis_g = geom[0, :, 5] > 0
+    g = geom[0].astype(np.float64)
+    vis_g = g[:, 8] > 0
     vis_o = pp["visible"] > 0
     near = pp["margin"] < 1e-5
     assert np.array_equal(vis_g[~near], vis_o[~near])
     v = vis_o & vis_g
-    g = geom[0][v]
-    assert np.allclose(g[:, 0:2], pp["mean2"][v], rtol=1e-5, atol=2e-3)
-    A = np.stack([g[:, 2], g[:, 3], g[:, 4]], 1)
-    assert np.allclose(A, pp["conic"][v], rtol=2e-3, atol=1e-6)
-    assert np.allclose(g[:, 5], pp["opacity"][v], rtol=1e-5)
+    g = g[v]
+    # projected mean (hi + lo pair evaluated in FP64)
+    m2 = np.stack([g[:, 0] + g[:, 2], g[:, 1] + g[:, 3]], 1)
+    assert np.abs(m2 - pp["mean2"][v]).max() < 1e-6
+    # conic: the quadratic form at random offsets, and the eigenvalues
+    rng = np.random.default_rng(2)
+    D = rng.normal(size=(len(g), 2)) * 3
+    e = g[:, 4:6]
+    pe = e[:, 0] * D[:, 0] + e[:, 1] * D[:, 1]
+    pq = e[:, 0] * D[:, 1] - e[:, 1] * D[:, 0]
+    q_gpu = g[:, 6] * pe * pe + g[:, 7] * pq * pq
+    A = pp["conic"][v]
+    q_ora = A[:, 0] * D[:, 0] ** 2 + 2 * A[:, 1] * D[:, 0] * D[:, 1] + A[:, 2] * D[:, 1] ** 2
+    assert np.allclose(q_gpu, q_ora, rtol=2e-5, atol=1e-9)
+    lam = np.linalg.eigvalsh(np.stack([np.stack([A[:, 0], A[:, 1]], 1), np.stack([A[:, 1], A[:, 2]], 1)], 1))
+    assert np.allclose(np.sort(g[:, 6:8], 1), lam, rtol=2e-5)
+    assert np.allclose(g[:, 8], pp["opacity"][v], rtol=1e-6)
     assert np.allclose(color[0][v][:, :3], pp["color"][v], atol=2e-5)
-    # camera-space Sigma^-1 and v = S p against the oracle's world-space values
+    # depth factors: sum_k m_k m_k^T is the camera-space Sigma^-1 and sum_k c_k m_k = Sigma^-1 p
     Rc = cam.R
     s6 = pp["sinv6"][v]
     Sw = np.stack([np.stack([s6[:, 0], s6[:, 1], s6[:, 2]], 1), np.stack([s6[:, 1], s6[:, 3], s6[:, 4]], 1),
                    np.stack([s6[:, 2], s6[:, 4], s6[:, 5]], 1)], 1)
     Sc = Rc @ Sw @ Rc.T
-    vc = (Rc @ pp["v"][v].T).T
-    gS = np.stack([g[:, 9], g[:, 10] / 2, g[:, 11] / 2, g[:, 12], g[:, 13] / 2, g[:, 14]], 1)
-    oS = np.stack([Sc[:, 0, 0], Sc[:, 0, 1], Sc[:, 0, 2], Sc[:, 1, 1], Sc[:, 1, 2], Sc[:, 2, 2]], 1)
-    scale = np.abs(oS).max(1, keepdims=True)
-    assert np.abs(gS - oS).max() <= 1e-4 * scale.max() and (np.abs(gS - oS) / scale).max() < 1e-4
-    gv = np.stack([g[:, 6], g[:, 7], g[:, 8]], 1)
-    assert (np.abs(gv - vc) / np.abs(vc).max(1, keepdims=True)).max() < 1e-4
+    m = np.stack([g[:, 12:15], g[:, 15:18], g[:, 18:21]], 1)     # [n, k, 3]
+    cfac = g[:, 9:12]
+    Sg = np.einsum("nki,nkj->nij", m, m)
+    scale = np.abs(Sc).reshape(len(Sc), -1).max(1)[:, None, None]
+    assert (np.abs(Sg - Sc) / scale).max() < 2e-5
+    # t_opt through the projected mean from the GPU record vs the oracle's world-space formula
+    d = np.stack([(m2[:, 0] - cam.cx) / cam.fx, (m2[:, 1] - cam.cy) / cam.fy, np.ones(len(g))], 1)
+    a_k = np.einsum("nki,ni->nk", m, d)
+    t_gpu = np.linalg.norm(d, axis=1) * (a_k * cfac).sum(1) / (a_k * a_k).sum(1)
+    dw = (Rc.T @ (d / np.linalg.norm(d, axis=1, keepdims=True)).T).T
+    t_ora = np.einsum("ni,ni->n", dw, pp["v"][v]) / np.einsum("ni,nij,nj->n", dw, Sw, dw)
+    assert np.allclose(t_gpu, t_ora, rtol=2e-6)
+    assert np.allclose(g[:, 21], pp["pcam"][v][:, 2], rtol=1e-6)
     rr = rect[0][v].astype(np.int64)
     orc = pp["rect"][v]
     same_rect = (rr[:, 0] == orc[:, 0]) & (rr[:, 1] == orc[:, 1]) & (rr[:, 2] == orc[:, 2] + 1) & (rr[:, 3] == orc[:, 3] + 1)
@@ -136,11 +155,16 @@ def test_sorted_tile_lists_match_oracle(oracle):
         assert np.array_equal(np.sort(vals[ga:gb]), np.sort(ids[a:b]))
         assert np.allclose(t_gpu[ga:gb], ts[a:b], rtol=2e-6, atol=1e-6)
         if not np.array_equal(vals[ga:gb], ids[a:b]):
-            # only permutations among near-equal depths are allowed
-            gaps = np.abs(np.diff(ts[a:b])) / np.maximum(np.abs(ts[a:b][1:]), 1e-30)
-            assert gaps.min() < 1e-6
+            # the order may differ only inside groups of consecutive entries whose depths are
+            # within 1e-6 relative of each other (FP32 keys vs FP64 depths)
+            o = ts[a:b]
+            gaps = np.abs(np.diff(o)) / np.maximum(np.maximum(np.abs(o[1:]), np.abs(o[:-1])), 1e-30)
+            group = np.concatenate([[0], np.cumsum(gaps >= 1e-6)])
+            gid = dict(zip(ids[a:b].tolist(), group.tolist()))
+            gseq = np.array([gid[x] for x in vals[ga:gb].tolist()])
+            assert np.array_equal(gseq, group)
             mism_tiles += 1
-    assert mism_tiles <= cam.num_tiles * 0.01
+    print("tiles with near-tie permutations:", mism_tiles)
 
 
 @pytest.mark.parametrize("size", [(100, 75), (17, 33), (1, 1), (64, 7)])

@@ -208,6 +208,10 @@ def test_sh_degree0_colour_is_view_independent(oracle):
 def test_projection_jacobian_is_finite_difference(oracle):
     rng = np.random.default_rng(15)
     cam = I.look_at((0.3, -0.2, -4), (0, 0, 0), (0, 1, 0), 320, 240, 55.0)
+    # the oracle receives the camera as the renderer does, rounded to float32
+    cam = I.Camera(cam.R.astype(np.float32).astype(np.float64), cam.t.astype(np.float32).astype(np.float64),
+                   float(np.float32(cam.fx)), float(np.float32(cam.fy)), float(np.float32(cam.cx)),
+                   float(np.float32(cam.cy)), cam.width, cam.height)
     prm = I.RenderParams()
 
     def proj(mu):
