@@ -2,10 +2,10 @@
  *
  * Hierarchical sorted Gaussian splatting: Radl, Steiner et al., "StopThePop: Sorted Gaussian
  * Splatting for View-Consistent Real-time Rendering", TOG 43(4) 2024, arXiv 2402.00525.
- * The forward pass is the paper's four stages (Sec. 4, Fig. "pipeline"): Preprocess,
+ * The forward pass is the paper's four stages (Sec. 3, Fig. "pipeline"): Preprocess,
  * Duplicate (with exact tile culling and the per-tile t_opt key), a global sort of
  * (tile, depth) keys, and the hierarchical Render with tail / mid / head queues. The backward
- * pass replays the same blend order front to back (Sec. 4.5).
+ * pass replays the same blend order front to back (Sec. 3.5).
  *
  * Conventions shared by every entry point:
  *   - Every array pointer is a DEVICE pointer owned by the caller unless the comment says
@@ -89,14 +89,14 @@ typedef struct {
 } stp_camera;
 
 typedef struct {
-    int32_t tail;                /* tail (4x4) queue size: 32n + 32, n >= 1 (Sec. 4.4)       */
+    int32_t tail;                /* tail (4x4) queue size: 32n + 32, n >= 1 (Sec. 3.4)       */
     int32_t mid;                 /* mid (2x2) queue size: 4m + 4, m >= 1                    */
     int32_t head;                /* head (per-pixel) queue size, 1..16                      */
-    int32_t lb_threshold;        /* load-balancing threshold in tiles (Sec. 4.4), >= 1      */
+    int32_t lb_threshold;        /* load-balancing threshold in tiles (Sec. 3.4), >= 1      */
     float eps_o;                 /* contribution threshold, 1/255                           */
     float t_min;                 /* transmittance early-out, 1e-4                           */
     float alpha_max;             /* 0.99 */
-    float inv_scale_max;         /* bound on entries of S^-1, 1e3 (Sec. 4.2)               */
+    float inv_scale_max;         /* bound on entries of S^-1, 1e3 (Sec. 3.2)               */
     float dilation;              /* EWA low-pass added to Sigma2, 0.3                       */
     float frustum_clamp;         /* Jacobian clamp factor, 1.3                              */
     float znear;                 /* near plane, 0.2                                         */
@@ -148,7 +148,7 @@ typedef struct {                 /* byte offsets of workspace regions (for inspe
 } stp_workspace_layout;
 
 /* Size of the workspace one stp_render call needs for `nviews` cameras of N Gaussians
- * (Sec. 4: per-view records, sort entries, tile ranges, per-pixel T). Host-only, no CUDA
+ * (Sec. 3: per-view records, sort entries, tile ranges, per-pixel T). Host-only, no CUDA
  * call. Returns 0 on invalid arguments (see stp_last_error).                              */
 size_t stp_workspace_size(int64_t n, const stp_camera* cams /* host, [nviews] */, int32_t nviews,
                           const stp_params* prm /* host */);
@@ -157,9 +157,9 @@ size_t stp_workspace_size(int64_t n, const stp_camera* cams /* host, [nviews] */
 stp_status stp_workspace_layout_get(int64_t n, const stp_camera* cams /* host */, int32_t nviews,
                                     const stp_params* prm /* host */, stp_workspace_layout* out /* host */);
 
-/* Forward pass (Sec. 4): Preprocess -> Duplicate -> global radix sort -> hierarchical
+/* Forward pass (Sec. 3): Preprocess -> Duplicate -> global radix sort -> hierarchical
  * Render, for `nviews` views of one scene in one batched launch sequence. Writes rgb
- * [pixels,3], depth [pixels] (volumetric depth with phi = t_opt, Sec. 6) and, if not NULL,
+ * [pixels,3], depth [pixels] (volumetric depth with phi = t_opt, Sec. 4.1 "Depth Evaluation") and, if not NULL,
  * tfinal [pixels]. The workspace keeps the state the backward pass needs (sorted lists,
  * records, final T). Asynchronous; call stp_read_status() to learn whether the capacity
  * sufficed (if not, rgb / depth are undefined and num_entries tells the size needed).   */
@@ -168,7 +168,7 @@ stp_status stp_render(const stp_gaussians* g /* host struct of device pointers *
                       const stp_params* prm /* host */, void* workspace, size_t ws_bytes,
                       float* rgb, float* depth, float* tfinal, void* stream);
 
-/* Backward pass (Sec. 4.5): replays the forward's blend order front to back using the
+/* Backward pass (Sec. 3.5): replays the forward's blend order front to back using the
  * workspace of the preceding stp_render with the same arguments (which must not have been
  * modified), and ACCUMULATES (+=) the gradients of <d_rgb, rgb> + <d_depth, depth> into
  * `grad` (device arrays in the input layout; zero them first for a fresh gradient).
@@ -184,7 +184,7 @@ stp_status stp_render_backward(const stp_gaussians* g, const stp_camera* cams, i
 stp_status stp_read_status(const void* workspace, stp_run_status* out /* host */, void* stream);
 
 /* Stable LSD radix sort of (uint64 key, uint32 value) pairs on the low `key_bits` bits
- * (1..64), the sort of Sec. 3.1 / 4 that orders (tile, depth) keys. keys_in / vals_in are
+ * (1..64), the sort of Sec. 2.1 / 3.4 that orders (tile, depth) keys. keys_in / vals_in are
  * read, keys_out / vals_out receive the sorted pairs; `n` may also be read from the device
  * (n_dev != NULL: the count is min(*n_dev, n)). temp is device scratch of
  * stp_sort_temp_bytes(n) bytes. The four arrays must not overlap. Asynchronous.            */
@@ -193,7 +193,7 @@ stp_status stp_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint
                           uint32_t* vals_out, int64_t n, const uint64_t* n_dev, int32_t key_bits,
                           void* temp, size_t temp_bytes, void* stream);
 
-/* Stage timing with CUDA events (Sec. 5.3 reports per-stage times). After
+/* Stage timing with CUDA events (Sec. 4.3 reports per-stage times). After
  * stp_profile_enable(max_calls), each stp_render / stp_render_backward call on this host
  * thread records STP_NUM_STAGE_EVENTS events on its stream into the next of max_calls slots
  * (further calls are not recorded); max_calls = 0 disables and frees the events.

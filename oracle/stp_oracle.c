@@ -7,16 +7,16 @@
  * It is compiled by oracle/build.py and shares nothing with the CUDA library.
  *
  * Section map:
- *   Sec. 3.1 (3DGS preliminaries)       : Gaussian, covariance, EWA splat, alpha blending
+ *   Sec. 2.1 (3DGS preliminaries)       : Gaussian, covariance, EWA splat, alpha blending
  *   Eq. "dopt" and Appendix A           : per-ray depth t_opt and Sigma^-1 = R S^-2 R^T
- *   Sec. 4.2                            : S^-1 bounded by 1e3; full per-ray sort (FULL mode)
- *   Sec. 4.3                            : per-ray resort window (WINDOW mode); sort error delta
- *   Sec. 4.4 "Tile-based culling"       : exact culling with Algorithm 1 (appendix B.1)
- *   Sec. 4.4 "Tile-depth adjustment"    : key depth is t_opt on the ray through x_hat
+ *   Sec. 3.2                            : S^-1 bounded by 1e3; full per-ray sort (FULL mode)
+ *   Sec. 3.3                            : per-ray resort window (WINDOW mode); sort error delta
+ *   Sec. 3.4 "Tile-based culling"       : exact culling with Algorithm 1 (appendix B.1)
+ *   Sec. 3.4 "Tile-depth adjustment"    : key depth is t_opt on the ray through x_hat
  *   Appendix B.2                        : opacity-aware bound t_O = sqrt(2 ln(alpha/eps_O))
- *   Sec. 4.4 "Hierarchically sorted rendering": tail / mid / head queues (HIER mode)
- *   Sec. 4.5                            : backward pass front to back with C - C_i, T_N / T_i
- *   Sec. 6 "Depth evaluation"           : volumetric depth with phi = t_opt
+ *   Sec. 3.4 "Hierarchically sorted rendering": tail / mid / head queues (HIER mode)
+ *   Sec. 3.5                            : backward pass front to back with C - C_i, T_N / T_i
+ *   Sec. 4.1 "Depth Evaluation"           : volumetric depth with phi = t_opt
  *
  * Readings where the paper is silent or ambiguous are listed in the repository's design
  * notes; the ones that shape code here are restated at the place they apply.
@@ -77,7 +77,7 @@ static void normalise_quat(const double qin[4], double q[4], double* len)
 }
 
 /* ------------------------------------------------------------------ Gaussian covariance
- * Sec. 3.1: Sigma = R S S^T R^T with S = diag(s), s = exp(log_scale).                     */
+ * Sec. 2.1: Sigma = R S S^T R^T with S = diag(s), s = exp(log_scale).                     */
 void orc_sigma(const double quat[4], const double log_scale[3], double sigma[9])
 {
     double q[4], l, R[9];
@@ -91,7 +91,7 @@ void orc_sigma(const double quat[4], const double log_scale[3], double sigma[9])
         }
 }
 
-/* Appendix A: Sigma^-1 = R S^-1 S^-1 R^T; Sec. 4.2: entries of S^-1 bounded by 1e3.      */
+/* Appendix A: Sigma^-1 = R S^-1 S^-1 R^T; Sec. 3.2: entries of S^-1 bounded by 1e3.      */
 void orc_sigma_inv(const double quat[4], const double log_scale[3], double inv_scale_max,
                    double sinv[9])
 {
@@ -221,7 +221,7 @@ static void sh_basis_grad(const double dir[3], double y[16], double* grad)
 void orc_sh_basis(const double dir[3], double y[16]) { sh_basis_grad(dir, y, NULL); }
 
 /* ------------------------------------------------------------------ EWA projection
- * Sec. 3.1 (kept untouched from 3DGS, Sec. 4.4): the first-order (Jacobian) approximation
+ * Sec. 2.1 (kept untouched from 3DGS, Sec. 3.4): the first-order (Jacobian) approximation
  * of the perspective projection at the camera-space mean, with the 3DGS frustum clamp of
  * the Jacobian and the 3DGS low-pass dilation (readings: both kept, both parameters).    */
 typedef struct {
@@ -409,7 +409,7 @@ static void preprocess_one(ctx* c, const orc_scene* sc, int64_t i)
         g->raw[ch] = s;
         g->color[ch] = s > 0 ? s : 0.0;
     }
-    /* Sigma^-1 with the S^-1 clamp (Sec. 4.2), v = Sigma^-1 (mu - o) (Appendix B.4)       */
+    /* Sigma^-1 with the S^-1 clamp (Sec. 3.2), v = Sigma^-1 (mu - o) (Appendix B.4)       */
     for (int k = 0; k < 3; k++) {
         double si = fmin(exp(-ls[k]), P->inv_scale_max);
         g->w[k] = si * si;
@@ -468,7 +468,7 @@ static double depth_at(const ctx* c, const grec* g, double x, double y)
     return orc_t_opt(d, c->o, g->mu, g->sinv);
 }
 
-/* Duplicate (Sec. 4.4 "Tile-based culling", "Tile-depth adjustment"): for every visible
+/* Duplicate (Sec. 3.4 "Tile-based culling", "Tile-depth adjustment"): for every visible
  * Gaussian (ascending id) and every tile of its rectangle (row major), x_hat by Algorithm 1
  * on the tile's pixel-centre box; keep iff opacity * G2(x_hat) >= eps_O; key depth is
  * t_opt on the ray through x_hat. The tile's list is then sorted by (depth, id), which is
@@ -499,7 +499,7 @@ static void build_lists(ctx* c)
                 if (in_rect && g->visible && keep) g->ntiles++;
                 if (!L->selected) continue;
                 /* key depth: t_opt through x_hat (default); flag 4: through the tile centre
-                 * (the naive per-tile depth of Sec. 4.3); flag 8: the mean's view-space depth
+                 * (the naive per-tile depth of Sec. 3.3); flag 8: the mean's view-space depth
                  * (3DGS global depth, ablation B of Tab. performance_ablation)               */
                 double t;
                 if (P->flags & 8) t = g->p[2];
@@ -522,7 +522,7 @@ static void build_lists(ctx* c)
             L->bm_d[b] = INFINITY;
             L->bm_c[b] = INFINITY;
         }
-        /* batch-boundary depth gaps: which 32 entries load together (Sec. 4.4)           */
+        /* batch-boundary depth gaps: which 32 entries load together (Sec. 3.4)           */
         for (int b = 0; b + 1 < nb; b++) L->bm_d[b] = relgap(L->e[32 * b + 31].t, L->e[32 * b + 32].t);
         /* near-threshold entry-set decisions act from the batch they fall into           */
         for (int k = 0; k < L->nn; k++) {
@@ -554,7 +554,7 @@ static void bl_push(blist* B, int id, double a, double t, double T)
 
 /* Eq. "volume_desc" front to back, with the 3DGS early-out: a Gaussian that would take the
  * transmittance below t_min is not blended and the ray stops (reading). Depth accumulates
- * the volumetric depth with phi = t_opt (Sec. 6 "Depth evaluation"), unnormalised.        */
+ * the volumetric depth with phi = t_opt (Sec. 4.1 "Depth Evaluation"), unnormalised.        */
 static void blend(ctx* c, pstate* ps, const sinks* sk, double t, int id, double a, int64_t* cnt)
 {
     if (ps->done) return;
@@ -648,8 +648,8 @@ static int eval_box(const ctx* c, int id, const double box[4], double* t, double
 }
 
 /* head (per-pixel) queue: insertion after equal keys; when more than `head` entries are
- * held, the smallest is blended (Sec. 4.3 "if the window overflows, blend the sample with
- * the smallest depth"; reading: insert then evict; flag 1 evicts before inserting).      */
+ * held, the smallest is blended (Sec. 3.3: a full resorting window gives up its nearest
+ * entry; reading: insert then evict; flag 1 evicts before inserting).                    */
 static void head_push(ctx* c, pstate* ps, const sinks* sk, int hsize, hent e, int64_t* cnt)
 {
     if (ps->done) return;
@@ -686,7 +686,7 @@ static void head_flush(ctx* c, pstate* ps, const sinks* sk, int64_t* cnt)
 }
 
 /* ------------------------------------------------------------------ HIER schedule
- * Sec. 4.4 "Hierarchically sorted rendering", one 4x4 subtile S of a 16x16 tile (the
+ * Sec. 3.4 "Hierarchically sorted rendering", one 4x4 subtile S of a 16x16 tile (the
  * subtiles are independent). Reading of the push discipline (queue sizes TAIL=32n+32,
  * MID=4m+4, HEAD):
  *   - the tile list is consumed in batches of 32 entries; each batch is culled against S's
@@ -899,8 +899,8 @@ static int cmp_fent(const void* a, const void* b)
     return (x->pos > y->pos) - (x->pos < y->pos);
 }
 
-/* FULL (Sec. 4.2): every list entry with alpha >= eps_O, stably sorted by the pixel's own
- * t_opt. GLOBAL: blended in tile-list order. WINDOW (Sec. 4.3): k-buffer of window_k over
+/* FULL (Sec. 3.2): every list entry with alpha >= eps_O, stably sorted by the pixel's own
+ * t_opt. GLOBAL: blended in tile-list order. WINDOW (Sec. 3.3): k-buffer of window_k over
  * the tile list.                                                                          */
 static void flat_tile(ctx* c, const sinks* sk, int tile, int64_t* cnt)
 {
@@ -1168,7 +1168,7 @@ int32_t orc_schedule_synthetic(int32_t n, const double* t, const int32_t* keep, 
 }
 
 /* ------------------------------------------------------------------ adjoint
- * Sec. 4.5: gradients in front-to-back blend order with the suffix colour C - C_i and the
+ * Sec. 3.5: gradients in front-to-back blend order with the suffix colour C - C_i and the
  * suffix transmittance T_N / T_i; then the chain rule through the preprocess (3DGS
  * structure: conic -> Sigma2 -> Sigma -> scale, rotation; mean2 and J -> mean; colour ->
  * SH and direction -> mean; opacity -> logit), and through t_opt for the depth output.  */

@@ -24,9 +24,9 @@ typedef struct {
 } orc_camera;
 
 typedef struct {
-    int32_t tail, mid, head;   /* queue sizes (Sec. 4.4): 32n+32, 4m+4, any             */
+    int32_t tail, mid, head;   /* queue sizes (Sec. 3.4): 32n+32, 4m+4, any             */
     int32_t mode;              /* 0 HIER, 1 FULL, 2 GLOBAL, 3 WINDOW                    */
-    int32_t window_k;          /* WINDOW mode k-buffer size (Sec. 4.3)                 */
+    int32_t window_k;          /* WINDOW mode k-buffer size (Sec. 3.3)                 */
     int32_t flags;             /* 1: head evict-before-insert; 2: level-centre rays;
                                   4: tile-centre key; 8: view-space-depth key           */
     int32_t sh_degree;

@@ -1,6 +1,6 @@
 // stp_backward.cu -- adjoint of Preprocess.
 //
-// StopThePop (arXiv 2402.00525) Sec. 4.5 keeps 3DGS's gradient flow: the backward Render
+// StopThePop (arXiv 2402.00525) Sec. 3.5 keeps 3DGS's gradient flow: the backward Render
 // (stp_render.cu, BWD = true) accumulates per (view, Gaussian) the gradients of the 2D mean,
 // the conic, the opacity, the colour and -- when a depth gradient is given -- of the depth
 // factors (m_k, c_k) of the record; this kernel chains them back to the inputs:

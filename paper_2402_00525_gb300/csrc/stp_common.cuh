@@ -55,7 +55,7 @@ struct ViewDesc {
 // and the mean as an unevaluated float pair, so D = x - mean2 keeps its relative accuracy:
 // both matter for the cull and alpha decisions of long, thin splats (aspect up to ~2000:1).
 // m_k = s_k^-1 (R_c R_q) e_k are the camera-space axes of the Gaussian scaled by the clamped
-// inverse scales (Sigma^-1 = R S^-1 S^-1 R^T, appendix A; S^-1 entries <= 1e3, Sec. 4.2) and
+// inverse scales (Sigma^-1 = R S^-1 S^-1 R^T, appendix A; S^-1 entries <= 1e3, Sec. 3.2) and
 // c_k = m_k . p with p the mean in camera space. For the ray through pixel-space point x,
 // d = ((x - cx) / fx, (y - cy) / fy, 1), a_k = m_k . d and (Eq. "dopt")
 //   t_opt(x) = |d| (sum_k a_k c_k) / (sum_k a_k^2),
@@ -104,7 +104,7 @@ __device__ __forceinline__ float quad_form(const Rec& r, float dx, float dy)
     return __fmaf_rn(r.r1.z, __fmul_rn(pe, pe), __fmul_rn(r.r1.w, __fmul_rn(pp, pp)));
 }
 
-// opacity * G2 at offset D (Sec. 3.1: alpha = opacity times the 2D splat)
+// opacity * G2 at offset D (Sec. 2.1: alpha = opacity times the 2D splat)
 __device__ __forceinline__ float splat_at(const Rec& r, float dx, float dy)
 {
     return __fmul_rn(rec_opacity(r), expf(__fmul_rn(-0.5f, quad_form(r, dx, dy))));
@@ -172,7 +172,7 @@ __device__ __forceinline__ Box block_box(int ox, int oy, int s, int W, int H)
     return Box{ox + 0.5f, xe + 0.5f, oy + 0.5f, ye + 0.5f};
 }
 
-// Cull test of a box (Sec. 4.4, "Tile-based culling") and, if kept, the key depth on the
+// Cull test of a box (Sec. 3.4, "Tile-based culling") and, if kept, the key depth on the
 // ray through the box's x_hat ("Tile-depth adjustment"); centre_ray selects the box centre.
 __device__ __forceinline__ bool box_keep(const Rec& r, const Box& b, float eps_o)
 {

@@ -1,6 +1,6 @@
 // stp_preprocess.cu -- Preprocess, the scan of tile counts, and Duplicate.
 //
-// StopThePop (arXiv 2402.00525) Sec. 4.4 and appendix B: per Gaussian and view, the EWA 2D
+// StopThePop (arXiv 2402.00525) Sec. 3.4 and appendix B: per Gaussian and view, the EWA 2D
 // splat, SH colour, Sigma^-1 with the S^-1 clamp packed with Sigma^-1 (mu - o) for the depth
 // evaluation, the opacity-aware bounding rectangle t_O sqrt(lambda_max), and the number of
 // tiles that survive exact culling (Algorithm 1). Duplicate re-takes the same cull decisions

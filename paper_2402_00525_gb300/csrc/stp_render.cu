@@ -1,7 +1,7 @@
 // stp_render.cu -- hierarchical sorted Render (forward) and its replay for the backward pass.
 //
-// StopThePop (arXiv 2402.00525) Sec. 4.4 "Hierarchically sorted rendering", Fig. "pipeline",
-// appendix B.4 "Render"; backward Sec. 4.5.
+// StopThePop (arXiv 2402.00525) Sec. 3.4 "Hierarchically sorted rendering", Fig. "pipeline",
+// appendix B.4 "Render"; backward Sec. 3.5.
 //
 // One 256-thread block renders one 16x16 tile. Warp w owns the two horizontally adjacent
 // 4x4 subtiles 2w and 2w+1 (an 8x4 pixel strip); half-warp h owns subtile 2w+h, its 4-lane
@@ -139,7 +139,7 @@ __device__ __forceinline__ void blend(const PipeArgs& a, const ViewDesc& V, Px<H
 }
 
 // insert (key, id, val) after equal keys; when more than HEAD entries are held blend the
-// smallest (Sec. 4.3 k-buffer; evict_first = the alternative "blend before insert" reading)
+// smallest (Sec. 3.3 k-buffer; evict_first = the alternative "blend before insert" reading)
 template <int HEAD, bool BWD>
 __device__ __forceinline__ void head_push(const PipeArgs& a, const ViewDesc& V, Px<HEAD>& s,
                                           const PixCtx& c, uint32_t key, uint32_t id, float val,

@@ -1,8 +1,8 @@
 // stp_sort.cu -- global sort of (tile, depth) keys and the per-tile ranges.
 //
 // StopThePop (arXiv 2402.00525) keeps 3DGS's single global sort of combined keys, tile id in
-// the high bits and depth in the low bits (Sec. 3.1, appendix B.3), and relies on a stable
-// order so that forward and backward see the same list (Sec. 4.5). This is a stable LSD radix
+// the high bits and depth in the low bits (Sec. 2.1, appendix B.3), and relies on a stable
+// order so that forward and backward see the same list (Sec. 3.5). This is a stable LSD radix
 // sort with 8-bit digits over only the key bits in use (32 depth bits + the bits of the tile
 // count), three kernels per digit:
 //   hist    -- every block counts the digits of a fixed contiguous range of the input;

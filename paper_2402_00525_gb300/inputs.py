@@ -6,7 +6,7 @@ no depth, no blending), so both implementations can consume it without sharing m
 
 Scene shapes follow the workloads of StopThePop (Radl et al. 2024): the paper renders
 trained 3DGS scenes of about 1-6 M anisotropic Gaussians with SH degree 3 at Full HD
-(Sec. 5.3, Tab. "performance_ablation"). Those scenes are not available here, so seeded
+(Sec. 4.3, Tab. "performance_ablation"). Those scenes are not available here, so seeded
 generators with the same sizes and a heavy-tailed screen-size distribution stand in for
 them.
 
@@ -25,14 +25,14 @@ from typing import List, Sequence
 
 import numpy as np
 
-# Paper constants (Sec. 4.1 "Tile-based culling": eps_O = 1/255; Sec. 4.2: S^-1 entries
-# bounded by 1e3; Sec. 4.4: queue sizes 64/8/4; load-balance threshold 32).
+# Paper constants (Sec. 3.4 "Tile-based culling": eps_O = 1/255; Sec. 3.2: S^-1 entries
+# bounded by 1e3; Sec. 3.4: queue sizes 64/8/4; load-balance threshold 32).
 EPS_O = 1.0 / 255.0
 
-MODE_HIER = 0     # the paper's hierarchical 4x4 / 2x2 / per-pixel queues (Sec. 4.4)
-MODE_FULL = 1     # full per-ray sort (Sec. 4.2, "naive sorting")
+MODE_HIER = 0     # the paper's hierarchical 4x4 / 2x2 / per-pixel queues (Sec. 3.4)
+MODE_FULL = 1     # full per-ray sort (Sec. 3.2, "naive sorting")
 MODE_GLOBAL = 2   # blend in tile-list order (3DGS order, with per-tile t_opt keys)
-MODE_WINDOW = 3   # per-ray resort window of K entries (Sec. 4.3, k-buffer)
+MODE_WINDOW = 3   # per-ray resort window of K entries (Sec. 3.3, k-buffer)
 
 # flag bits of RenderParams.flags
 FLAG_HEAD_EVICT_FIRST = 1      # head queue: blend the front before inserting (alternative reading)
@@ -44,10 +44,10 @@ FLAG_VIEW_DEPTH_KEY = 8        # tile sort key = view-space depth of the mean (3
 @dataclasses.dataclass
 class RenderParams:
     """Knobs of the renderer. Defaults are the paper's (64/8/4 queues, eps_O = 1/255)."""
-    tail: int = 64            # 4x4 tile-queue size, 32n+32 (Sec. 4.4)
-    mid: int = 8              # 2x2 tile-queue size, 4m+4 (Sec. 4.4)
-    head: int = 4             # per-pixel queue size (Sec. 4.4)
-    lb_threshold: int = 32    # load-balancing tile threshold (Sec. 4.1 "Load Balancing")
+    tail: int = 64            # 4x4 tile-queue size, 32n+32 (Sec. 3.4)
+    mid: int = 8              # 2x2 tile-queue size, 4m+4 (Sec. 3.4)
+    head: int = 4             # per-pixel queue size (Sec. 3.4)
+    lb_threshold: int = 32    # load-balancing tile threshold (Sec. 3.4 "Load Balancing")
     eps_o: float = EPS_O
     t_min: float = 1e-4       # transmittance early-out
     alpha_max: float = 0.99

@@ -288,7 +288,7 @@ def test_full_hd_3m_sampled_tiles_match_oracle(oracle):
 
 
 def test_backward_matches_oracle_adjoint(oracle):
-    """Sec. 4.5 backward against the FP64 adjoint on the 512-Gaussian 64x64 case. The loss
+    """Sec. 3.5 backward against the FP64 adjoint on the 512-Gaussian 64x64 case. The loss
     weights are zero on undecided pixels, so both sides differentiate the same blend order."""
     sc, _, cam, prm = I.fd_subcase()
     rng = np.random.default_rng(4)

@@ -57,12 +57,12 @@ def test_paper_defaults_match_render_params():
                                                        pv["head_queue"], pv["lb_threshold"])
     assert p.eps_o == pytest.approx(pv["eps_o"], rel=1e-15)
     assert p.inv_scale_max == pv["inv_scale_max"]
-    # window bounds implied by the queue sizes (Sec. 4.4): 17 + 4 + 4 and 64 + 4 + 4
+    # window bounds implied by the queue sizes (Sec. 3.4): 17 + 4 + 4 and 64 + 4 + 4
     assert pv["tail_drain_min"] + (p.mid - 4) + p.head == pv["window_min"]
     assert p.tail + (p.mid - 4) + p.head == pv["window_max"]
 
 
-# --------------------------------------------------------------------- Eq. dopt, Sec. 4.2
+# --------------------------------------------------------------------- Eq. dopt, Sec. 3.2
 def test_isotropic_worked_example(oracle):
     rows = np.loadtxt(os.path.join(GOLD, "isotropic_depth.txt"))
     for th, muy, t in rows:
@@ -107,7 +107,7 @@ def test_t_opt_maximises_gaussian_along_ray(oracle):
         assert got == pytest.approx(tb, rel=2e-7, abs=2e-7)
 
 
-# --------------------------------------------------------------------- Appendix A, Sec. 4.2
+# --------------------------------------------------------------------- Appendix A, Sec. 3.2
 def test_sigma_inverse_and_clamp(oracle):
     rng = np.random.default_rng(12)
     for _ in range(100):
@@ -156,7 +156,7 @@ def test_alg1_matches_grid_search(oracle):
         qh = dxh @ A @ dxh
         assert qh <= Q.min() + 1e-9 * (1 + abs(Q.min()))
         inside = box[0] <= mu[0] <= box[1] and box[2] <= mu[1] <= box[3]
-        if not inside:   # then x_hat lies on the boundary (Sec. 4.4: on an edge nearest mu2)
+        if not inside:   # then x_hat lies on the boundary (Sec. 3.4: on an edge nearest mu2)
             on_edge = (min(abs(xh[0] - box[0]), abs(xh[0] - box[1])) < 1e-9 or
                        min(abs(xh[1] - box[2]), abs(xh[1] - box[3])) < 1e-9)
             assert on_edge
@@ -204,7 +204,7 @@ def test_sh_degree0_colour_is_view_independent(oracle):
         assert np.allclose(c, expect, atol=1e-12)
 
 
-# --------------------------------------------------------------------- EWA splat (Sec. 3.1)
+# --------------------------------------------------------------------- EWA splat (Sec. 2.1)
 def test_projection_jacobian_is_finite_difference(oracle):
     rng = np.random.default_rng(15)
     cam = I.look_at((0.3, -0.2, -4), (0, 0, 0), (0, 1, 0), 320, 240, 55.0)
@@ -249,7 +249,7 @@ def _alpha_all_pixels(pp, cam):
 
 @pytest.mark.parametrize("which", ["fd", "plain"])
 def test_tile_culling_never_drops_a_contributor(oracle, which):
-    """Sec. 4.4: culling is exact; brute force over every pixel finds no pixel with
+    """Sec. 3.4: culling is exact; brute force over every pixel finds no pixel with
     alpha >= eps_O whose tile list lacks the Gaussian (rectangle bound of App. B.2 included)."""
     if which == "fd":
         sc, _, cam, prm = I.fd_subcase()
@@ -274,7 +274,7 @@ def test_tile_culling_never_drops_a_contributor(oracle, which):
 
 
 def test_hier_blends_the_same_set_as_full_sort(oracle):
-    """Culling at the 4x4, 2x2 and pixel levels (Sec. 4.4) drops no contributor: without early
+    """Culling at the 4x4, 2x2 and pixel levels (Sec. 3.4) drops no contributor: without early
     termination every pixel blends exactly the Gaussians a full per-ray sort blends."""
     sc, cams, prm = I.plain_forward_workload()
     prm = dataclasses.replace(prm, t_min=1e-30)
@@ -287,7 +287,7 @@ def test_hier_blends_the_same_set_as_full_sort(oracle):
     assert np.array_equal(hs, fs)
 
 
-# --------------------------------------------------------------------- Sec. 4.4 schedule
+# --------------------------------------------------------------------- Sec. 3.4 schedule
 def _late(n, src, D):
     order = list(range(n))
     x = order.pop(src)
@@ -296,7 +296,7 @@ def _late(n, src, D):
 
 
 def test_hier_window_is_25_in_the_worst_case(oracle):
-    """Sec. 4.4: the effective window is at least 25 (tail drained to 17 plus 4 in mid and 4 in
+    """Sec. 3.4: the effective window is at least 25 (tail drained to 17 plus 4 in mid and 4 in
     head). Worst case: 32 survivors, then 17 survivors (15 culled) drain the tail to 17; an entry
     arriving 25 survivor positions late is still sorted, 26 is not."""
     def case(disp):
@@ -334,7 +334,7 @@ def test_hier_sorts_any_list_displaced_by_at_most_25(oracle):
 
 @pytest.mark.parametrize("k", [4, 8, 16, 24])
 def test_resort_window_k(oracle, k):
-    """Sec. 4.3: a k-buffer of size k blends the smallest on overflow, so an entry arriving
+    """Sec. 3.3: a k-buffer of size k blends the smallest on overflow, so an entry arriving
     up to k positions late is placed correctly and k+1 is not."""
     n = 80
     ok = [bool(np.all(np.diff(t[oracle.schedule_synthetic(t, None, mode=I.MODE_WINDOW, head=k)]) >= 0))
@@ -355,7 +355,7 @@ def test_layered_scene_all_orderings_agree(oracle):
 
 
 def test_sort_error_full_is_zero_and_hier_beats_small_windows(oracle):
-    """Sec. 4.3 / Tab. sortcost: full per-ray sort has delta = 0; the hierarchical order has a
+    """Sec. 3.3 / Tab. sortcost: full per-ray sort has delta = 0; the hierarchical order has a
     smaller sort error than a resort window of 4 (trend of the table, on a synthetic scene)."""
     sc = I.cluster_scene(20000, 31, nclusters=8, centre_range=1.0, scale_range=(0.005, 0.1))
     cam = I.look_at((0, 0.5, -6), (0, 0, 0), (0, 1, 0), 128, 128, 50.0)
@@ -369,7 +369,7 @@ def test_sort_error_full_is_zero_and_hier_beats_small_windows(oracle):
 
 
 def test_tile_depth_adjustment_reduces_sort_error(oracle):
-    """Sec. 4.4 "Tile-depth adjustment": a tile key from t_opt on the ray through x_hat sorts
+    """Sec. 3.4 "Tile-depth adjustment": a tile key from t_opt on the ray through x_hat sorts
     better than the key from the tile-centre ray (the paper: (1.553, 0.006) -> (0.575, 0.003))
     and better than 3DGS's view-space depth of the mean (ablation B)."""
     sc = I.cluster_scene(20000, 32, nclusters=8, centre_range=1.0, scale_range=(0.005, 0.15))
@@ -396,7 +396,7 @@ def test_input_order_does_not_matter(oracle):
     assert np.array_equal(sa, sb)
 
 
-# --------------------------------------------------------------------- Sec. 4.5 adjoint
+# --------------------------------------------------------------------- Sec. 3.5 adjoint
 def _scene64(sc):
     return I.Scene(sc.means.astype(np.float64), sc.log_scales.astype(np.float64),
                    sc.quats.astype(np.float64), sc.opacity_logits.astype(np.float64),
@@ -404,7 +404,7 @@ def _scene64(sc):
 
 
 def test_adjoint_matches_central_differences(oracle):
-    """Front-to-back adjoint with C - C_i and T_N / T_i (Sec. 4.5) chained through the
+    """Front-to-back adjoint with C - C_i and T_N / T_i (Sec. 3.5) chained through the
     preprocess, against FP64 central differences of L = <w, rgb> + <wz, depth>; parameters
     whose +-h perturbation changes any blend decision are skipped."""
     sc, _, cam, prm = I.fd_subcase()
