@@ -193,6 +193,24 @@ stp_status stp_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint
                           uint32_t* vals_out, int64_t n, const uint64_t* n_dev, int32_t key_bits,
                           void* temp, size_t temp_bytes, void* stream);
 
+/* The same sort for callers that cannot allocate device memory: code recording into a CUDA
+ * graph under stream capture, plugins whose host framework owns the device memory pool, and
+ * loops that must not allocate after start-up. It takes no scratch argument and allocates
+ * nothing: its scratch is a fixed device array inside the library, sized for at most
+ * STP_SORT_STATIC_MAX_N pairs (12.25 MiB, held by every GPU that loads the library until the
+ * process exits). The paper has no counterpart; this is a deployment variant of
+ * stp_sort_pairs with the same arguments minus temp and the same results.
+ *   - n > STP_SORT_STATIC_MAX_N is rejected with STP_ERR_ARG before any work.
+ *   - The first call on a device looks up the array's device address (once per device,
+ *     with that device current); make that first call before any stream capture.
+ *   - All calls share the array: calls whose work overlaps on the GPU (other streams, other
+ *     host threads) race and must be serialised by the caller. Nothing in the array needs
+ *     to start at zero.                                                                    */
+#define STP_SORT_STATIC_MAX_N 1048576
+stp_status stp_sort_pairs_noalloc(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
+                                  uint32_t* vals_out, int64_t n, const uint64_t* n_dev, int32_t key_bits,
+                                  void* stream);
+
 /* Stage timing with CUDA events (Sec. 4.3 reports per-stage times). After
  * stp_profile_enable(max_calls), each stp_render / stp_render_backward call on this host
  * thread records STP_NUM_STAGE_EVENTS events on its stream into the next of max_calls slots

@@ -19,6 +19,7 @@ STP_OK, STP_ERR_ARG, STP_ERR_CAPACITY, STP_ERR_TIMEOUT, STP_ERR_CUDA, STP_ERR_NO
 FLAG_DEBUG_STATS = 32
 FLAG_BACKWARD = 64
 FLAG_DEBUG_TRACE = 128
+SORT_STATIC_MAX_N = 1 << 20
 TRACE_LEN = 64
 
 
@@ -80,7 +81,8 @@ class Layout(C.Structure):
 
 # every symbol include/stp.h declares (the CPU tests check the library exports them)
 EXPORTS = ["stp_workspace_size", "stp_workspace_layout_get", "stp_render", "stp_render_backward",
-           "stp_read_status", "stp_sort_temp_bytes", "stp_sort_pairs", "stp_profile_enable",
+           "stp_read_status", "stp_sort_temp_bytes", "stp_sort_pairs", "stp_sort_pairs_noalloc",
+           "stp_profile_enable",
            "stp_profile_read", "stp_last_error", "stp_version"]
 
 NUM_STAGES = 8
@@ -110,6 +112,8 @@ def lib():
         L.stp_sort_temp_bytes.argtypes = [C.c_int64]
         L.stp_sort_pairs.restype = C.c_int
         L.stp_sort_pairs.argtypes = [vp, vp, vp, vp, C.c_int64, vp, C.c_int32, vp, sz, vp]
+        L.stp_sort_pairs_noalloc.restype = C.c_int
+        L.stp_sort_pairs_noalloc.argtypes = [vp, vp, vp, vp, C.c_int64, vp, C.c_int32, vp]
         L.stp_profile_enable.restype = C.c_int
         L.stp_profile_enable.argtypes = [C.c_int32]
         L.stp_profile_read.restype = C.c_int

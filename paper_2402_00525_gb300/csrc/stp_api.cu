@@ -431,4 +431,20 @@ stp_status stp_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint
     return STP_OK;
 }
 
+stp_status stp_sort_pairs_noalloc(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
+                                  uint32_t* vals_out, int64_t n, const uint64_t* n_dev, int32_t key_bits,
+                                  void* stream)
+{
+    g_err.clear();
+    if (n < 0 || n > stp::sort_static_max_n())
+        return fail(STP_ERR_ARG, "stp_sort_pairs_noalloc: n = %lld exceeds the fixed scratch of %lld pairs",
+                    (long long)n, stp::sort_static_max_n());
+    if (key_bits < 1 || key_bits > 64) return fail(STP_ERR_ARG, "key_bits must be in 1..64");
+    if (n > 0 && (!keys_in || !vals_in || !keys_out || !vals_out)) return fail(STP_ERR_ARG, "null array");
+    cudaError_t e = stp::sort_pairs_static(keys_in, vals_in, keys_out, vals_out, n,
+                                           (const unsigned long long*)n_dev, key_bits, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sort (static scratch)");
+    return STP_OK;
+}
+
 }  // extern "C"

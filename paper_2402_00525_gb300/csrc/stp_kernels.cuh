@@ -85,5 +85,8 @@ size_t sort_temp_bytes(long long n);
 cudaError_t sort_pairs(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout,
                        long long n, const unsigned long long* n_dev, int key_bits, void* temp,
                        size_t temp_bytes, cudaStream_t s);
+long long sort_static_max_n();
+cudaError_t sort_pairs_static(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout,
+                              long long n, const unsigned long long* n_dev, int key_bits, cudaStream_t s);
 
 }  // namespace stp

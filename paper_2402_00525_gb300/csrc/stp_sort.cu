@@ -15,6 +15,8 @@
 // memory, so the whole sequence needs no host synchronisation and can be graph-captured.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "stp_common.cuh"
 #include "stp_kernels.cuh"
 
@@ -216,20 +218,16 @@ static void sort_pass(const uint64_t* sk, const uint32_t* sv, uint64_t* dk, uint
     k_scatter<<<G, kThreads, 0, s>>>(sk, sv, dk, dv, n, n_dev, shift, hist, G);
 }
 
-// Library sort: input preserved, output in (kout, vout); temp holds the histogram and the
-// ping-pong partner, so the passes alternate between `out` and the partner and the last
-// pass writes `out`.
-cudaError_t sort_pairs(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout,
-                       long long n, const unsigned long long* n_dev, int key_bits, void* temp,
-                       size_t temp_bytes, cudaStream_t s)
+// Sort with explicit scratch: hist holds kRadix x grid counters, (kalt, valt) is the ping-pong
+// partner of (kout, vout). Input preserved; the passes alternate between `out` and the partner
+// and the last pass writes `out`.
+static cudaError_t sort_with(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout,
+                             long long n, const unsigned long long* n_dev, int key_bits, uint32_t* hist,
+                             uint64_t* kalt, uint32_t* valt, cudaStream_t s)
 {
-    if (temp_bytes < sort_temp_bytes(n)) return cudaErrorInvalidValue;
     const int passes = (key_bits + 7) / 8;
     if (n == 0 || passes == 0) return cudaSuccess;
     const int G = sort_grid(n);
-    uint32_t* hist = (uint32_t*)temp;
-    uint64_t* kalt = (uint64_t*)((char*)temp + sort_hist_bytes());
-    uint32_t* valt = (uint32_t*)((char*)temp + sort_hist_bytes() + align256((size_t)n * sizeof(uint64_t)));
     const uint64_t* sk = kin;
     const uint32_t* sv = vin;
     for (int p = 0; p < passes; p++) {
@@ -241,6 +239,72 @@ cudaError_t sort_pairs(const uint64_t* kin, const uint32_t* vin, uint64_t* kout,
         sv = dv;
     }
     return cudaGetLastError();
+}
+
+// Library sort: temp holds the histogram and the ping-pong partner.
+cudaError_t sort_pairs(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout,
+                       long long n, const unsigned long long* n_dev, int key_bits, void* temp,
+                       size_t temp_bytes, cudaStream_t s)
+{
+    if (temp_bytes < sort_temp_bytes(n)) return cudaErrorInvalidValue;
+    uint32_t* hist = (uint32_t*)temp;
+    uint64_t* kalt = (uint64_t*)((char*)temp + sort_hist_bytes());
+    uint32_t* valt = (uint32_t*)((char*)temp + sort_hist_bytes() + align256((size_t)n * sizeof(uint64_t)));
+    return sort_with(kin, vin, kout, vout, n, n_dev, key_bits, hist, kalt, valt, s);
+}
+
+// ---------------------------------------------------------------- sort without allocation
+// Some callers cannot hand the library a device buffer for scratch: code that records work
+// into a CUDA graph under stream capture (where a new allocation would not be part of the
+// graph), plugins running inside a host framework that owns the device memory pool, and
+// real-time loops that must not allocate (an allocation can synchronise the device) after
+// start-up. For them the sort's scratch lives in this file-scope device array of fixed size,
+// held by every GPU that loads the library until the process exits. All calls share it:
+// calls whose work overlaps on the GPU (different streams, or another host thread) race on
+// it. Nothing in it needs to start at zero: every call writes the histogram counters and the
+// ping-pong keys before it reads them.
+constexpr long long kStaticMaxN = 1LL << 20;                          // STP_SORT_STATIC_MAX_N
+constexpr long long kStaticGrid = (kStaticMaxN + kTileItems - 1) / kTileItems;
+constexpr size_t kStaticHistBytes = ((size_t)kRadix * kStaticGrid * sizeof(uint32_t) + 255) & ~(size_t)255;
+constexpr size_t kStaticKeyBytes = (size_t)kStaticMaxN * sizeof(uint64_t);
+constexpr size_t kStaticValBytes = (size_t)kStaticMaxN * sizeof(uint32_t);
+static __device__ __align__(256) unsigned char g_sort_static_scratch[kStaticHistBytes + kStaticKeyBytes + kStaticValBytes];
+
+constexpr int kMaxDevices = 64;
+static void* g_static_addr[kMaxDevices];
+static std::mutex g_static_mu;
+
+long long sort_static_max_n() { return kStaticMaxN; }
+
+// Device address of the static scratch on the current device, looked up once per device.
+cudaError_t sort_static_scratch(void** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_sort_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
+    return cudaSuccess;
+}
+
+cudaError_t sort_pairs_static(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout,
+                              long long n, const unsigned long long* n_dev, int key_bits, cudaStream_t s)
+{
+    if (n < 0 || n > kStaticMaxN || sort_grid(n) > kStaticGrid) return cudaErrorInvalidValue;
+    void* base = nullptr;
+    cudaError_t e = sort_static_scratch(&base);
+    if (e != cudaSuccess) return e;
+    uint32_t* hist = (uint32_t*)base;
+    uint64_t* kalt = (uint64_t*)((char*)base + kStaticHistBytes);
+    uint32_t* valt = (uint32_t*)((char*)base + kStaticHistBytes + kStaticKeyBytes);
+    return sort_with(kin, vin, kout, vout, n, n_dev, key_bits, hist, kalt, valt, s);
 }
 
 // Pipeline sort: Duplicate's output in buffer A = (keys_alt, vals_alt) is sorted by ping-pong
