@@ -57,8 +57,11 @@ enum {
     STP_FLAG_DEBUG_STATS = 32,       /* workspace also receives per-pixel blend count and hash */
     STP_FLAG_BACKWARD = 64,          /* workspace also holds the backward pass's scratch; the
                                         forward and backward calls must both set it          */
-    STP_FLAG_DEBUG_TRACE = 128       /* workspace also receives, per pixel, the ids of the first
+    STP_FLAG_DEBUG_TRACE = 128,      /* workspace also receives, per pixel, the ids of the first
                                         STP_TRACE_LEN blended Gaussians (-1 padded)          */
+    STP_FLAG_GLOBAL_SORT = 256       /* order the entries with one global LSD radix sort of
+                                        (tile, depth) keys instead of the default partitioned
+                                        per-tile sort (appendix B.3); same result            */
 };
 #define STP_TRACE_LEN 64
 
@@ -140,6 +143,10 @@ typedef struct {                 /* byte offsets of workspace regions (for inspe
     size_t dbg_hash;             /* [total pixels] uint64 blend-order hash (flag 32), else 0 */
     size_t grad_geom;            /* [V*N*24] float backward scratch (flag 64), else 0        */
     size_t dbg_trace;            /* [total pixels][STP_TRACE_LEN] int32 blend ids (flag 128)  */
+    size_t tile_counts;          /* [total tiles] uint32 entries per tile (partitioned sort)  */
+    size_t tile_offsets;         /* [total tiles] uint32 first entry of each tile            */
+    size_t tile_cursor;          /* [total tiles] uint32 placement cursors                   */
+    size_t tile_partials;        /* scan scratch of the tile counts                          */
     size_t total;                /* total bytes                                              */
     int64_t capacity;            /* sort-entry capacity                                      */
     int64_t total_tiles, total_pixels;

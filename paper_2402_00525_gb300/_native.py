@@ -19,6 +19,7 @@ STP_OK, STP_ERR_ARG, STP_ERR_CAPACITY, STP_ERR_TIMEOUT, STP_ERR_CUDA, STP_ERR_NO
 FLAG_DEBUG_STATS = 32
 FLAG_BACKWARD = 64
 FLAG_DEBUG_TRACE = 128
+FLAG_GLOBAL_SORT = 256
 SORT_STATIC_MAX_N = 1 << 20
 TRACE_LEN = 64
 
@@ -67,7 +68,8 @@ class RunStatus(C.Structure):
 _LAYOUT_SIZE_FIELDS = ["status", "views", "geom", "color", "rect", "counts", "offsets",
                        "scan_partials", "keys", "vals", "keys_alt", "vals_alt", "sorted_keys",
                        "sorted_vals", "ranges", "tfinal", "pix_state", "scratch", "dbg_nblend",
-                       "dbg_hash", "grad_geom", "dbg_trace", "total"]
+                       "dbg_hash", "grad_geom", "dbg_trace", "tile_counts", "tile_offsets",
+                       "tile_cursor", "tile_partials", "total"]
 
 
 class Layout(C.Structure):

@@ -63,6 +63,7 @@ stp_status cuda_fail(cudaError_t e, const char* where)
 constexpr int kFlagDebug = 32;      // per-pixel blend count / hash written to the workspace
 constexpr int kFlagBackward = 64;   // workspace also holds the backward pass's scratch
 constexpr int kFlagTrace = 128;     // per-pixel ids of the first kTraceLen blended Gaussians
+constexpr int kFlagGlobalSort = 256;  // one global LSD radix sort instead of the per-tile sort
 
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -169,9 +170,13 @@ void make_plan(int64_t n, const stp_camera* cams, int32_t nviews, const stp_para
         L.dbg_nblend = take((size_t)pixels * 4);
         L.dbg_hash = take((size_t)pixels * 8);
     }
-    const bool in_alt = stp::pipeline_sorted_in_alt(L.key_bits);
+    const bool in_alt = (p->flags & kFlagGlobalSort) && stp::pipeline_sorted_in_alt(L.key_bits);
     L.sorted_keys = in_alt ? L.keys_alt : L.keys;
     L.sorted_vals = in_alt ? L.vals_alt : L.vals;
+    L.tile_counts = take((size_t)tiles * 4);
+    L.tile_offsets = take((size_t)tiles * 4);
+    L.tile_cursor = take((size_t)tiles * 4);
+    L.tile_partials = take(stp::scan_partials_count(tiles) * 8);
     L.grad_geom = 0;
     if (p->flags & kFlagBackward) L.grad_geom = take((size_t)P.m * stp::kGradStride * 4);
     L.dbg_trace = 0;
@@ -224,6 +229,11 @@ stp::PipeArgs make_args(const stp_gaussians* g, const stp_params* p, const Plan&
     a.key_bits = L.key_bits;
     a.grad_geom = L.grad_geom ? (float*)(b + L.grad_geom) : nullptr;
     a.dbg_trace = L.dbg_trace ? (int*)(b + L.dbg_trace) : nullptr;
+    a.partitioned = (p->flags & kFlagGlobalSort) ? 0 : 1;
+    a.tile_counts = (uint32_t*)(b + L.tile_counts);
+    a.tile_offsets = (uint32_t*)(b + L.tile_offsets);
+    a.tile_cursor = (uint32_t*)(b + L.tile_cursor);
+    a.tile_partials = (unsigned long long*)(b + L.tile_partials);
     return a;
 }
 
@@ -296,16 +306,27 @@ stp_status stp_render(const stp_gaussians* g, const stp_camera* cams, int32_t nv
     k_status_init<<<1, 1, 0, s>>>(a.status, a.capacity);
     if ((e = stp::launch_views_init(P.views.data(), nviews, const_cast<stp::ViewDesc*>(a.views), s)) != cudaSuccess)
         return cuda_fail(e, "view table");
+    if (a.partitioned) {
+        if ((e = cudaMemsetAsync(a.tile_counts, 0, (size_t)a.total_tiles * 4, s)) != cudaSuccess ||
+            (e = cudaMemsetAsync(a.tile_cursor, 0, (size_t)a.total_tiles * 4, s)) != cudaSuccess)
+            return cuda_fail(e, "clear tile counters");
+    }
     prof_mark(1, s);
     if ((e = stp::launch_preprocess(a, s)) != cudaSuccess) return cuda_fail(e, "preprocess");
     prof_mark(2, s);
-    if ((e = stp::launch_scan_counts(a, s)) != cudaSuccess) return cuda_fail(e, "scan");
+    if ((e = a.partitioned ? stp::launch_scan_tiles(a, s) : stp::launch_scan_counts(a, s)) != cudaSuccess)
+        return cuda_fail(e, "scan");
     prof_mark(3, s);
     if ((e = stp::launch_duplicate(a, s)) != cudaSuccess) return cuda_fail(e, "duplicate");
     prof_mark(4, s);
-    if ((e = stp::pipeline_sort(a, s)) != cudaSuccess) return cuda_fail(e, "sort");
-    prof_mark(5, s);
-    if ((e = stp::launch_ranges(a, s)) != cudaSuccess) return cuda_fail(e, "ranges");
+    if (a.partitioned) {
+        if ((e = stp::launch_tile_sort(a, s)) != cudaSuccess) return cuda_fail(e, "tile sort");
+        prof_mark(5, s);
+    } else {
+        if ((e = stp::pipeline_sort(a, s)) != cudaSuccess) return cuda_fail(e, "sort");
+        prof_mark(5, s);
+        if ((e = stp::launch_ranges(a, s)) != cudaSuccess) return cuda_fail(e, "ranges");
+    }
     if (a.dbg_trace && (e = cudaMemsetAsync(a.dbg_trace, 0xFF, (size_t)a.total_pixels * stp::kTraceLen * 4, s)) != cudaSuccess)
         return cuda_fail(e, "clear trace");
     prof_mark(6, s);

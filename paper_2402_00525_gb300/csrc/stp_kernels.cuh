@@ -40,6 +40,11 @@ struct PipeArgs {
     const uint32_t* svals;
     unsigned long long capacity;
     uint2* ranges;           // [total_tiles]
+    int partitioned;         // 1: per-tile counting + placement + per-tile sort (appendix B.3)
+    uint32_t* tile_counts;   // [total_tiles] entries per tile (partitioned)
+    uint32_t* tile_offsets;  // [total_tiles] exclusive prefix sum of tile_counts
+    uint32_t* tile_cursor;   // [total_tiles] placement cursors
+    unsigned long long* tile_partials;
     float* tfinal_ws;        // [total_pixels]
     float* pix_state;        // [total_pixels] float4 (C without background, depth)
     uint32_t* dbg_nblend;    // [total_pixels] or null
@@ -70,6 +75,9 @@ cudaError_t launch_views_init(const ViewDesc* host_views, int nviews, ViewDesc* 
                               cudaStream_t s);
 cudaError_t launch_preprocess(const PipeArgs& a, cudaStream_t s);
 cudaError_t launch_scan_counts(const PipeArgs& a, cudaStream_t s);
+cudaError_t launch_scan_tiles(const PipeArgs& a, cudaStream_t s);
+cudaError_t launch_tile_sort(const PipeArgs& a, cudaStream_t s);
+size_t tile_sort_smem_bytes();
 cudaError_t launch_duplicate(const PipeArgs& a, cudaStream_t s);
 cudaError_t launch_ranges(const PipeArgs& a, cudaStream_t s);
 cudaError_t launch_render(const PipeArgs& a, bool backward, cudaStream_t s);

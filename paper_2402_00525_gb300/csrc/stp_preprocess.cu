@@ -10,12 +10,15 @@
 //
 // One thread per Gaussian loops over all views of the launch, so the Gaussian's parameters
 // (236 bytes at SH degree 3) are read from HBM once for every view of the batch.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "stp_common.cuh"
 #include "stp_kernels.cuh"
 
 namespace stp {
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -203,20 +206,59 @@ __device__ __forceinline__ Rec shfl_rec(const Rec& r, int src)
     return o;
 }
 
-// Key of one kept (Gaussian, tile) pair: tile in the high word, ordered depth bits low.
-__device__ __forceinline__ bool tile_key(const PipeArgs& a, const ViewDesc& V, const Rec& r,
-                                         int tx, int ty, unsigned long long* key)
+// Depth key of one (Gaussian, tile) pair if the tile is kept: ordered bits of t_opt on the ray
+// through the tile's x_hat (or the tile centre / the view-space depth, by flag).
+__device__ __forceinline__ bool tile_depth_key(const PipeArgs& a, const ViewDesc& V, const Rec& r,
+                                               int tx, int ty, uint32_t* dkey)
 {
     const Box b = block_box(tx * kTile, ty * kTile, kTile, V.W, V.H);
     float t = 0.f;
     if (!box_keep_depth(r, b, V, a.eps_o, (a.flags & 4) != 0, &t)) return false;
     if (a.flags & 8) t = r.r5.y;
-    *key = ((unsigned long long)(V.tile_off + ty * V.tiles_x + tx) << 32) | fkey(t);
+    *dkey = fkey(t);
     return true;
 }
 
+// Partitioned sort (appendix B.3): count a kept entry of global tile `gt`. Lanes of the
+// calling (possibly divergent) group that hit the same tile add once (labelled partition).
+__device__ __forceinline__ void count_entry(const PipeArgs& a, uint32_t gt, bool aggregate)
+{
+    if (!aggregate) {
+        atomicAdd(&a.tile_counts[gt], 1u);
+        return;
+    }
+    cg::coalesced_group act = cg::coalesced_threads();
+    cg::coalesced_group same = cg::labeled_partition(act, gt);
+    if (same.thread_rank() == 0) atomicAdd(&a.tile_counts[gt], same.size());
+}
+
+// Partitioned sort: place an entry in its tile's range through the tile's atomic cursor. The
+// order inside a range is arbitrary here and fixed by the per-tile sort on (depth, id).
+__device__ __forceinline__ void place_entry(const PipeArgs& a, uint32_t gt, uint32_t dkey, uint32_t gid,
+                                            bool aggregate)
+{
+    uint32_t slot;
+    if (aggregate) {
+        cg::coalesced_group act = cg::coalesced_threads();
+        cg::coalesced_group same = cg::labeled_partition(act, gt);
+        uint32_t base = 0;
+        if (same.thread_rank() == 0) base = atomicAdd(&a.tile_cursor[gt], same.size());
+        slot = same.shfl(base, 0) + same.thread_rank();
+    } else {
+        slot = atomicAdd(&a.tile_cursor[gt], 1u);
+    }
+    if (slot >= a.tile_counts[gt]) {   // more entries than Preprocess counted: cannot happen
+        atomicOr(&a.status->error_bits, 2u);
+        return;
+    }
+    const unsigned long long pos = (unsigned long long)a.tile_offsets[gt] + slot;
+    if (pos < a.capacity) a.dup_keys[pos] = ((unsigned long long)dkey << 32) | gid;
+}
+
 // Count (EMIT = false) or write (EMIT = true) the kept tiles of this lane's Gaussian, with the
-// two-phase warp load balancing. Every lane of the warp must call it.
+// two-phase warp load balancing. Every lane of the warp must call it. With the global radix
+// sort the keys go to the Gaussian's own range [off, off + want) in tile order; with the
+// partitioned sort they go to their tiles' ranges.
 template <bool EMIT>
 __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, bool has, const Rec& r,
                                ushort4 rc, uint32_t off, uint32_t want, uint32_t gid)
@@ -225,20 +267,32 @@ __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, bool has, c
     const int w = (int)rc.z - (int)rc.x, h = (int)rc.w - (int)rc.y;
     const int ncand = has ? w * h : 0;
     const bool big = ncand > a.lb_threshold && !(a.flags & 16);
+    const bool part = a.partitioned != 0;
     uint32_t cnt = 0;
     if (!big) {
         for (int k = 0; k < ncand; k++) {
             const int tx = rc.x + k % w, ty = rc.y + k / w;
+            const uint32_t gt = (uint32_t)(V.tile_off + ty * V.tiles_x + tx);
             if (EMIT) {
-                unsigned long long key;
-                if (tile_key(a, V, r, tx, ty, &key)) {
-                    const unsigned long long pos = (unsigned long long)off + cnt;
-                    if (cnt < want && pos < a.capacity) { a.dup_keys[pos] = key; a.dup_vals[pos] = gid; }
+                uint32_t dk;
+                if (tile_depth_key(a, V, r, tx, ty, &dk)) {
+                    if (part) {
+                        place_entry(a, gt, dk, gid, true);
+                    } else {
+                        const unsigned long long pos = (unsigned long long)off + cnt;
+                        if (cnt < want && pos < a.capacity) {
+                            a.dup_keys[pos] = ((unsigned long long)gt << 32) | dk;
+                            a.dup_vals[pos] = gid;
+                        }
+                    }
                     cnt++;
                 }
             } else {
                 const Box b = block_box(tx * kTile, ty * kTile, kTile, V.W, V.H);
-                cnt += box_keep(r, b, a.eps_o) ? 1u : 0u;
+                if (box_keep(r, b, a.eps_o)) {
+                    cnt++;
+                    if (part) count_entry(a, gt, true);
+                }
             }
         }
     }
@@ -255,17 +309,29 @@ __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, bool has, c
         for (int k0 = 0; k0 < nc; k0 += 32) {
             const int k = k0 + lane;
             bool keep = false;
-            unsigned long long key = 0;
+            uint32_t dk = 0, gt = 0;
             if (k < nc) {
                 const int tx = x0 + k % ws, ty = y0 + k / ws;
-                if (EMIT) keep = tile_key(a, V, rs, tx, ty, &key);
+                gt = (uint32_t)(V.tile_off + ty * V.tiles_x + tx);
+                if (EMIT) keep = tile_depth_key(a, V, rs, tx, ty, &dk);
                 else keep = box_keep(rs, block_box(tx * kTile, ty * kTile, kTile, V.W, V.H), a.eps_o);
             }
             const unsigned m = __ballot_sync(kFull, keep);
-            if (EMIT && keep) {
-                const uint32_t rank = base + __popc(m & lanemask_lt());
-                const unsigned long long pos = (unsigned long long)offs + rank;
-                if (rank < wants && pos < a.capacity) { a.dup_keys[pos] = key; a.dup_vals[pos] = gids; }
+            if (keep) {
+                if (EMIT) {
+                    if (part) {
+                        place_entry(a, gt, dk, gids, false);
+                    } else {
+                        const uint32_t rank = base + __popc(m & lanemask_lt());
+                        const unsigned long long pos = (unsigned long long)offs + rank;
+                        if (rank < wants && pos < a.capacity) {
+                            a.dup_keys[pos] = ((unsigned long long)gt << 32) | dk;
+                            a.dup_vals[pos] = gids;
+                        }
+                    }
+                } else if (part) {
+                    count_entry(a, gt, false);
+                }
             }
             base += __popc(m);
         }
@@ -319,7 +385,7 @@ __global__ void __launch_bounds__(256) k_duplicate(PipeArgs a)
             r.r0 = r.r1 = r.r2 = r.r3 = r.r4 = r.r5 = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         const uint32_t got = tiles_pass<true>(a, V, live && want > 0, r, rc, off, want, (uint32_t)i);
-        if (live && got != want) {
+        if (live && got != want && !a.partitioned) {
             // Preprocess and Duplicate disagree (cannot happen with the shared rounding of the
             // decision arithmetic; kept as the paper's safety net, appendix B.4): pad with
             // dummy keys that sort behind every tile.
@@ -449,14 +515,24 @@ cudaError_t launch_preprocess(const PipeArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+static cudaError_t scan_u32(const uint32_t* in, uint32_t* out, unsigned long long* partials, long long m,
+                            Status* st, cudaStream_t s)
+{
+    const int nb = (int)((m + kScanTile - 1) / kScanTile);
+    if (nb > 0) k_scan_reduce<<<nb, kScanThreads, 0, s>>>(in, m, partials);
+    k_scan_partials<<<1, 1024, 0, s>>>(partials, nb, st);
+    if (nb > 0) k_scan_apply<<<nb, kScanThreads, 0, s>>>(in, m, partials, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_scan_counts(const PipeArgs& a, cudaStream_t s)
 {
-    const long long m = (long long)a.n * a.nviews;
-    const int nb = (int)((m + kScanTile - 1) / kScanTile);
-    if (nb > 0) k_scan_reduce<<<nb, kScanThreads, 0, s>>>(a.counts, m, a.scan_partials);
-    k_scan_partials<<<1, 1024, 0, s>>>(a.scan_partials, nb, a.status);
-    if (nb > 0) k_scan_apply<<<nb, kScanThreads, 0, s>>>(a.counts, m, a.scan_partials, a.offsets);
-    return cudaGetLastError();
+    return scan_u32(a.counts, a.offsets, a.scan_partials, (long long)a.n * a.nviews, a.status, s);
+}
+
+cudaError_t launch_scan_tiles(const PipeArgs& a, cudaStream_t s)
+{
+    return scan_u32(a.tile_counts, a.tile_offsets, a.tile_partials, (long long)a.total_tiles, a.status, s);
 }
 
 cudaError_t launch_duplicate(const PipeArgs& a, cudaStream_t s)

@@ -200,6 +200,146 @@ int sort_grid(long long n)
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// ---------------------------------------------------------------- partitioned per-tile sort
+// Appendix B.3's alternative to the global sort: Preprocess counted the entries of every tile
+// with atomics, a scan gave each tile its range, and Duplicate placed (depth << 32 | id) words
+// into the ranges through atomic cursors. One block per tile now sorts its range by depth
+// with four stable 8-bit passes and orders equal depths by Gaussian id, which reproduces the
+// stable global sort exactly (ties by id), independently of the atomic placement order.
+// Ranges of at most kSegCap entries are sorted in shared memory; longer ones in place in global
+// memory (the second buffer of the range serves as the ping-pong partner).
+constexpr int kSegThreads = 256, kSegWarps = kSegThreads / 32, kSegCap = 4096;
+
+__device__ __forceinline__ uint32_t seg_digit(unsigned long long x, int shift)
+{
+    return (uint32_t)(x >> (32 + shift)) & (kRadix - 1);
+}
+
+// one stable counting pass of n words from src to dst by the depth digit at `shift`
+__device__ void seg_pass(const unsigned long long* src, unsigned long long* dst, int n, int shift,
+                         uint32_t (*whist)[kRadix], uint32_t* dtot)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int chunk = (n + kSegWarps - 1) / kSegWarps;
+    const int beg = min(n, warp * chunk), end = min(n, beg + chunk);
+    const unsigned lt = lanemask_lt();
+    for (int d = lane; d < kRadix; d += 32) whist[warp][d] = 0;
+    __syncwarp();
+    for (int i0 = beg; i0 < end; i0 += 32) {
+        const int i = i0 + lane;
+        const uint32_t d = i < end ? seg_digit(src[i], shift) : (uint32_t)kRadix;
+        const unsigned m = __match_any_sync(kFull, d);
+        if (d < kRadix && (m & lt) == 0) whist[warp][d] += __popc(m);
+        __syncwarp();
+    }
+    __syncthreads();
+    {   // offsets of (digit, warp): digit-major exclusive scan
+        const int d = threadIdx.x;
+        uint32_t tot = 0;
+        for (int w = 0; w < kSegWarps; w++) tot += whist[w][d];
+        dtot[d] = tot;
+        __syncthreads();
+        if (threadIdx.x < 32) {   // exclusive scan of the 256 digit totals by one warp
+            uint32_t v[kRadix / 32], run = 0;
+            for (int k = 0; k < kRadix / 32; k++) {
+                v[k] = dtot[lane * (kRadix / 32) + k];
+                run += v[k];
+            }
+            uint32_t inc = run;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, inc, o);
+                if (lane >= o) inc += y;
+            }
+            uint32_t base = inc - run;
+            for (int k = 0; k < kRadix / 32; k++) {
+                dtot[lane * (kRadix / 32) + k] = base;
+                base += v[k];
+            }
+        }
+        __syncthreads();
+        uint32_t run = dtot[d];
+        for (int w = 0; w < kSegWarps; w++) {
+            const uint32_t c = whist[w][d];
+            whist[w][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int i0 = beg; i0 < end; i0 += 32) {
+        const int i = i0 + lane;
+        const unsigned long long x = i < end ? src[i] : 0ull;
+        const uint32_t d = i < end ? seg_digit(x, shift) : (uint32_t)kRadix;
+        const unsigned m = __match_any_sync(kFull, d);
+        const uint32_t rank = __popc(m & lt);
+        const uint32_t base = d < kRadix ? whist[warp][d] : 0u;
+        if (d < kRadix) dst[base + rank] = x;
+        __syncwarp();
+        if (d < kRadix && rank == 0) whist[warp][d] = base + __popc(m);
+        __syncwarp();
+    }
+    __syncthreads();
+}
+
+// order runs of equal depth by Gaussian id (the low word)
+__device__ void seg_fix_ties(unsigned long long* x, int n)
+{
+    for (int i = threadIdx.x; i < n; i += kSegThreads) {
+        const uint32_t hi = (uint32_t)(x[i] >> 32);
+        const bool start = (i == 0 || (uint32_t)(x[i - 1] >> 32) != hi) && i + 1 < n && (uint32_t)(x[i + 1] >> 32) == hi;
+        if (!start) continue;
+        int j = i + 1;
+        while (j < n && (uint32_t)(x[j] >> 32) == hi) j++;
+        for (int a = i + 1; a < j; a++) {
+            const unsigned long long v = x[a];
+            int b = a - 1;
+            while (b >= i && x[b] > v) {
+                x[b + 1] = x[b];
+                b--;
+            }
+            x[b + 1] = v;
+        }
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kSegThreads) k_tile_sort(PipeArgs a)
+{
+    extern __shared__ unsigned long long seg_smem[];
+    __shared__ uint32_t whist[kSegWarps][kRadix];
+    __shared__ uint32_t dtot[kRadix];
+    const int t = blockIdx.x;
+    if (a.status->error_bits & 1u) {
+        if (threadIdx.x == 0) a.ranges[t] = make_uint2(0u, 0u);
+        return;
+    }
+    const uint32_t cnt = a.tile_counts[t];
+    const uint32_t n = min(a.tile_cursor[t], cnt);
+    const uint32_t off = a.tile_offsets[t];
+    if (threadIdx.x == 0) a.ranges[t] = make_uint2(off, off + n);
+    if (n == 0) return;
+    unsigned long long* g0 = (unsigned long long*)a.dup_keys + off;   // placed words (buffer A)
+    unsigned long long* g1 = (unsigned long long*)a.keys + off;   // partner (buffer B)
+    unsigned long long* x;
+    if (n <= (uint32_t)kSegCap) {
+        unsigned long long* s0 = seg_smem;
+        unsigned long long* s1 = seg_smem + kSegCap;
+        for (uint32_t i = threadIdx.x; i < n; i += kSegThreads) s0[i] = g0[i];
+        __syncthreads();
+        for (int p = 0; p < 4; p++) seg_pass(p % 2 ? s1 : s0, p % 2 ? s0 : s1, (int)n, 8 * p, whist, dtot);
+        x = s0;
+    } else {
+        for (int p = 0; p < 4; p++) seg_pass(p % 2 ? g1 : g0, p % 2 ? g0 : g1, (int)n, 8 * p, whist, dtot);
+        x = g0;
+    }
+    seg_fix_ties(x, (int)n);
+    const unsigned long long hi = (unsigned long long)t << 32;
+    for (uint32_t i = threadIdx.x; i < n; i += kSegThreads) {
+        const unsigned long long v = x[i];
+        a.keys[off + i] = hi | (v >> 32);
+        a.vals[off + i] = (uint32_t)v;
+    }
+}
+
 }  // namespace
 
 size_t sort_hist_bytes() { return align256((size_t)kRadix * kMaxGrid * sizeof(uint32_t)); }
@@ -325,6 +465,17 @@ cudaError_t pipeline_sort(const PipeArgs& a, cudaStream_t s)
         sort_pass(even ? a.keys_alt : a.keys, even ? a.vals_alt : a.vals, even ? a.keys : a.keys_alt,
                   even ? a.vals : a.vals_alt, n, n_dev, 8 * p, hist, G, s);
     }
+    return cudaGetLastError();
+}
+
+size_t tile_sort_smem_bytes() { return (size_t)2 * kSegCap * sizeof(unsigned long long); }
+
+cudaError_t launch_tile_sort(const PipeArgs& a, cudaStream_t s)
+{
+    if (a.total_tiles == 0) return cudaSuccess;
+    const size_t smem = tile_sort_smem_bytes();
+    cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_tile_sort<<<a.total_tiles, kSegThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -39,6 +39,8 @@ FLAG_HEAD_EVICT_FIRST = 1      # head queue: blend the front before inserting (a
 FLAG_LEVEL_CENTRE_RAYS = 2     # 4x4 / 2x2 depth from the level-centre ray instead of its x_hat
 FLAG_TILE_CENTRE_KEY = 4       # tile sort key from the tile-centre ray (no tile-depth adjustment)
 FLAG_VIEW_DEPTH_KEY = 8        # tile sort key = view-space depth of the mean (3DGS global depth)
+FLAG_NO_LOAD_BALANCE = 16      # every Gaussian's tiles handled by its own thread
+FLAG_GLOBAL_SORT = 256         # one global radix sort of (tile, depth) keys (same order)
 
 
 @dataclasses.dataclass
