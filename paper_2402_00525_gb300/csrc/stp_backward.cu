@@ -103,9 +103,9 @@ __global__ void __launch_bounds__(128) k_backward_pre(PipeArgs a)
         const long long ri = V.rec_off + i;
         if (a.geom[kRecFloat4 * ri + 2].x == 0.f) continue;      // invisible in this view
         const float* gg = a.grad_geom + ri * kGradStride;
-        float g[21];
+        float g[24];
         bool nz = false;
-        for (int k = 0; k < 21; k++) {
+        for (int k = 0; k < 24; k++) {
             g[k] = gg[k];
             nz |= g[k] != 0.f;
         }
@@ -194,16 +194,16 @@ __global__ void __launch_bounds__(128) k_backward_pre(PipeArgs a)
         dp[2] -= (g[0] * V.fx * p[0] + g[1] * V.fy * p[1]) * iz2;
         // depth factors: m_k = si_k R_c Rq e_k, c_k = m_k . p
         bool depth_nz = false;
-        for (int k = 9; k < 21; k++) depth_nz |= g[k] != 0.f;
+        for (int k = 12; k < 24; k++) depth_nz |= g[k] != 0.f;
         if (depth_nz) {
             for (int k = 0; k < 3; k++) {
                 float mk[3];   // camera-space axis k (unscaled)
                 for (int r = 0; r < 3; r++) mk[r] = V.R[3 * r] * Rq[0][k] + V.R[3 * r + 1] * Rq[1][k] + V.R[3 * r + 2] * Rq[2][k];
-                const float dc = g[18 + k];
+                const float dc = g[21 + k];
                 float dm[3];
                 for (int r = 0; r < 3; r++) {
                     dp[r] += dc * si[k] * mk[r];
-                    dm[r] = g[9 + 3 * k + r] + dc * p[r];
+                    dm[r] = g[12 + 3 * k + r] + dc * p[r];
                 }
                 // world-space gradient of the unscaled axis and of the scale factor
                 float gw[3];

@@ -107,7 +107,7 @@ __device__ __forceinline__ float quad_form(const Rec& r, float dx, float dy)
 // opacity * G2 at offset D (Sec. 2.1: alpha = opacity times the 2D splat)
 __device__ __forceinline__ float splat_at(const Rec& r, float dx, float dy)
 {
-    return __fmul_rn(rec_opacity(r), expf(__fmul_rn(-0.5f, quad_form(r, dx, dy))));
+    return __fmul_rn(rec_opacity(r), __expf(__fmul_rn(-0.5f, quad_form(r, dx, dy))));
 }
 __device__ __forceinline__ float splat_value(const Rec& r, float x, float y)
 {
@@ -139,27 +139,29 @@ __device__ __forceinline__ float2 box_max_offset(const Rec& r, float x0, float x
     if (!inx) {     // search along the y-edge x = px: minimise q(p + t (0, ey))
         const float Ayy = __fmaf_rn(r.r1.z, __fmul_rn(r.r1.y, r.r1.y), __fmul_rn(r.r1.w, __fmul_rn(r.r1.x, r.r1.x)));
         const float den = __fmul_rn(ey, Ayy);
-        ty = den != 0.f ? fminf(1.f, fmaxf(0.f, __fdiv_rn(-Apy, den))) : 0.f;
+        ty = den != 0.f ? fminf(1.f, fmaxf(0.f, __fdividef(-Apy, den))) : 0.f;
     }
     if (!iny) {     // search along the x-edge y = py
         const float Axx = __fmaf_rn(r.r1.z, __fmul_rn(r.r1.x, r.r1.x), __fmul_rn(r.r1.w, __fmul_rn(r.r1.y, r.r1.y)));
         const float den = __fmul_rn(ex, Axx);
-        tx = den != 0.f ? fminf(1.f, fmaxf(0.f, __fdiv_rn(-Apx, den))) : 0.f;
+        tx = den != 0.f ? fminf(1.f, fmaxf(0.f, __fdividef(-Apx, den))) : 0.f;
     }
     return make_float2(__fmaf_rn(tx, ex, px), __fmaf_rn(ty, ey, py));
 }
 
-// t_opt on the ray through camera-normalised coordinates (u, w) = ((x-cx)/fx, (y-cy)/fy)
-__device__ __forceinline__ float depth_uv(const Rec& r, float u, float w)
+// t_opt on the ray through camera-normalised coordinates (u, w) = ((x-cx)/fx, (y-cy)/fy),
+// n = |(u, w, 1)| (precomputed for a pixel's own ray)
+__device__ __forceinline__ float depth_uvn(const Rec& r, float u, float w, float n)
 {
     const float a0 = __fmaf_rn(r.r3.x, u, __fmaf_rn(r.r3.y, w, r.r3.z));
     const float a1 = __fmaf_rn(r.r3.w, u, __fmaf_rn(r.r4.x, w, r.r4.y));
     const float a2 = __fmaf_rn(r.r4.z, u, __fmaf_rn(r.r4.w, w, r.r5.x));
     const float num = __fmaf_rn(a0, r.r2.y, __fmaf_rn(a1, r.r2.z, __fmul_rn(a2, r.r2.w)));
     const float den = __fmaf_rn(a0, a0, __fmaf_rn(a1, a1, __fmul_rn(a2, a2)));
-    const float n = __fsqrt_rn(__fmaf_rn(u, u, __fmaf_rn(w, w, 1.f)));
-    return __fmul_rn(n, __fdiv_rn(num, den));
+    return __fmul_rn(n, __fdividef(num, den));
 }
+__device__ __forceinline__ float ray_norm(float u, float w) { return __fsqrt_rn(__fmaf_rn(u, u, __fmaf_rn(w, w, 1.f))); }
+__device__ __forceinline__ float depth_uv(const Rec& r, float u, float w) { return depth_uvn(r, u, w, ray_norm(u, w)); }
 
 __device__ __forceinline__ float to_u(const ViewDesc& V, float x) { return __fmul_rn(__fsub_rn(x, V.cx), V.ifx); }
 __device__ __forceinline__ float to_w(const ViewDesc& V, float y) { return __fmul_rn(__fsub_rn(y, V.cy), V.ify); }

@@ -69,7 +69,7 @@ struct PipeArgs {
 };
 
 constexpr int kTraceLen = 64;
-constexpr int kGradStride = 24;   // dmean2(2) dconic(3) dopacity(1) dcolor(3) dm(9) dc(3) pad(3)
+constexpr int kGradStride = 24;   // dmean2(2) dconic(3) dopacity(1) dcolour(3) pad(3) dm(9) dc(3)
 
 cudaError_t launch_views_init(const ViewDesc* host_views, int nviews, ViewDesc* dev_views,
                               cudaStream_t s);

@@ -61,7 +61,7 @@ struct Px {
 
 struct PixCtx {
     float xc, yc;                // pixel centre
-    float u, w;                  // camera-normalised coordinates of the centre
+    float u, w, n;               // camera-normalised coordinates of the centre, |(u, w, 1)|
     long long pix;               // packed pixel index, -1 outside the image
     float g0, g1, g2, gz, gbg;   // backward: dL/drgb, dL/ddepth, <dL/drgb, bg>
     float Cf0, Cf1, Cf2, Zf, Tf; // backward: final colour (no background), depth, T
@@ -87,15 +87,17 @@ __device__ __forceinline__ void blend(const PipeArgs& a, const ViewDesc& V, Px<H
     s.C2 += col.z * wgt;
     s.Z += t * wgt;
     if (BWD) {
+        // per-(view, Gaussian) scratch, 24 floats: [0..7] (dmean2.xy, dA00, dA01, dA11,
+        // dopacity, dcolour.rg), [8] dcolour.b, [12..23] depth factors (dm_k 9, dc_k 3);
+        // accumulated with vector reductions (red.global.add.v4.f32)
         float* gg = a.grad_geom + ri * kGradStride;
-        atomicAdd(gg + 6, c.g0 * wgt);
-        atomicAdd(gg + 7, c.g1 * wgt);
-        atomicAdd(gg + 8, c.g2 * wgt);
         const float inv = 1.f / (1.f - alpha);
         float da = c.g0 * (col.x * s.T - (c.Cf0 - s.C0) * inv) + c.g1 * (col.y * s.T - (c.Cf1 - s.C1) * inv) +
                    c.g2 * (col.z * s.T - (c.Cf2 - s.C2) * inv) - c.gbg * c.Tf * inv;
         da += c.gz * (t * s.T - (c.Zf - s.Z) * inv);
         const Rec r = load_rec(a.geom, ri);
+        float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 q1 = make_float4(0.f, 0.f, c.g0 * wgt, c.g1 * wgt);
         if (val < a.alpha_max) {
             const float dx = off_x(r, c.xc), dy = off_y(r, c.yc);
             const float o = rec_opacity(r);
@@ -103,33 +105,32 @@ __device__ __forceinline__ void blend(const PipeArgs& a, const ViewDesc& V, Px<H
             // conic entries (A00, A01, A11) from the eigen form
             const float ex = r.r1.x, ey = r.r1.y, l0 = r.r1.z, l1 = r.r1.w;
             const float A00 = l0 * ex * ex + l1 * ey * ey, A01 = (l0 - l1) * ex * ey, A11 = l0 * ey * ey + l1 * ex * ex;
-            atomicAdd(gg + 5, da * G);
             const float dGG = da * o * G;
-            atomicAdd(gg + 2, dGG * (-0.5f * dx * dx));
-            atomicAdd(gg + 3, dGG * (-dx * dy));
-            atomicAdd(gg + 4, dGG * (-0.5f * dy * dy));
-            atomicAdd(gg + 0, dGG * (A00 * dx + A01 * dy));
-            atomicAdd(gg + 1, dGG * (A01 * dx + A11 * dy));
+            q0 = make_float4(dGG * (A00 * dx + A01 * dy), dGG * (A01 * dx + A11 * dy), dGG * (-0.5f * dx * dx),
+                             dGG * (-dx * dy));
+            q1.x = dGG * (-0.5f * dy * dy);
+            q1.y = da * G;
         }
+        atomicAdd(reinterpret_cast<float4*>(gg), q0);
+        atomicAdd(reinterpret_cast<float4*>(gg + 4), q1);
+        atomicAdd(gg + 8, c.g2 * wgt);
         if (c.gz != 0.f) {
             // t = |d| N / D with a_k = m_k . d, N = sum a_k c_k, D = sum a_k^2 (record layout)
             const float u = c.u, w = c.w;
             const float m[3][3] = {{r.r3.x, r.r3.y, r.r3.z}, {r.r3.w, r.r4.x, r.r4.y}, {r.r4.z, r.r4.w, r.r5.x}};
             const float cc[3] = {r.r2.y, r.r2.z, r.r2.w};
-            float ak[3];
+            float ak[3], dak[3];
             for (int k = 0; k < 3; k++) ak[k] = m[k][0] * u + m[k][1] * w + m[k][2];
             const float num = ak[0] * cc[0] + ak[1] * cc[1] + ak[2] * cc[2];
             const float den = ak[0] * ak[0] + ak[1] * ak[1] + ak[2] * ak[2];
             const float n = sqrtf(u * u + w * w + 1.f);
             const float dt = c.gz * wgt;
             const float tq = num / den;
-            for (int k = 0; k < 3; k++) {
-                const float da_k = dt * n * (cc[k] - 2.f * tq * ak[k]) / den;   // dt/da_k
-                atomicAdd(gg + 9 + 3 * k, da_k * u);
-                atomicAdd(gg + 10 + 3 * k, da_k * w);
-                atomicAdd(gg + 11 + 3 * k, da_k);
-                atomicAdd(gg + 18 + k, dt * n * ak[k] / den);                    // dt/dc_k
-            }
+            for (int k = 0; k < 3; k++) dak[k] = dt * n * (cc[k] - 2.f * tq * ak[k]) / den;   // dt/da_k
+            const float fc = dt * n / den;                                                   // dt/dc_k = fc a_k
+            atomicAdd(reinterpret_cast<float4*>(gg + 12), make_float4(dak[0] * u, dak[0] * w, dak[0], dak[1] * u));
+            atomicAdd(reinterpret_cast<float4*>(gg + 16), make_float4(dak[1] * w, dak[1], dak[2] * u, dak[2] * w));
+            atomicAdd(reinterpret_cast<float4*>(gg + 20), make_float4(dak[2], fc * ak[0], fc * ak[1], fc * ak[2]));
         }
     }
     if (!BWD && a.dbg_trace && s.nbl < (uint32_t)kTraceLen) a.dbg_trace[c.pix * kTraceLen + s.nbl] = (int)id;
@@ -211,7 +212,7 @@ __device__ __forceinline__ void headstage(const PipeArgs& a, const ViewDesc& V, 
             const float val = splat_value(r, c.xc, c.yc);
             if (a.dbg_nblend != nullptr && !BWD) atomicAdd(&a.status->counters[4], 1ull);
             if (fminf(a.alpha_max, val) >= a.eps_o) {
-                const float t = depth_uv(r, c.u, c.w);
+                const float t = depth_uvn(r, c.u, c.w, c.n);
                 head_push<HEAD, BWD>(a, V, s, c, depth_key(t), gid, val, evict_first);
             }
         }
@@ -229,12 +230,15 @@ __device__ void midstage(const PipeArgs& a, const ViewDesc& V, Px<HEAD>& s, cons
     const int cmax = max(c0, c1);
     const int MID = a.mid;
     const bool centre = (a.flags & 2) != 0;
+    // a quad whose four pixels are saturated takes no further part (its results are final)
+    const unsigned live = __ballot_sync(kFull, !s.done);
+    const bool qlive = qval && ((live >> qbase) & 0xFu) != 0;
     for (int j0 = 0; j0 < cmax; j0 += 4) {
         const int e = j0 + pq;
         uint32_t key = kInvalidKey, gid = 0;
         if (e < cnt) {
             gid = chunk[e].y;
-            if (qval) {
+            if (qlive) {
                 const Rec r = load_rec(a.geom, V.rec_off + gid);
                 const Box bq = bQ;
                 float t;
@@ -359,6 +363,7 @@ __global__ void __launch_bounds__(256) k_render(PipeArgs a)
     c.yc = pyi + 0.5f;
     c.u = to_u(V, c.xc);
     c.w = to_w(V, c.yc);
+    c.n = ray_norm(c.u, c.w);
     c.pix = inside ? V.pix_off + (long long)pyi * W + pxi : -1;
     c.g0 = c.g1 = c.g2 = c.gz = c.gbg = 0.f;
     c.Cf0 = c.Cf1 = c.Cf2 = c.Zf = c.Tf = 0.f;
@@ -406,11 +411,14 @@ __global__ void __launch_bounds__(256) k_render(PipeArgs a)
         const bool in = idx < nL;
         const uint32_t gid = in ? __ldg(a.svals + lst + idx) : 0u;
         uint32_t k0 = kInvalidKey, k1 = kInvalidKey;
-        if (in) {
+        // a subtile whose sixteen pixels are saturated takes no further part
+        const unsigned live = __ballot_sync(kFull, !s.done);
+        const bool s0 = sval[0] && (live & 0xFFFFu) != 0, s1 = sval[1] && (live >> 16) != 0;
+        if (in && (s0 || s1)) {
             const Rec r = load_rec(a.geom, V.rec_off + gid);
             float t;
-            if (sval[0] && box_keep_depth(r, bS[0], V, a.eps_o, centre, &t)) k0 = depth_key(t);
-            if (sval[1] && box_keep_depth(r, bS[1], V, a.eps_o, centre, &t)) k1 = depth_key(t);
+            if (s0 && box_keep_depth(r, bS[0], V, a.eps_o, centre, &t)) k0 = depth_key(t);
+            if (s1 && box_keep_depth(r, bS[1], V, a.eps_o, centre, &t)) k1 = depth_key(t);
         }
         uint32_t r0 = 0, r1 = 0;
 #pragma unroll 8
@@ -448,6 +456,9 @@ __global__ void __launch_bounds__(256) k_render(PipeArgs a)
     }
     if (!finished) {
         while ((wq.nt[0] > 0 || wq.nt[1] > 0) && !__all_sync(kFull, s.done)) {
+            const unsigned live = __ballot_sync(kFull, !s.done);
+            if ((live & 0xFFFFu) == 0) wq.nt[0] = 0;
+            if ((live >> 16) == 0) wq.nt[1] = 0;
             const int c0 = min(16, wq.nt[0]), c1 = min(16, wq.nt[1]);
             midstage<HEAD, BWD>(a, V, s, c, wq, tailb, mq, bQ, qval, c0, c1, lane);
             wq.ts[0] += c0; wq.nt[0] -= c0;
@@ -476,7 +487,7 @@ __global__ void __launch_bounds__(256) k_render(PipeArgs a)
         a.rgb[3 * p + 2] = s.C2 + s.T * a.bg[2];
         a.depth[p] = s.Z;
         a.tfinal_ws[p] = s.T;
-        reinterpret_cast<float4*>(a.pix_state)[p] = make_float4(s.C0, s.C1, s.C2, s.Z);
+        if (a.grad_geom) reinterpret_cast<float4*>(a.pix_state)[p] = make_float4(s.C0, s.C1, s.C2, s.Z);
         if (a.tfinal_out) a.tfinal_out[p] = s.T;
         if (a.dbg_nblend) a.dbg_nblend[p] = s.nbl;
         if (a.dbg_hash) a.dbg_hash[p] = s.hash;
