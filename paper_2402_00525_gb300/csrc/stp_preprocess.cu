@@ -277,7 +277,7 @@ __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, bool has, c
                 uint32_t dk;
                 if (tile_depth_key(a, V, r, tx, ty, &dk)) {
                     if (part) {
-                        place_entry(a, gt, dk, gid, true);
+                        place_entry(a, gt, dk, gid, false);
                     } else {
                         const unsigned long long pos = (unsigned long long)off + cnt;
                         if (cnt < want && pos < a.capacity) {
@@ -291,7 +291,7 @@ __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, bool has, c
                 const Box b = block_box(tx * kTile, ty * kTile, kTile, V.W, V.H);
                 if (box_keep(r, b, a.eps_o)) {
                     cnt++;
-                    if (part) count_entry(a, gt, true);
+                    if (part) count_entry(a, gt, false);
                 }
             }
         }
