@@ -130,6 +130,7 @@ typedef struct {                 /* byte offsets of workspace regions (for inspe
     size_t rect;                 /* [V*N] ushort4 tile rectangles [x0, y0, x1, y1)           */
     size_t counts;               /* [V*N] uint32 entries per (view, Gaussian)                */
     size_t offsets;              /* [V*N] uint32 exclusive prefix sum of counts              */
+    size_t keep_mask;            /* [V*N] uint32 kept tiles of rectangles of <= 32 tiles      */
     size_t scan_partials;        /* scan scratch                                             */
     size_t keys, vals;           /* [capacity] uint64 / uint32 radix-sort buffer B           */
     size_t keys_alt, vals_alt;   /* [capacity] radix-sort buffer A (Duplicate output)        */

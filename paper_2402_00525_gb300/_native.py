@@ -65,7 +65,7 @@ class RunStatus(C.Structure):
                 ("counters", C.c_uint64 * 5)]
 
 
-_LAYOUT_SIZE_FIELDS = ["status", "views", "geom", "color", "rect", "counts", "offsets",
+_LAYOUT_SIZE_FIELDS = ["status", "views", "geom", "color", "rect", "counts", "offsets", "keep_mask",
                        "scan_partials", "keys", "vals", "keys_alt", "vals_alt", "sorted_keys",
                        "sorted_vals", "ranges", "tfinal", "pix_state", "scratch", "dbg_nblend",
                        "dbg_hash", "grad_geom", "dbg_trace", "tile_counts", "tile_offsets",

@@ -156,6 +156,7 @@ void make_plan(int64_t n, const stp_camera* cams, int32_t nviews, const stp_para
     L.rect = take((size_t)P.m * 8);
     L.counts = take((size_t)P.m * 4);
     L.offsets = take((size_t)P.m * 4);
+    L.keep_mask = take((size_t)P.m * 4);
     L.scan_partials = take(stp::scan_partials_count(P.m) * 8);
     L.keys = take((size_t)cap * 8);
     L.vals = take((size_t)cap * 4);
@@ -209,6 +210,7 @@ stp::PipeArgs make_args(const stp_gaussians* g, const stp_params* p, const Plan&
     a.rect = (ushort4*)(b + L.rect);
     a.counts = (uint32_t*)(b + L.counts);
     a.offsets = (uint32_t*)(b + L.offsets);
+    a.keep_mask = (uint32_t*)(b + L.keep_mask);
     a.scan_partials = (unsigned long long*)(b + L.scan_partials);
     a.keys = (uint64_t*)(b + L.keys);
     a.vals = (uint32_t*)(b + L.vals);

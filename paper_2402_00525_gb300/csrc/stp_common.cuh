@@ -181,6 +181,14 @@ __device__ __forceinline__ bool box_keep(const Rec& r, const Box& b, float eps_o
     const float2 d = box_max_offset(r, b.x0, b.x1, b.y0, b.y1);
     return splat_at(r, d.x, d.y) >= eps_o;
 }
+// key depth of a box already known to be kept (the same arithmetic as box_keep_depth)
+__device__ __forceinline__ float box_depth(const Rec& r, const Box& b, const ViewDesc& V, bool centre_ray)
+{
+    const float2 d = box_max_offset(r, b.x0, b.x1, b.y0, b.y1);
+    const float x = centre_ray ? __fmul_rn(0.5f, __fadd_rn(b.x0, b.x1)) : __fadd_rn(r.r0.x, __fadd_rn(r.r0.z, d.x));
+    const float y = centre_ray ? __fmul_rn(0.5f, __fadd_rn(b.y0, b.y1)) : __fadd_rn(r.r0.y, __fadd_rn(r.r0.w, d.y));
+    return depth_uv(r, to_u(V, x), to_w(V, y));
+}
 __device__ __forceinline__ bool box_keep_depth(const Rec& r, const Box& b, const ViewDesc& V,
                                                float eps_o, bool centre_ray, float* t)
 {

@@ -28,6 +28,7 @@ struct PipeArgs {
     float4* color;           // [V*N]
     ushort4* rect;           // [V*N]
     uint32_t* counts;        // [V*N]
+    uint32_t* keep_mask;     // [V*N] kept candidate tiles of the per-thread path (bit k = k-th tile)
     uint32_t* offsets;       // [V*N]
     unsigned long long* scan_partials;
     uint64_t* keys;          // sort buffer B

@@ -259,9 +259,24 @@ __device__ __forceinline__ void place_entry(const PipeArgs& a, uint32_t gt, uint
 // two-phase warp load balancing. Every lane of the warp must call it. With the global radix
 // sort the keys go to the Gaussian's own range [off, off + want) in tile order; with the
 // partitioned sort they go to their tiles' ranges.
+// depth key of a tile Preprocess found kept
+__device__ __forceinline__ uint32_t kept_depth_key(const PipeArgs& a, const ViewDesc& V, const Rec& r, int tx, int ty)
+{
+    const Box b = block_box(tx * kTile, ty * kTile, kTile, V.W, V.H);
+    float t = box_depth(r, b, V, (a.flags & 4) != 0);
+    if (a.flags & 8) t = r.r5.y;
+    return fkey(t);
+}
+
+// Count (EMIT = false) or write (EMIT = true) the kept tiles of this lane's Gaussian, with the
+// two-phase warp load balancing. Every lane of the warp must call it. Preprocess records the
+// kept candidates of the per-thread phase in a bit mask (rectangles of at most 32 tiles), so
+// Duplicate computes depths only for kept tiles and never re-takes a cull decision there.
+// With the global radix sort the keys go to the Gaussian's own range [off, off + want) in
+// tile order; with the partitioned sort they go to their tiles' ranges.
 template <bool EMIT>
 __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, bool has, const Rec& r,
-                               ushort4 rc, uint32_t off, uint32_t want, uint32_t gid)
+                               ushort4 rc, uint32_t off, uint32_t want, uint32_t gid, uint32_t* mask_io)
 {
     const int lane = threadIdx.x & 31;
     const int w = (int)rc.z - (int)rc.x, h = (int)rc.w - (int)rc.y;
@@ -270,10 +285,71 @@ __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, bool has, c
     const bool part = a.partitioned != 0;
     uint32_t cnt = 0;
     if (!big) {
-        for (int k = 0; k < ncand; k++) {
-            const int tx = rc.x + k % w, ty = rc.y + k / w;
-            const uint32_t gt = (uint32_t)(V.tile_off + ty * V.tiles_x + tx);
-            if (EMIT) {
+        if (!EMIT) {
+            uint32_t mask = 0;
+            for (int k = 0; k < ncand; k++) {
+                const int tx = rc.x + k % w, ty = rc.y + k / w;
+                const Box b = block_box(tx * kTile, ty * kTile, kTile, V.W, V.H);
+                if (box_keep(r, b, a.eps_o)) {
+                    cnt++;
+                    if (k < 32) mask |= 1u << k;
+                    if (part) count_entry(a, (uint32_t)(V.tile_off + ty * V.tiles_x + tx), false);
+                }
+            }
+            *mask_io = mask;
+        } else if (ncand <= 32) {
+            // emit the kept tiles of the mask, four cursor reservations in flight at a time
+            uint32_t mask = *mask_io;
+            while (mask) {
+                uint32_t gts[4], dks[4];
+                int np = 0;
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    if (mask) {
+                        const int k = __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        const int tx = rc.x + k % w, ty = rc.y + k / w;
+                        gts[j] = (uint32_t)(V.tile_off + ty * V.tiles_x + tx);
+                        dks[j] = kept_depth_key(a, V, r, tx, ty);
+                        np = j + 1;
+                    }
+                }
+                if (part) {
+                    uint32_t slot[4];
+#pragma unroll
+                    for (int j = 0; j < 4; j++)
+                        if (j < np) slot[j] = atomicAdd(&a.tile_cursor[gts[j]], 1u);
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        if (j < np) {
+                            if (slot[j] >= a.tile_counts[gts[j]]) {
+                                atomicOr(&a.status->error_bits, 2u);
+                            } else {
+                                const unsigned long long pos = (unsigned long long)a.tile_offsets[gts[j]] + slot[j];
+                                if (pos < a.capacity) a.dup_keys[pos] = ((unsigned long long)dks[j] << 32) | gid;
+                            }
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        if (j < np) {
+                            const unsigned long long pos = (unsigned long long)off + cnt;
+                            if (cnt < want && pos < a.capacity) {
+                                a.dup_keys[pos] = ((unsigned long long)gts[j] << 32) | dks[j];
+                                a.dup_vals[pos] = gid;
+                            }
+                            cnt++;
+                        }
+                    }
+                }
+                if (part) cnt += np;
+            }
+        } else {
+            // per-thread path with more than 32 candidates (lb_threshold > 32): evaluate again
+            for (int k = 0; k < ncand; k++) {
+                const int tx = rc.x + k % w, ty = rc.y + k / w;
+                const uint32_t gt = (uint32_t)(V.tile_off + ty * V.tiles_x + tx);
                 uint32_t dk;
                 if (tile_depth_key(a, V, r, tx, ty, &dk)) {
                     if (part) {
@@ -286,12 +362,6 @@ __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, bool has, c
                         }
                     }
                     cnt++;
-                }
-            } else {
-                const Box b = block_box(tx * kTile, ty * kTile, kTile, V.W, V.H);
-                if (box_keep(r, b, a.eps_o)) {
-                    cnt++;
-                    if (part) count_entry(a, gt, false);
                 }
             }
         }
@@ -354,8 +424,10 @@ __global__ void __launch_bounds__(256) k_preprocess(PipeArgs a)
         bool vis = false;
         if (live) vis = make_record(a, V, g, i, r, col, rc);
         else r.r0 = r.r1 = r.r2 = r.r3 = r.r4 = r.r5 = make_float4(0.f, 0.f, 0.f, 0.f);
-        const uint32_t cnt = tiles_pass<false>(a, V, vis, r, rc, 0, 0, 0);
+        uint32_t mask = 0;
+        const uint32_t cnt = tiles_pass<false>(a, V, vis, r, rc, 0, 0, 0, &mask);
         if (live) {
+            a.keep_mask[V.rec_off + i] = mask;
             const long long o = V.rec_off + i;
             float4* gp = a.geom + kRecFloat4 * o;
             gp[0] = r.r0; gp[1] = r.r1; gp[2] = r.r2; gp[3] = r.r3; gp[4] = r.r4; gp[5] = r.r5;
@@ -375,16 +447,17 @@ __global__ void __launch_bounds__(256) k_duplicate(PipeArgs a)
         const long long o = V.rec_off + i;
         Rec r;
         ushort4 rc = make_ushort4(0, 0, 0, 0);
-        uint32_t off = 0, want = 0;
+        uint32_t off = 0, want = 0, mask = 0;
         if (live) {
             r = load_rec(a.geom, o);
             rc = a.rect[o];
-            off = a.offsets[o];
+            off = a.partitioned ? 0u : a.offsets[o];
             want = a.counts[o];
+            mask = a.keep_mask[o];
         } else {
             r.r0 = r.r1 = r.r2 = r.r3 = r.r4 = r.r5 = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        const uint32_t got = tiles_pass<true>(a, V, live && want > 0, r, rc, off, want, (uint32_t)i);
+        const uint32_t got = tiles_pass<true>(a, V, live && want > 0, r, rc, off, want, (uint32_t)i, &mask);
         if (live && got != want && !a.partitioned) {
             // Preprocess and Duplicate disagree (cannot happen with the shared rounding of the
             // decision arithmetic; kept as the paper's safety net, appendix B.4): pad with

@@ -136,7 +136,7 @@ __device__ __forceinline__ void blend(const PipeArgs& a, const ViewDesc& V, Px<H
     if (!BWD && a.dbg_trace && s.nbl < (uint32_t)kTraceLen) a.dbg_trace[c.pix * kTraceLen + s.nbl] = (int)id;
     s.T = Tn;
     s.nbl++;
-    s.hash = s.hash * kHashMul + (unsigned long long)(id + 1u);
+    if (a.dbg_hash) s.hash = s.hash * kHashMul + (unsigned long long)(id + 1u);
 }
 
 // insert (key, id, val) after equal keys; when more than HEAD entries are held blend the
