@@ -496,6 +496,12 @@ static void build_lists(ctx* c)
                 double val = g->opacity * gauss2(g, xh[0], xh[1]);
                 double m = fabs(val / P->eps_o - 1.0);
                 int keep = val >= P->eps_o;
+                /* flag 512: no tile-based culling (ablation D of Tab. performance_ablation):
+                 * every tile of the rectangle is kept; the key depth still goes through x_hat */
+                if (P->flags & 512) {
+                    keep = 1;
+                    m = INFINITY;
+                }
                 if (in_rect && g->visible && keep) g->ntiles++;
                 if (!L->selected) continue;
                 /* key depth: t_opt through x_hat (default); flag 4: through the tile centre
@@ -641,7 +647,10 @@ static int eval_box(const ctx* c, int id, const double box[4], double* t, double
     orc_alg1(g->mean2, g->conic, box, xh);
     double val = g->opacity * gauss2(g, xh[0], xh[1]);
     *margin = fabs(val / c->P.eps_o - 1.0);
-    if (val < c->P.eps_o) return 0;
+    /* flag 1024: no hierarchical culling inside Render (ablation E): every entry passes the
+     * 4x4 and 2x2 levels; only the per-pixel alpha test drops Gaussians                   */
+    if (c->P.flags & 1024) *margin = INFINITY;
+    else if (val < c->P.eps_o) return 0;
     if (c->P.flags & 2) *t = depth_at(c, g, 0.5 * (box[0] + box[1]), 0.5 * (box[2] + box[3]));
     else *t = depth_at(c, g, xh[0], xh[1]);
     return 1;
@@ -937,12 +946,16 @@ static void flat_tile(ctx* c, const sinks* sk, int tile, int64_t* cnt)
             } else {
                 int have_prev = 0;
                 double prev_key = 0;
-                for (int j = 0; j < L->n && !ps->done; j++) {
+                for (int j = 0; j < L->n; j++) {
                     cnt[CNT_EVAL_P]++;
                     double a = pixel_alpha(c, L->e[j].id, ps);
                     ps->cmin = fmin(ps->cmin, fabs(a / P->eps_o - 1.0));
                     if (a < P->eps_o) continue;
                     if (have_prev) ps->dmin = fmin(ps->dmin, relgap(prev_key, L->e[j].t));
+                    /* once the ray has terminated, the list order of the entry that ended it
+                     * and the next contributing entry is the last decision that matters: had
+                     * they been swapped, the other one would have been taken first           */
+                    if (ps->done) break;
                     have_prev = 1;
                     prev_key = L->e[j].t;
                     double t = pixel_depth(c, L->e[j].id, ps);

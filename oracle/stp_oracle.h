@@ -28,7 +28,9 @@ typedef struct {
     int32_t mode;              /* 0 HIER, 1 FULL, 2 GLOBAL, 3 WINDOW                    */
     int32_t window_k;          /* WINDOW mode k-buffer size (Sec. 3.3)                 */
     int32_t flags;             /* 1: head evict-before-insert; 2: level-centre rays;
-                                  4: tile-centre key; 8: view-space-depth key           */
+                                  4: tile-centre key; 8: view-space-depth key;
+                                  512: no tile-based culling; 1024: no culling at the
+                                  4x4 / 2x2 levels of Render (ablations D, E)           */
     int32_t sh_degree;
     int32_t record_blends;     /* keep per-pixel blend lists (needed by the adjoint)   */
     double eps_o, t_min, alpha_max, inv_scale_max, dilation, frustum_clamp, znear;

@@ -41,6 +41,8 @@ FLAG_TILE_CENTRE_KEY = 4       # tile sort key from the tile-centre ray (no tile
 FLAG_VIEW_DEPTH_KEY = 8        # tile sort key = view-space depth of the mean (3DGS global depth)
 FLAG_NO_LOAD_BALANCE = 16      # every Gaussian's tiles handled by its own thread
 FLAG_GLOBAL_SORT = 256         # one global radix sort of (tile, depth) keys (same order)
+FLAG_NO_TILE_CULL = 512        # ablation D: Duplicate keeps every tile of the rectangle
+FLAG_NO_HIER_CULL = 1024       # ablation E: no culling at the 4x4 / 2x2 levels of Render
 
 
 @dataclasses.dataclass

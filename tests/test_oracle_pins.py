@@ -446,3 +446,47 @@ def test_adjoint_matches_central_differences(oracle):
         assert abs(fd - g) <= 1e-6 * max(abs(g), abs(fd)) + 1e-9, (name, i, j, fd, g)
         checked += 1
     assert checked >= 60
+
+
+# --------------------------------------------------------------------- ablations D and E
+def test_without_tile_culling_lists_grow_but_per_pixel_orders_do_not_change(oracle):
+    """Ablation D (Tab. performance_ablation): keeping every tile of a Gaussian's rectangle
+    adds exactly the rectangle tiles Algorithm 1 culls. Each added entry is below eps_O at every
+    pixel of its tile, so the orders that test alpha per pixel over the whole list (FULL,
+    GLOBAL) give the same images, and the hierarchy culls the additions at its 4x4 level."""
+    sc = I.uniform_scene(600, 21, scale_range=(0.01, 0.2))
+    cam = I.look_at((0, 0, -3), (0, 0, 0), (0, 1, 0), 96, 80, 60.0)
+    base = I.RenderParams()
+    with oracle.OracleRun(sc, cam, base) as r:
+        pp = r.preprocess()
+    vis = pp["visible"] > 0
+    rc = pp["rect"][vis]
+    area = int(((rc[:, 2] - rc[:, 0] + 1) * (rc[:, 3] - rc[:, 1] + 1)).sum())
+    for mode in (I.MODE_FULL, I.MODE_GLOBAL, I.MODE_HIER):
+        a = oracle.render(sc, cam, dataclasses.replace(base, mode=mode))
+        b = oracle.render(sc, cam, dataclasses.replace(base, mode=mode, flags=I.FLAG_NO_TILE_CULL))
+        assert b["num_entries"] == area > a["num_entries"] == int(pp["ntiles"].sum())
+        d = a["decided"] & b["decided"]
+        if mode != I.MODE_HIER:
+            assert d.mean() > 0.97
+            assert np.array_equal(a["hash"][d], b["hash"][d]) and np.array_equal(a["rgb"][d], b["rgb"][d])
+        else:
+            # same 4x4 survivors; only the batch boundaries of the longer lists move
+            assert a["counters"]["surv_subtile"] == b["counters"]["surv_subtile"]
+            assert b["counters"]["eval_subtile"] > a["counters"]["eval_subtile"]
+
+
+def test_without_hierarchical_culling_every_entry_reaches_the_pixels(oracle):
+    """Ablation E: without the 4x4 / 2x2 culls every list entry survives both levels, the
+    per-pixel alpha test still drops the non-contributors, so well separated layers blend in
+    the exact order, as with culling."""
+    sc = I.layered_scene(6, 10, 7)
+    cam = I.look_at((0.2, 0.1, -3), (0, 0, 0), (0, 1, 0), 160, 144, 60.0)
+    full = oracle.render(sc, cam, I.RenderParams(mode=I.MODE_FULL))
+    e = oracle.render(sc, cam, I.RenderParams(flags=I.FLAG_NO_HIER_CULL))
+    h = oracle.render(sc, cam, I.RenderParams())
+    d = full["decided"] & e["decided"]
+    assert d.mean() > 0.97
+    assert np.array_equal(e["hash"][d], full["hash"][d])
+    assert e["counters"]["surv_subtile"] == e["counters"]["eval_subtile"] > h["counters"]["surv_subtile"]
+    assert e["counters"]["eval_quad"] > h["counters"]["eval_quad"]
