@@ -45,6 +45,11 @@ typedef enum {
     STP_ERR_NOT_SUPPORTED = 5   /* parameter combination not compiled in                      */
 } stp_status;
 
+/* Blend orders (Sec. 3.3, 3.4). HIER: the hierarchical resort (tail / mid / head queues).
+ * The others are forward-only comparison orders over the same sorted tile lists: FULL, every
+ * Gaussian with alpha >= eps_O in exact per-pixel t_opt order (ties by list position);
+ * GLOBAL, tile-list order (the global sort alone); WINDOW, a per-pixel k-buffer of window_k
+ * entries (1, 2, 4, 8 or 16) fed in tile-list order.                                      */
 enum { STP_MODE_HIER = 0, STP_MODE_FULL = 1, STP_MODE_GLOBAL = 2, STP_MODE_WINDOW = 3 };
 
 /* flag bits of stp_params.flags */
@@ -59,9 +64,13 @@ enum {
                                         forward and backward calls must both set it          */
     STP_FLAG_DEBUG_TRACE = 128,      /* workspace also receives, per pixel, the ids of the first
                                         STP_TRACE_LEN blended Gaussians (-1 padded)          */
-    STP_FLAG_GLOBAL_SORT = 256       /* order the entries with one global LSD radix sort of
+    STP_FLAG_GLOBAL_SORT = 256,      /* order the entries with one global LSD radix sort of
                                         (tile, depth) keys instead of the default partitioned
                                         per-tile sort (appendix B.3); same result            */
+    STP_FLAG_NO_TILE_CULL = 512,     /* Duplicate keeps every tile of a Gaussian's rectangle
+                                        (ablation D, Tab. performance_ablation)              */
+    STP_FLAG_NO_HIER_CULL = 1024     /* Render does not cull at the 4x4 / 2x2 levels; only the
+                                        per-pixel alpha test drops Gaussians (ablation E)     */
 };
 #define STP_TRACE_LEN 64
 
@@ -125,12 +134,15 @@ typedef struct {                 /* device status block, read back by stp_read_s
 typedef struct {                 /* byte offsets of workspace regions (for inspection)       */
     size_t status;               /* stp_run_status                                           */
     size_t views;                /* internal view table                                      */
-    size_t geom;                 /* [V*N] 96-byte render records (layout in stp_common.cuh)  */
-    size_t color;                /* [V*N] float4 colours                                     */
-    size_t rect;                 /* [V*N] ushort4 tile rectangles [x0, y0, x1, y1)           */
-    size_t counts;               /* [V*N] uint32 entries per (view, Gaussian)                */
-    size_t offsets;              /* [V*N] uint32 exclusive prefix sum of counts              */
-    size_t keep_mask;            /* [V*N] uint32 kept tiles of rectangles of <= 32 tiles      */
+    size_t scenes;               /* internal scene table                                     */
+    size_t geom;                 /* [M] 96-byte render records (layout in stp_common.cuh);
+                                    M = sum over views of the N of the view's scene, view
+                                    after view, Gaussian id ascending within a view          */
+    size_t color;                /* [M] float4 colours                                       */
+    size_t rect;                 /* [M] ushort4 tile rectangles [x0, y0, x1, y1)             */
+    size_t counts;               /* [M] uint32 entries per (view, Gaussian)                  */
+    size_t offsets;              /* [M] uint32 exclusive prefix sum of counts                */
+    size_t keep_mask;            /* [M] uint32 kept tiles of rectangles of <= 32 tiles        */
     size_t scan_partials;        /* scan scratch                                             */
     size_t keys, vals;           /* [capacity] uint64 / uint32 radix-sort buffer B           */
     size_t keys_alt, vals_alt;   /* [capacity] radix-sort buffer A (Duplicate output)        */
@@ -142,7 +154,9 @@ typedef struct {                 /* byte offsets of workspace regions (for inspe
     size_t scratch;              /* sort histogram scratch                                   */
     size_t dbg_nblend;           /* [total pixels] uint32 blends per pixel (flag 32), else 0 */
     size_t dbg_hash;             /* [total pixels] uint64 blend-order hash (flag 32), else 0 */
-    size_t grad_geom;            /* [V*N*24] float backward scratch (flag 64), else 0        */
+    size_t dbg_delta;            /* [total pixels] float sort error delta (flag 32): the sum
+                                    of t_opt steps backwards along the blend order (Sec. 3.3) */
+    size_t grad_geom;            /* [M*24] float backward scratch (flag 64), else 0          */
     size_t dbg_trace;            /* [total pixels][STP_TRACE_LEN] int32 blend ids (flag 128)  */
     size_t tile_counts;          /* [total tiles] uint32 entries per tile (partitioned sort)  */
     size_t tile_offsets;         /* [total tiles] uint32 first entry of each tile            */
@@ -165,12 +179,16 @@ size_t stp_workspace_size(int64_t n, const stp_camera* cams /* host, [nviews] */
 stp_status stp_workspace_layout_get(int64_t n, const stp_camera* cams /* host */, int32_t nviews,
                                     const stp_params* prm /* host */, stp_workspace_layout* out /* host */);
 
-/* Forward pass (Sec. 3): Preprocess -> Duplicate -> global radix sort -> hierarchical
- * Render, for `nviews` views of one scene in one batched launch sequence. Writes rgb
- * [pixels,3], depth [pixels] (volumetric depth with phi = t_opt, Sec. 4.1 "Depth Evaluation") and, if not NULL,
- * tfinal [pixels]. The workspace keeps the state the backward pass needs (sorted lists,
+/* Forward pass (Sec. 3): Preprocess -> Duplicate -> per-tile depth sort (appendix B.3;
+ * STP_FLAG_GLOBAL_SORT selects one global radix sort instead) -> hierarchical Render, for
+ * `nviews` views of one scene (1 <= nviews <= STP_MAX_VIEWS) in one launch per stage. Writes
+ * rgb [pixels,3], depth [pixels] (volumetric depth with phi = t_opt, Sec. 4.1 "Depth
+ * Evaluation") and, if not NULL, tfinal [pixels]; pixels are packed view after view, row
+ * major within a view. The workspace keeps the state the backward pass needs (sorted lists,
  * records, final T). Asynchronous; call stp_read_status() to learn whether the capacity
- * sufficed (if not, rgb / depth are undefined and num_entries tells the size needed).   */
+ * sufficed (if not, rgb / depth are undefined and num_entries tells the size needed).
+ * Launches only kernels and memsets after the first call for a given parameter set (kernel
+ * attributes are set once per device), so a call can be recorded under stream capture.  */
 stp_status stp_render(const stp_gaussians* g /* host struct of device pointers */,
                       const stp_camera* cams /* host, [nviews] */, int32_t nviews,
                       const stp_params* prm /* host */, void* workspace, size_t ws_bytes,
@@ -186,6 +204,32 @@ stp_status stp_render_backward(const stp_gaussians* g, const stp_camera* cams, i
                                const float* d_rgb, const float* d_depth,
                                const stp_gaussians_grad* grad /* host struct of device ptrs */,
                                void* stream);
+
+/* Batched rendering of several scenes (each with its own Gaussians and views) in one launch
+ * per stage. Scene s (0 <= s < nscenes <= STP_MAX_SCENES) owns views_per_scene[s] consecutive
+ * cameras of cams, starting after the views of scenes 0..s-1; the counts sum to nviews
+ * (<= STP_MAX_VIEWS). Results are identical to one stp_render call per scene with the same
+ * parameters; outputs are packed view after view over all scenes. `n` (host, [nscenes]) is
+ * each scene's Gaussian count. The batched backward ACCUMULATES into grads[s] (host array
+ * of nscenes structs of device pointers) for scene s.                                     */
+#define STP_MAX_SCENES 64
+#define STP_MAX_VIEWS 64
+size_t     stp_workspace_size_batched(const int64_t* n, const int32_t* views_per_scene, int32_t nscenes,
+                                      const stp_camera* cams, int32_t nviews, const stp_params* prm);
+stp_status stp_workspace_layout_batched(const int64_t* n, const int32_t* views_per_scene, int32_t nscenes,
+                                        const stp_camera* cams, int32_t nviews, const stp_params* prm,
+                                        stp_workspace_layout* out);
+stp_status stp_render_batched(const stp_gaussians* scenes /* host, [nscenes] */, int32_t nscenes,
+                              const int32_t* views_per_scene /* host, [nscenes] */,
+                              const stp_camera* cams /* host, [nviews] */, int32_t nviews,
+                              const stp_params* prm, void* workspace, size_t ws_bytes,
+                              float* rgb, float* depth, float* tfinal, void* stream);
+stp_status stp_render_backward_batched(const stp_gaussians* scenes, int32_t nscenes,
+                                       const int32_t* views_per_scene, const stp_camera* cams,
+                                       int32_t nviews, const stp_params* prm, void* workspace,
+                                       size_t ws_bytes, const float* d_rgb, const float* d_depth,
+                                       const stp_gaussians_grad* grads /* host, [nscenes] */,
+                                       void* stream);
 
 /* Synchronises `stream`, copies the workspace's status block to *out (host) and returns
  * STP_ERR_CAPACITY / STP_ERR_TIMEOUT if the device recorded that condition, else STP_OK.  */
@@ -227,8 +271,8 @@ stp_status stp_sort_pairs_noalloc(const uint64_t* keys_in, const uint32_t* vals_
  * milliseconds of each stage (ms[call * STP_NUM_STAGES + stage]); *ncalls receives the number
  * of calls recorded; recording then restarts at slot 0. Stages of a forward call: 0 status and
  * view table, 1 Preprocess, 2 scan, 3 Duplicate, 4 sort, 5 tile ranges, 6 Render; of a
- * backward call: 5 clearing the gradient scratch, 6 backward Render, 7 backward Preprocess
- * (the others are 0).                                                                     */
+ * backward call: 4 view and scene tables, 5 clearing the gradient scratch, 6 backward Render,
+ * 7 backward Preprocess (the others are 0).                                                                     */
 #define STP_NUM_STAGES 8
 #define STP_NUM_STAGE_EVENTS (STP_NUM_STAGES + 1)
 stp_status stp_profile_enable(int32_t max_calls);
@@ -238,7 +282,7 @@ stp_status stp_profile_read(float* ms /* host, [max_calls * STP_NUM_STAGES] */, 
 /* Thread-local message of the last error on this host thread (empty if none).            */
 const char* stp_last_error(void);
 
-/* Library version, e.g. 0x000100 for 0.1.0.                                              */
+/* Library version, e.g. 0x000200 for 0.2.0.                                              */
 int32_t stp_version(void);
 
 #ifdef __cplusplus

@@ -20,8 +20,12 @@ FLAG_DEBUG_STATS = 32
 FLAG_BACKWARD = 64
 FLAG_DEBUG_TRACE = 128
 FLAG_GLOBAL_SORT = 256
+FLAG_NO_TILE_CULL = 512
+FLAG_NO_HIER_CULL = 1024
 SORT_STATIC_MAX_N = 1 << 20
 TRACE_LEN = 64
+MAX_SCENES = 64
+MAX_VIEWS = 64
 
 
 class StpError(RuntimeError):
@@ -65,10 +69,10 @@ class RunStatus(C.Structure):
                 ("counters", C.c_uint64 * 5)]
 
 
-_LAYOUT_SIZE_FIELDS = ["status", "views", "geom", "color", "rect", "counts", "offsets", "keep_mask",
+_LAYOUT_SIZE_FIELDS = ["status", "views", "scenes", "geom", "color", "rect", "counts", "offsets", "keep_mask",
                        "scan_partials", "keys", "vals", "keys_alt", "vals_alt", "sorted_keys",
                        "sorted_vals", "ranges", "tfinal", "pix_state", "scratch", "dbg_nblend",
-                       "dbg_hash", "grad_geom", "dbg_trace", "tile_counts", "tile_offsets",
+                       "dbg_hash", "dbg_delta", "grad_geom", "dbg_trace", "tile_counts", "tile_offsets",
                        "tile_cursor", "tile_partials", "total"]
 
 
@@ -83,7 +87,8 @@ class Layout(C.Structure):
 
 # every symbol include/stp.h declares (the CPU tests check the library exports them)
 EXPORTS = ["stp_workspace_size", "stp_workspace_layout_get", "stp_render", "stp_render_backward",
-           "stp_read_status", "stp_sort_temp_bytes", "stp_sort_pairs", "stp_sort_pairs_noalloc",
+           "stp_workspace_size_batched", "stp_workspace_layout_batched", "stp_render_batched",
+           "stp_render_backward_batched", "stp_read_status", "stp_sort_temp_bytes", "stp_sort_pairs", "stp_sort_pairs_noalloc",
            "stp_profile_enable",
            "stp_profile_read", "stp_last_error", "stp_version"]
 
@@ -108,6 +113,14 @@ def lib():
         L.stp_render.argtypes = [vp, vp, C.c_int32, vp, vp, sz, vp, vp, vp, vp]
         L.stp_render_backward.restype = C.c_int
         L.stp_render_backward.argtypes = [vp, vp, C.c_int32, vp, vp, sz, vp, vp, vp, vp]
+        L.stp_workspace_size_batched.restype = sz
+        L.stp_workspace_size_batched.argtypes = [vp, vp, C.c_int32, vp, C.c_int32, vp]
+        L.stp_workspace_layout_batched.restype = C.c_int
+        L.stp_workspace_layout_batched.argtypes = [vp, vp, C.c_int32, vp, C.c_int32, vp, vp]
+        L.stp_render_batched.restype = C.c_int
+        L.stp_render_batched.argtypes = [vp, C.c_int32, vp, vp, C.c_int32, vp, vp, sz, vp, vp, vp, vp]
+        L.stp_render_backward_batched.restype = C.c_int
+        L.stp_render_backward_batched.argtypes = [vp, C.c_int32, vp, vp, C.c_int32, vp, vp, sz, vp, vp, vp, vp]
         L.stp_read_status.restype = C.c_int
         L.stp_read_status.argtypes = [vp, vp, vp]
         L.stp_sort_temp_bytes.restype = sz
@@ -168,11 +181,20 @@ def params_struct(prm: RenderParams, extra_flags: int = 0, max_entries: int = 0)
     return p
 
 
-def layout(n: int, cams, prm: Params) -> Layout:
+def layout(n, cams, prm: Params, views_per_scene=None) -> Layout:
+    """Workspace layout for one scene of n Gaussians, or for several scenes (n a sequence of
+    sizes, views_per_scene the number of consecutive cameras of each)."""
     arr = cameras_array(cams)
     L = Layout()
-    check(lib().stp_workspace_layout_get(n, C.cast(arr, C.c_void_p), len(cams), C.byref(prm),
-                                         C.byref(L)))
+    if views_per_scene is None:
+        check(lib().stp_workspace_layout_get(int(n), C.cast(arr, C.c_void_p), len(cams), C.byref(prm),
+                                             C.byref(L)))
+    else:
+        n = [n] if np.isscalar(n) else list(n)
+        ns = (C.c_int64 * len(n))(*[int(x) for x in n])
+        vps = (C.c_int32 * len(views_per_scene))(*[int(x) for x in views_per_scene])
+        check(lib().stp_workspace_layout_batched(C.cast(ns, C.c_void_p), C.cast(vps, C.c_void_p), len(n),
+                                                 C.cast(arr, C.c_void_p), len(cams), C.byref(prm), C.byref(L)))
     return L
 
 

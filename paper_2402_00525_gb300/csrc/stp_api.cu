@@ -74,12 +74,27 @@ int bits_for(long long v)   // bits needed to store the value v (v >= 1)
     return b;
 }
 
-stp_status check(int64_t n, const stp_camera* cams, int32_t nviews, const stp_params* p)
+// Checks shared by every entry point: scene sizes, cameras, parameters.
+stp_status check(const int64_t* ns, const int32_t* vps, int32_t nscenes, const stp_camera* cams, int32_t nviews,
+                 const stp_params* p)
 {
-    if (!cams || !p) return fail(STP_ERR_ARG, "null camera or parameter pointer");
-    if (n < 0 || n >= (1LL << 31)) return fail(STP_ERR_ARG, "n = %lld out of range [0, 2^31)", (long long)n);
+    if (!cams || !p || !ns || !vps) return fail(STP_ERR_ARG, "null camera, parameter or scene-size pointer");
+    if (nscenes < 1 || nscenes > stp::kMaxScenes)
+        return fail(STP_ERR_ARG, "nscenes = %d out of range [1, %d]", nscenes, stp::kMaxScenes);
     if (nviews < 1 || nviews > stp::kMaxViews)
         return fail(STP_ERR_ARG, "nviews = %d out of range [1, %d]", nviews, stp::kMaxViews);
+    long long vsum = 0, threads = 0, m = 0;
+    for (int s = 0; s < nscenes; s++) {
+        if (ns[s] < 0 || ns[s] >= (1LL << 31))
+            return fail(STP_ERR_ARG, "scene %d: n = %lld out of range [0, 2^31)", s, (long long)ns[s]);
+        if (vps[s] < 0) return fail(STP_ERR_ARG, "scene %d: negative view count", s);
+        vsum += vps[s];
+        threads += (ns[s] + stp::kSceneAlign - 1) / stp::kSceneAlign * stp::kSceneAlign;
+        m += ns[s] * (long long)vps[s];
+    }
+    if (vsum != nviews) return fail(STP_ERR_ARG, "views per scene sum to %lld, nviews = %d", vsum, nviews);
+    if (threads / 256 >= (1LL << 31) || m >= (1LL << 40))
+        return fail(STP_ERR_ARG, "scenes too large for one launch sequence");
     for (int v = 0; v < nviews; v++) {
         const stp_camera& c = cams[v];
         if (c.width < 1 || c.height < 1 || c.width > 16384 || c.height > 16384)
@@ -100,8 +115,10 @@ stp_status check(int64_t n, const stp_camera* cams, int32_t nviews, const stp_pa
     if (!(p->inv_scale_max > 0.f)) return fail(STP_ERR_ARG, "inv_scale_max must be > 0");
     if (!(p->dilation >= 0.f) || !(p->frustum_clamp > 0.f) || !(p->znear > 0.f))
         return fail(STP_ERR_ARG, "dilation >= 0, frustum_clamp > 0 and znear > 0 required");
-    if (p->mode != STP_MODE_HIER)
-        return fail(STP_ERR_NOT_SUPPORTED, "mode %d is not compiled into the GPU renderer", p->mode);
+    if (p->mode < STP_MODE_HIER || p->mode > STP_MODE_WINDOW)
+        return fail(STP_ERR_ARG, "mode %d: must be one of STP_MODE_HIER, FULL, GLOBAL, WINDOW", p->mode);
+    if (p->mode == STP_MODE_WINDOW && !stp::render_head_supported(p->window_k))
+        return fail(STP_ERR_NOT_SUPPORTED, "window_k = %d: compiled sizes are 1, 2, 4, 8, 16", p->window_k);
     if (p->max_entries < 0 || p->max_entries >= 0xFFFFFFFFLL)
         return fail(STP_ERR_ARG, "max_entries must be in [0, 2^32 - 1)");
     return STP_OK;
@@ -109,37 +126,53 @@ stp_status check(int64_t n, const stp_camera* cams, int32_t nviews, const stp_pa
 
 struct Plan {
     stp_workspace_layout L;
-    long long m;                       // views * n
+    long long m;                       // render records: sum over views of the view's scene size
+    long long threads;                 // per-Gaussian threads (scenes aligned to kSceneAlign)
     std::vector<stp::ViewDesc> views;
+    std::vector<stp::SceneDesc> scenes;   // sizes and view ranges; pointers filled per call
 };
 
-void make_plan(int64_t n, const stp_camera* cams, int32_t nviews, const stp_params* p, Plan& P)
+void make_plan(const int64_t* ns, const int32_t* vps, int32_t nscenes, const stp_camera* cams, int32_t nviews,
+               const stp_params* p, Plan& P)
 {
     std::memset(&P.L, 0, sizeof P.L);
-    P.m = (long long)n * nviews;
     P.views.resize(nviews);
-    long long tiles = 0, pixels = 0;
-    for (int v = 0; v < nviews; v++) {
-        const stp_camera& c = cams[v];
-        stp::ViewDesc& d = P.views[v];
-        std::memset(&d, 0, sizeof d);
-        for (int k = 0; k < 9; k++) d.R[k] = c.R[k];
-        for (int k = 0; k < 3; k++) d.t[k] = c.t[k];
-        for (int k = 0; k < 3; k++)   // o = -R^T t
-            d.o[k] = -(c.R[k] * c.t[0] + c.R[3 + k] * c.t[1] + c.R[6 + k] * c.t[2]);
-        d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
-        d.ifx = 1.f / c.fx; d.ify = 1.f / c.fy;
-        d.limx = p->frustum_clamp * 0.5f * c.width / c.fx;
-        d.limy = p->frustum_clamp * 0.5f * c.height / c.fy;
-        d.W = c.width; d.H = c.height;
-        d.tiles_x = (c.width + 15) / 16;
-        d.tiles_y = (c.height + 15) / 16;
-        d.tile_off = (int)tiles;
-        d.pix_off = pixels;
-        d.rec_off = (long long)v * n;
-        tiles += (long long)d.tiles_x * d.tiles_y;
-        pixels += (long long)c.width * c.height;
+    P.scenes.resize(nscenes);
+    long long tiles = 0, pixels = 0, rec = 0, threads = 0;
+    int v = 0;
+    for (int sc = 0; sc < nscenes; sc++) {
+        stp::SceneDesc& S = P.scenes[sc];
+        std::memset(&S, 0, sizeof S);
+        S.n = (int)ns[sc];
+        S.view_begin = v;
+        S.view_end = v + vps[sc];
+        S.thread_off = threads;
+        threads += (ns[sc] + stp::kSceneAlign - 1) / stp::kSceneAlign * stp::kSceneAlign;
+        for (; v < S.view_end; v++) {
+            const stp_camera& c = cams[v];
+            stp::ViewDesc& d = P.views[v];
+            std::memset(&d, 0, sizeof d);
+            for (int k = 0; k < 9; k++) d.R[k] = c.R[k];
+            for (int k = 0; k < 3; k++) d.t[k] = c.t[k];
+            for (int k = 0; k < 3; k++)   // o = -R^T t
+                d.o[k] = -(c.R[k] * c.t[0] + c.R[3 + k] * c.t[1] + c.R[6 + k] * c.t[2]);
+            d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
+            d.ifx = 1.f / c.fx; d.ify = 1.f / c.fy;
+            d.limx = p->frustum_clamp * 0.5f * c.width / c.fx;
+            d.limy = p->frustum_clamp * 0.5f * c.height / c.fy;
+            d.W = c.width; d.H = c.height;
+            d.tiles_x = (c.width + 15) / 16;
+            d.tiles_y = (c.height + 15) / 16;
+            d.tile_off = (int)tiles;
+            d.pix_off = pixels;
+            d.rec_off = rec;
+            tiles += (long long)d.tiles_x * d.tiles_y;
+            pixels += (long long)c.width * c.height;
+            rec += ns[sc];
+        }
     }
+    P.m = rec;
+    P.threads = threads;
     long long cap = p->max_entries > 0 ? p->max_entries : std::max<long long>(1LL << 20, 4LL * P.m);
     if (cap > 0xFFFFFFFELL) cap = 0xFFFFFFFELL;
     stp_workspace_layout& L = P.L;
@@ -151,6 +184,7 @@ void make_plan(int64_t n, const stp_camera* cams, int32_t nviews, const stp_para
     auto take = [&](size_t bytes) { size_t r = o; o += al(bytes); return r; };
     L.status = take(sizeof(stp::Status));
     L.views = take(sizeof(stp::ViewDesc) * nviews);
+    L.scenes = take(sizeof(stp::SceneDesc) * nscenes);
     L.geom = take((size_t)P.m * 16 * stp::kRecFloat4);
     L.color = take((size_t)P.m * 16);
     L.rect = take((size_t)P.m * 8);
@@ -166,10 +200,11 @@ void make_plan(int64_t n, const stp_camera* cams, int32_t nviews, const stp_para
     L.tfinal = take((size_t)pixels * 4);
     L.pix_state = take((size_t)pixels * 16);
     L.scratch = take(stp::sort_hist_bytes());
-    L.dbg_nblend = L.dbg_hash = 0;
+    L.dbg_nblend = L.dbg_hash = L.dbg_delta = 0;
     if (p->flags & kFlagDebug) {
         L.dbg_nblend = take((size_t)pixels * 4);
         L.dbg_hash = take((size_t)pixels * 8);
+        L.dbg_delta = take((size_t)pixels * 4);
     }
     const bool in_alt = (p->flags & kFlagGlobalSort) && stp::pipeline_sorted_in_alt(L.key_bits);
     L.sorted_keys = in_alt ? L.keys_alt : L.keys;
@@ -185,16 +220,16 @@ void make_plan(int64_t n, const stp_camera* cams, int32_t nviews, const stp_para
     L.total = o;
 }
 
-stp::PipeArgs make_args(const stp_gaussians* g, const stp_params* p, const Plan& P, void* ws)
+stp::PipeArgs make_args(const stp_params* p, const Plan& P, void* ws)
 {
     stp::PipeArgs a;
     std::memset(&a, 0, sizeof a);
     char* b = (char*)ws;
     const stp_workspace_layout& L = P.L;
-    a.means = g->means; a.log_scales = g->log_scales; a.quats = g->quats;
-    a.logits = g->opacity_logits; a.sh = g->sh;
-    a.n = (int)g->n;
-    a.sh_k = (g->sh_degree + 1) * (g->sh_degree + 1);
+    a.scenes = (const stp::SceneDesc*)(b + L.scenes);
+    a.nscenes = (int)P.scenes.size();
+    a.threads = P.threads;
+    a.m = P.m;
     a.nviews = (int)P.views.size();
     a.lb_threshold = p->lb_threshold; a.flags = p->flags; a.mode = p->mode; a.window_k = p->window_k;
     a.tail = p->tail; a.mid = p->mid; a.head = p->head;
@@ -226,6 +261,7 @@ stp::PipeArgs make_args(const stp_gaussians* g, const stp_params* p, const Plan&
     a.pix_state = (float*)(b + L.pix_state);
     a.dbg_nblend = L.dbg_nblend ? (uint32_t*)(b + L.dbg_nblend) : nullptr;
     a.dbg_hash = L.dbg_hash ? (unsigned long long*)(b + L.dbg_hash) : nullptr;
+    a.dbg_delta = L.dbg_delta ? (float*)(b + L.dbg_delta) : nullptr;
     a.sort_temp = b + L.scratch;
     a.sort_temp_bytes = stp::sort_hist_bytes();
     a.key_bits = L.key_bits;
@@ -248,66 +284,60 @@ __global__ void k_status_init(stp::Status* st, unsigned long long cap)
     for (int k = 0; k < 5; k++) st->counters[k] = 0;
 }
 
-stp_status check_scene(const stp_gaussians* g, int64_t expect_n)
+stp_status check_scene(const stp_gaussians& g, int s)
 {
-    if (!g) return fail(STP_ERR_ARG, "null Gaussian struct");
-    if (g->n != expect_n) return fail(STP_ERR_ARG, "inconsistent n");
-    if (g->sh_degree < 0 || g->sh_degree > 3) return fail(STP_ERR_ARG, "sh_degree must be 0..3");
-    if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh))
-        return fail(STP_ERR_ARG, "null Gaussian parameter array");
+    if (g.sh_degree < 0 || g.sh_degree > 3) return fail(STP_ERR_ARG, "scene %d: sh_degree must be 0..3", s);
+    if (g.n > 0 && (!g.means || !g.log_scales || !g.quats || !g.opacity_logits || !g.sh))
+        return fail(STP_ERR_ARG, "scene %d: null Gaussian parameter array", s);
     return STP_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-const char* stp_last_error(void) { return g_err.c_str(); }
-
-int32_t stp_version(void) { return 0x000100; }
-
-stp_status stp_workspace_layout_get(int64_t n, const stp_camera* cams, int32_t nviews, const stp_params* prm,
-                                    stp_workspace_layout* out)
+// Validates the scenes, builds the plan and fills the scene table's input pointers.
+stp_status prepare(const stp_gaussians* scenes, int32_t nscenes, const int32_t* vps, const stp_camera* cams,
+                   int32_t nviews, const stp_params* prm, size_t ws_bytes, const void* workspace, Plan& P)
 {
-    stp_status st = check(n, cams, nviews, prm);
+    if (!scenes) return fail(STP_ERR_ARG, "null Gaussian struct");
+    if (nscenes < 1 || nscenes > stp::kMaxScenes)
+        return fail(STP_ERR_ARG, "nscenes = %d out of range [1, %d]", nscenes, stp::kMaxScenes);
+    std::vector<int64_t> ns(nscenes);
+    for (int s = 0; s < nscenes; s++) ns[s] = scenes[s].n;
+    stp_status st = check(ns.data(), vps, nscenes, cams, nviews, prm);
     if (st != STP_OK) return st;
-    if (!out) return fail(STP_ERR_ARG, "null layout pointer");
-    Plan P;
-    make_plan(n, cams, nviews, prm, P);
-    *out = P.L;
-    return STP_OK;
-}
-
-size_t stp_workspace_size(int64_t n, const stp_camera* cams, int32_t nviews, const stp_params* prm)
-{
-    stp_workspace_layout L;
-    if (stp_workspace_layout_get(n, cams, nviews, prm, &L) != STP_OK) return 0;
-    return L.total;
-}
-
-stp_status stp_render(const stp_gaussians* g, const stp_camera* cams, int32_t nviews, const stp_params* prm,
-                      void* workspace, size_t ws_bytes, float* rgb, float* depth, float* tfinal, void* stream)
-{
-    g_err.clear();
-    if (!g) return fail(STP_ERR_ARG, "null Gaussian struct");
-    stp_status st = check(g->n, cams, nviews, prm);
-    if (st != STP_OK) return st;
-    if ((st = check_scene(g, g->n)) != STP_OK) return st;
-    Plan P;
-    make_plan(g->n, cams, nviews, prm, P);
+    for (int s = 0; s < nscenes; s++)
+        if ((st = check_scene(scenes[s], s)) != STP_OK) return st;
+    make_plan(ns.data(), vps, nscenes, cams, nviews, prm, P);
     if (!workspace || ws_bytes < P.L.total)
         return fail(STP_ERR_ARG, "workspace of %zu bytes, %zu needed", ws_bytes, P.L.total);
+    for (int s = 0; s < nscenes; s++) {
+        stp::SceneDesc& S = P.scenes[s];
+        const stp_gaussians& g = scenes[s];
+        S.means = g.means; S.log_scales = g.log_scales; S.quats = g.quats;
+        S.logits = g.opacity_logits; S.sh = g.sh;
+        S.sh_k = (g.sh_degree + 1) * (g.sh_degree + 1);
+    }
+    return STP_OK;
+}
+
+stp_status render_impl(const stp_gaussians* scenes, int32_t nscenes, const int32_t* vps, const stp_camera* cams,
+                       int32_t nviews, const stp_params* prm, void* workspace, size_t ws_bytes, float* rgb,
+                       float* depth, float* tfinal, void* stream)
+{
+    g_err.clear();
+    Plan P;
+    stp_status st = prepare(scenes, nscenes, vps, cams, nviews, prm, ws_bytes, workspace, P);
+    if (st != STP_OK) return st;
     if (!rgb || !depth) return fail(STP_ERR_ARG, "null rgb or depth output");
     cudaStream_t s = (cudaStream_t)stream;
-    stp::PipeArgs a = make_args(g, prm, P, workspace);
+    stp::PipeArgs a = make_args(prm, P, workspace);
     a.rgb = rgb;
     a.depth = depth;
     a.tfinal_out = tfinal;
     cudaError_t e;
     prof_mark(0, s);
     k_status_init<<<1, 1, 0, s>>>(a.status, a.capacity);
-    if ((e = stp::launch_views_init(P.views.data(), nviews, const_cast<stp::ViewDesc*>(a.views), s)) != cudaSuccess)
-        return cuda_fail(e, "view table");
+    if ((e = stp::launch_tables_init(P.views.data(), nviews, const_cast<stp::ViewDesc*>(a.views), P.scenes.data(),
+                                     nscenes, const_cast<stp::SceneDesc*>(a.scenes), s)) != cudaSuccess)
+        return cuda_fail(e, "view and scene tables");
     if (a.partitioned) {
         if ((e = cudaMemsetAsync(a.tile_counts, 0, (size_t)a.total_tiles * 4, s)) != cudaSuccess ||
             (e = cudaMemsetAsync(a.tile_cursor, 0, (size_t)a.total_tiles * 4, s)) != cudaSuccess)
@@ -339,32 +369,37 @@ stp_status stp_render(const stp_gaussians* g, const stp_camera* cams, int32_t nv
     return STP_OK;
 }
 
-stp_status stp_render_backward(const stp_gaussians* g, const stp_camera* cams, int32_t nviews,
-                               const stp_params* prm, void* workspace, size_t ws_bytes, const float* d_rgb,
-                               const float* d_depth, const stp_gaussians_grad* grad, void* stream)
+stp_status backward_impl(const stp_gaussians* scenes, int32_t nscenes, const int32_t* vps, const stp_camera* cams,
+                         int32_t nviews, const stp_params* prm, void* workspace, size_t ws_bytes,
+                         const float* d_rgb, const float* d_depth, const stp_gaussians_grad* grads, void* stream)
 {
     g_err.clear();
-    if (!g) return fail(STP_ERR_ARG, "null Gaussian struct");
-    stp_status st = check(g->n, cams, nviews, prm);
-    if (st != STP_OK) return st;
-    if ((st = check_scene(g, g->n)) != STP_OK) return st;
-    if (!(prm->flags & kFlagBackward))
+    if (prm && !(prm->flags & kFlagBackward))
         return fail(STP_ERR_ARG, "the forward pass must reserve backward scratch (flag 64)");
+    if (prm && prm->mode != STP_MODE_HIER)
+        return fail(STP_ERR_NOT_SUPPORTED, "the backward pass replays the hierarchical order only (STP_MODE_HIER)");
     Plan P;
-    make_plan(g->n, cams, nviews, prm, P);
-    if (!workspace || ws_bytes < P.L.total)
-        return fail(STP_ERR_ARG, "workspace of %zu bytes, %zu needed", ws_bytes, P.L.total);
-    if (!d_rgb || !grad || (g->n > 0 && (!grad->means || !grad->log_scales || !grad->quats ||
-                                         !grad->opacity_logits || !grad->sh)))
-        return fail(STP_ERR_ARG, "null gradient input or output");
+    stp_status st = prepare(scenes, nscenes, vps, cams, nviews, prm, ws_bytes, workspace, P);
+    if (st != STP_OK) return st;
+    if (!d_rgb || !grads) return fail(STP_ERR_ARG, "null gradient input or output");
+    for (int sc = 0; sc < nscenes; sc++) {
+        const stp_gaussians_grad& gr = grads[sc];
+        if (scenes[sc].n > 0 && (!gr.means || !gr.log_scales || !gr.quats || !gr.opacity_logits || !gr.sh))
+            return fail(STP_ERR_ARG, "scene %d: null gradient array", sc);
+        stp::SceneDesc& S = P.scenes[sc];
+        S.g_means = gr.means; S.g_log_scales = gr.log_scales; S.g_quats = gr.quats;
+        S.g_logits = gr.opacity_logits; S.g_sh = gr.sh;
+    }
     cudaStream_t s = (cudaStream_t)stream;
-    stp::PipeArgs a = make_args(g, prm, P, workspace);
+    stp::PipeArgs a = make_args(prm, P, workspace);
     a.d_rgb = d_rgb;
     a.d_depth = d_depth;
-    a.g_means = grad->means; a.g_log_scales = grad->log_scales; a.g_quats = grad->quats;
-    a.g_logits = grad->opacity_logits; a.g_sh = grad->sh;
     cudaError_t e;
-    for (int k = 0; k <= 5; k++) prof_mark(k, s);
+    for (int k = 0; k <= 4; k++) prof_mark(k, s);
+    if ((e = stp::launch_tables_init(P.views.data(), nviews, const_cast<stp::ViewDesc*>(a.views), P.scenes.data(),
+                                     nscenes, const_cast<stp::SceneDesc*>(a.scenes), s)) != cudaSuccess)
+        return cuda_fail(e, "view and scene tables");
+    prof_mark(5, s);
     if ((e = cudaMemsetAsync(a.grad_geom, 0, (size_t)P.m * stp::kGradStride * 4, s)) != cudaSuccess)
         return cuda_fail(e, "clear gradient scratch");
     prof_mark(6, s);
@@ -374,6 +409,76 @@ stp_status stp_render_backward(const stp_gaussians* g, const stp_camera* cams, i
     prof_mark(8, s);
     prof_finish(1);
     return STP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* stp_last_error(void) { return g_err.c_str(); }
+
+int32_t stp_version(void) { return 0x000200; }
+
+stp_status stp_workspace_layout_batched(const int64_t* n, const int32_t* views_per_scene, int32_t nscenes,
+                                        const stp_camera* cams, int32_t nviews, const stp_params* prm,
+                                        stp_workspace_layout* out)
+{
+    stp_status st = check(n, views_per_scene, nscenes, cams, nviews, prm);
+    if (st != STP_OK) return st;
+    if (!out) return fail(STP_ERR_ARG, "null layout pointer");
+    Plan P;
+    make_plan(n, views_per_scene, nscenes, cams, nviews, prm, P);
+    *out = P.L;
+    return STP_OK;
+}
+
+size_t stp_workspace_size_batched(const int64_t* n, const int32_t* views_per_scene, int32_t nscenes,
+                                  const stp_camera* cams, int32_t nviews, const stp_params* prm)
+{
+    stp_workspace_layout L;
+    if (stp_workspace_layout_batched(n, views_per_scene, nscenes, cams, nviews, prm, &L) != STP_OK) return 0;
+    return L.total;
+}
+
+stp_status stp_workspace_layout_get(int64_t n, const stp_camera* cams, int32_t nviews, const stp_params* prm,
+                                    stp_workspace_layout* out)
+{
+    return stp_workspace_layout_batched(&n, &nviews, 1, cams, nviews, prm, out);
+}
+
+size_t stp_workspace_size(int64_t n, const stp_camera* cams, int32_t nviews, const stp_params* prm)
+{
+    return stp_workspace_size_batched(&n, &nviews, 1, cams, nviews, prm);
+}
+
+stp_status stp_render(const stp_gaussians* g, const stp_camera* cams, int32_t nviews, const stp_params* prm,
+                      void* workspace, size_t ws_bytes, float* rgb, float* depth, float* tfinal, void* stream)
+{
+    return render_impl(g, 1, &nviews, cams, nviews, prm, workspace, ws_bytes, rgb, depth, tfinal, stream);
+}
+
+stp_status stp_render_batched(const stp_gaussians* scenes, int32_t nscenes, const int32_t* views_per_scene,
+                              const stp_camera* cams, int32_t nviews, const stp_params* prm, void* workspace,
+                              size_t ws_bytes, float* rgb, float* depth, float* tfinal, void* stream)
+{
+    return render_impl(scenes, nscenes, views_per_scene, cams, nviews, prm, workspace, ws_bytes, rgb, depth,
+                       tfinal, stream);
+}
+
+stp_status stp_render_backward(const stp_gaussians* g, const stp_camera* cams, int32_t nviews,
+                               const stp_params* prm, void* workspace, size_t ws_bytes, const float* d_rgb,
+                               const float* d_depth, const stp_gaussians_grad* grad, void* stream)
+{
+    return backward_impl(g, 1, &nviews, cams, nviews, prm, workspace, ws_bytes, d_rgb, d_depth, grad, stream);
+}
+
+stp_status stp_render_backward_batched(const stp_gaussians* scenes, int32_t nscenes, const int32_t* views_per_scene,
+                                       const stp_camera* cams, int32_t nviews, const stp_params* prm,
+                                       void* workspace, size_t ws_bytes, const float* d_rgb, const float* d_depth,
+                                       const stp_gaussians_grad* grads, void* stream)
+{
+    return backward_impl(scenes, nscenes, views_per_scene, cams, nviews, prm, workspace, ws_bytes, d_rgb, d_depth,
+                         grads, stream);
 }
 
 stp_status stp_read_status(const void* workspace, stp_run_status* out, void* stream)

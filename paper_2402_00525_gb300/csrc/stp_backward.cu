@@ -62,11 +62,13 @@ __device__ __forceinline__ void sh_basis_grad(float x, float y, float z, int K, 
 
 __global__ void __launch_bounds__(128) k_backward_pre(PipeArgs a)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
-    const int K = a.sh_k;
-    float mu[3] = {a.means[3 * i], a.means[3 * i + 1], a.means[3 * i + 2]};
-    float q[4] = {a.quats[4 * i], a.quats[4 * i + 1], a.quats[4 * i + 2], a.quats[4 * i + 3]};
+    const long long t0 = (long long)blockIdx.x * blockDim.x;
+    const SceneDesc& S = a.scenes[scene_of(a, t0)];
+    const int i = (int)(t0 - S.thread_off) + threadIdx.x;
+    if (i >= S.n) return;
+    const int K = S.sh_k;
+    float mu[3] = {S.means[3 * i], S.means[3 * i + 1], S.means[3 * i + 2]};
+    float q[4] = {S.quats[4 * i], S.quats[4 * i + 1], S.quats[4 * i + 2], S.quats[4 * i + 3]};
     const float ql = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
     const float qw = q[0] / ql, qx = q[1] / ql, qy = q[2] / ql, qz = q[3] / ql;
     const float Rq[3][3] = {{1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy)},
@@ -75,7 +77,7 @@ __global__ void __launch_bounds__(128) k_backward_pre(PipeArgs a)
     float sc[3], si[3];
     bool unclamped[3];
     for (int k = 0; k < 3; k++) {
-        const float ls = a.log_scales[3 * i + k];
+        const float ls = S.log_scales[3 * i + k];
         sc[k] = expf(ls);
         const float s_inv = expf(-ls);
         unclamped[k] = s_inv < a.inv_scale_max;
@@ -87,8 +89,8 @@ __global__ void __launch_bounds__(128) k_backward_pre(PipeArgs a)
             Sig[r][c] = 0.f;
             for (int k = 0; k < 3; k++) Sig[r][c] += Rq[r][k] * sc[k] * sc[k] * Rq[c][k];
         }
-    const float opac = 1.f / (1.f + expf(-a.logits[i]));
-    const float* shc = a.sh + (long long)i * K * 3;
+    const float opac = 1.f / (1.f + expf(-S.logits[i]));
+    const float* shc = S.sh + (long long)i * K * 3;
 
     float dmu[3] = {0.f, 0.f, 0.f}, dls[3] = {0.f, 0.f, 0.f}, dlogit = 0.f;
     float dRq[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
@@ -98,7 +100,7 @@ __global__ void __launch_bounds__(128) k_backward_pre(PipeArgs a)
     for (int k = 0; k < 48; k++) dsh[k] = 0.f;
     bool any = false;
 
-    for (int v = 0; v < a.nviews; v++) {
+    for (int v = S.view_begin; v < S.view_end; v++) {
         const ViewDesc& V = a.views[v];
         const long long ri = V.rec_off + i;
         if (a.geom[kRecFloat4 * ri + 2].x == 0.f) continue;      // invisible in this view
@@ -239,20 +241,20 @@ __global__ void __launch_bounds__(128) k_backward_pre(PipeArgs a)
     const float dot = gq[0] * qw + gq[1] * qx + gq[2] * qy + gq[3] * qz;
     const float qn[4] = {qw, qx, qy, qz};
     for (int k = 0; k < 3; k++) {
-        a.g_means[3 * i + k] += dmu[k];
-        a.g_log_scales[3 * i + k] += dls[k];
+        S.g_means[3 * i + k] += dmu[k];
+        S.g_log_scales[3 * i + k] += dls[k];
     }
-    for (int k = 0; k < 4; k++) a.g_quats[4 * i + k] += (gq[k] - dot * qn[k]) / ql;
-    a.g_logits[i] += dlogit;
-    for (int k = 0; k < 3 * K; k++) a.g_sh[(long long)i * K * 3 + k] += dsh[k];
+    for (int k = 0; k < 4; k++) S.g_quats[4 * i + k] += (gq[k] - dot * qn[k]) / ql;
+    S.g_logits[i] += dlogit;
+    for (int k = 0; k < 3 * K; k++) S.g_sh[(long long)i * K * 3 + k] += dsh[k];
 }
 
 }  // namespace
 
 cudaError_t launch_backward_preprocess(const PipeArgs& a, cudaStream_t s)
 {
-    if (a.n == 0) return cudaSuccess;
-    k_backward_pre<<<(a.n + 127) / 128, 128, 0, s>>>(a);
+    if (a.threads == 0) return cudaSuccess;
+    k_backward_pre<<<(unsigned)(a.threads / 128), 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 

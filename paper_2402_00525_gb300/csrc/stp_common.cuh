@@ -14,7 +14,15 @@ namespace stp {
 
 constexpr uint32_t kInvalidKey = 0xFFFFFFFFu;   // culled entry / empty queue slot
 constexpr int kTile = 16;
-constexpr int kMaxViews = 64;                    // views per launch sequence
+constexpr int kMaxViews = 64;                    // views per launch sequence (all scenes)
+constexpr int kMaxScenes = 64;
+constexpr int STP_MODE_HIER_ID = 0;              // stp_params.mode values (include/stp.h)
+constexpr int STP_MODE_FULL_ID = 1;
+constexpr int STP_MODE_GLOBAL_ID = 2;
+constexpr int STP_MODE_WINDOW_ID = 3;
+constexpr int kFlagNoTileCull = 512;             // ablation D: Duplicate keeps every rectangle tile
+constexpr int kFlagNoHierCull = 1024;            // ablation E: no culling at the 4x4 / 2x2 levels                   // scenes per launch sequence
+constexpr int kSceneAlign = 256;                 // first thread of each scene: multiple of this
 constexpr int kMaxMid = 20;                      // largest supported mid-queue size
 constexpr uint64_t kHashInit = 1469598103934665603ULL;
 constexpr uint64_t kHashMul = 1099511628211ULL;
@@ -39,7 +47,27 @@ struct ViewDesc {
     int tile_off;                // first global tile id of this view
     int pad;
     long long pix_off;           // first pixel of this view in the packed image arrays
-    long long rec_off;           // view * N: first render record of this view
+    long long rec_off;           // first render record of this view (sum of N over earlier views)
+};
+
+// ---------------------------------------------------------------- per-scene constants
+// The per-Gaussian kernels run one thread per (scene, Gaussian); each scene starts on a
+// kSceneAlign boundary of the thread index space, so a thread block never straddles two scenes
+// and every warp loops over the same views.
+struct SceneDesc {
+    const float* means;          // [n][3]
+    const float* log_scales;     // [n][3]
+    const float* quats;          // [n][4] (w, x, y, z)
+    const float* logits;         // [n]
+    const float* sh;             // [n][sh_k][3]
+    float* g_means;              // gradients (backward only; null in the forward pass)
+    float* g_log_scales;
+    float* g_quats;
+    float* g_logits;
+    float* g_sh;
+    int n, sh_k;
+    int view_begin, view_end;    // the scene's views [view_begin, view_end)
+    long long thread_off;        // first thread of the scene (multiple of kSceneAlign)
 };
 
 // ---------------------------------------------------------------- render record
@@ -198,6 +226,20 @@ __device__ __forceinline__ bool box_keep_depth(const Rec& r, const Box& b, const
     const float y = centre_ray ? __fmul_rn(0.5f, __fadd_rn(b.y0, b.y1)) : __fadd_rn(r.r0.y, __fadd_rn(r.r0.w, d.y));
     *t = depth_uv(r, to_u(V, x), to_w(V, y));
     return true;
+}
+
+// Raise a kernel's dynamic shared-memory limit once per device (host side). Later launches,
+// including launches recorded under stream capture, then make no attribute call.
+template <typename F>
+inline cudaError_t ensure_smem_limit(F* fn, size_t bytes, int* done_per_device, int ndev)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < ndev && done_per_device[dev] >= (int)bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess && dev >= 0 && dev < ndev) done_per_device[dev] = (int)bytes;
+    return e;
 }
 
 __device__ __forceinline__ unsigned lanemask_lt()

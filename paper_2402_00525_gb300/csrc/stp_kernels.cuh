@@ -10,13 +10,12 @@
 namespace stp {
 
 struct PipeArgs {
-    // inputs (device, caller owned)
-    const float* means;
-    const float* log_scales;
-    const float* quats;
-    const float* logits;
-    const float* sh;
-    int n, sh_k, nviews, lb_threshold, flags, mode, window_k, tail, mid, head;
+    // inputs: the scene table (device copy in the workspace; pointers caller owned)
+    const SceneDesc* scenes;
+    int nscenes;
+    long long threads;       // per-Gaussian thread count: sum over scenes of n rounded up to kSceneAlign
+    long long m;             // render records: sum over views of the view's scene size
+    int nviews, lb_threshold, flags, mode, window_k, tail, mid, head;
     float eps_o, t_min, alpha_max, inv_scale_max, dilation, znear;
     float bg[3];
     int total_tiles;
@@ -24,7 +23,7 @@ struct PipeArgs {
     // workspace regions
     const ViewDesc* views;
     Status* status;
-    float4* geom;            // [V*N*kRecFloat4]
+    float4* geom;            // [m*kRecFloat4]
     float4* color;           // [V*N]
     ushort4* rect;           // [V*N]
     uint32_t* counts;        // [V*N]
@@ -51,6 +50,7 @@ struct PipeArgs {
     uint32_t* dbg_nblend;    // [total_pixels] or null
     unsigned long long* dbg_hash;   // [total_pixels] or null
     int* dbg_trace;          // [total_pixels][kTraceLen] or null
+    float* dbg_delta;        // [total_pixels] per-pixel sort error or null
     void* sort_temp;
     size_t sort_temp_bytes;
     int key_bits;
@@ -61,19 +61,27 @@ struct PipeArgs {
     // backward
     const float* d_rgb;
     const float* d_depth;
-    float* grad_geom;        // [V*N*kGradStride] per-(view, Gaussian) 2D gradients
-    float* g_means;
-    float* g_log_scales;
-    float* g_quats;
-    float* g_logits;
-    float* g_sh;
+    float* grad_geom;        // [m*kGradStride] per-(view, Gaussian) 2D gradients
 };
+
+// Scene of the thread block whose first thread is t0 (largest s with thread_off <= t0).
+__device__ __forceinline__ int scene_of(const PipeArgs& a, long long t0)
+{
+    int lo = 0, hi = a.nscenes - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.scenes[mid].thread_off <= t0) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
 
 constexpr int kTraceLen = 64;
 constexpr int kGradStride = 24;   // dmean2(2) dconic(3) dopacity(1) dcolour(3) pad(3) dm(9) dc(3)
 
-cudaError_t launch_views_init(const ViewDesc* host_views, int nviews, ViewDesc* dev_views,
-                              cudaStream_t s);
+cudaError_t launch_tables_init(const ViewDesc* host_views, int nviews, ViewDesc* dev_views,
+                               const SceneDesc* host_scenes, int nscenes, SceneDesc* dev_scenes,
+                               cudaStream_t s);
 cudaError_t launch_preprocess(const PipeArgs& a, cudaStream_t s);
 cudaError_t launch_scan_counts(const PipeArgs& a, cudaStream_t s);
 cudaError_t launch_scan_tiles(const PipeArgs& a, cudaStream_t s);

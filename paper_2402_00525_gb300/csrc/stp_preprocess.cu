@@ -69,27 +69,31 @@ struct GaussIn {             // view-independent quantities of one Gaussian
     float Rq[9];             // rotation of the normalised quaternion (row major)
     float si[3];             // clamped inverse scales min(1/s, inv_scale_max)
     float opacity;
+    const float* sh;         // this Gaussian's SH coefficients [sh_k][3]
+    int sh_k;
 };
 
-__device__ __forceinline__ void load_gauss(const PipeArgs& a, int i, GaussIn& g)
+__device__ __forceinline__ void load_gauss(const PipeArgs& a, const SceneDesc& S, int i, GaussIn& g)
 {
-    g.mu[0] = __ldg(a.means + 3 * i);
-    g.mu[1] = __ldg(a.means + 3 * i + 1);
-    g.mu[2] = __ldg(a.means + 3 * i + 2);
-    float qw = __ldg(a.quats + 4 * i), qx = __ldg(a.quats + 4 * i + 1);
-    float qy = __ldg(a.quats + 4 * i + 2), qz = __ldg(a.quats + 4 * i + 3);
+    g.mu[0] = __ldg(S.means + 3 * i);
+    g.mu[1] = __ldg(S.means + 3 * i + 1);
+    g.mu[2] = __ldg(S.means + 3 * i + 2);
+    float qw = __ldg(S.quats + 4 * i), qx = __ldg(S.quats + 4 * i + 1);
+    float qy = __ldg(S.quats + 4 * i + 2), qz = __ldg(S.quats + 4 * i + 3);
     const float ql = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
     qw *= ql; qx *= ql; qy *= ql; qz *= ql;
     const float R[9] = {1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy),
                         2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx),
                         2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)};
     for (int k = 0; k < 3; k++) {
-        const float ls = __ldg(a.log_scales + 3 * i + k);
+        const float ls = __ldg(S.log_scales + 3 * i + k);
         g.s[k] = expf(ls);
         g.si[k] = fminf(expf(-ls), a.inv_scale_max);
     }
     for (int k = 0; k < 9; k++) g.Rq[k] = R[k];
-    g.opacity = 1.f / (1.f + expf(-__ldg(a.logits + i)));
+    g.opacity = 1.f / (1.f + expf(-__ldg(S.logits + i)));
+    g.sh = S.sh + (long long)i * S.sh_k * 3;
+    g.sh_k = S.sh_k;
 }
 
 // Per-(view, Gaussian) record (layout in stp_common.cuh). Returns false if invisible.
@@ -172,7 +176,7 @@ __device__ bool make_record(const PipeArgs& a, const ViewDesc& V, const GaussIn&
     float d[3] = {g.mu[0] - V.o[0], g.mu[1] - V.o[1], g.mu[2] - V.o[2]};
     const float dl = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     float rgb[3];
-    sh_colour(a.sh + (long long)i * a.sh_k * 3, a.sh_k, d[0] * dl, d[1] * dl, d[2] * dl, rgb);
+    sh_colour(g.sh, g.sh_k, d[0] * dl, d[1] * dl, d[2] * dl, rgb);
     col = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
     // opacity-aware radius (appendix B.2) and the rectangle of tiles holding a pixel centre
     // within [mean2 - r, mean2 + r]
@@ -213,10 +217,18 @@ __device__ __forceinline__ bool tile_depth_key(const PipeArgs& a, const ViewDesc
 {
     const Box b = block_box(tx * kTile, ty * kTile, kTile, V.W, V.H);
     float t = 0.f;
-    if (!box_keep_depth(r, b, V, a.eps_o, (a.flags & 4) != 0, &t)) return false;
+    if (a.flags & kFlagNoTileCull) t = box_depth(r, b, V, (a.flags & 4) != 0);
+    else if (!box_keep_depth(r, b, V, a.eps_o, (a.flags & 4) != 0, &t)) return false;
     if (a.flags & 8) t = r.r5.y;
     *dkey = fkey(t);
     return true;
+}
+
+// Tile-based culling decision (Sec. 3.4); flag kFlagNoTileCull keeps every tile of the
+// rectangle (ablation D of the paper's performance table).
+__device__ __forceinline__ bool tile_keep(const PipeArgs& a, const Rec& r, const Box& b)
+{
+    return (a.flags & kFlagNoTileCull) != 0 || box_keep(r, b, a.eps_o);
 }
 
 // Partitioned sort (appendix B.3): count a kept entry of global tile `gt`. Lanes of the
@@ -255,10 +267,6 @@ __device__ __forceinline__ void place_entry(const PipeArgs& a, uint32_t gt, uint
     if (pos < a.capacity) a.dup_keys[pos] = ((unsigned long long)dkey << 32) | gid;
 }
 
-// Count (EMIT = false) or write (EMIT = true) the kept tiles of this lane's Gaussian, with the
-// two-phase warp load balancing. Every lane of the warp must call it. With the global radix
-// sort the keys go to the Gaussian's own range [off, off + want) in tile order; with the
-// partitioned sort they go to their tiles' ranges.
 // depth key of a tile Preprocess found kept
 __device__ __forceinline__ uint32_t kept_depth_key(const PipeArgs& a, const ViewDesc& V, const Rec& r, int tx, int ty)
 {
@@ -290,7 +298,7 @@ __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, bool has, c
             for (int k = 0; k < ncand; k++) {
                 const int tx = rc.x + k % w, ty = rc.y + k / w;
                 const Box b = block_box(tx * kTile, ty * kTile, kTile, V.W, V.H);
-                if (box_keep(r, b, a.eps_o)) {
+                if (tile_keep(a, r, b)) {
                     cnt++;
                     if (k < 32) mask |= 1u << k;
                     if (part) count_entry(a, (uint32_t)(V.tile_off + ty * V.tiles_x + tx), false);
@@ -384,7 +392,7 @@ __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, bool has, c
                 const int tx = x0 + k % ws, ty = y0 + k / ws;
                 gt = (uint32_t)(V.tile_off + ty * V.tiles_x + tx);
                 if (EMIT) keep = tile_depth_key(a, V, rs, tx, ty, &dk);
-                else keep = box_keep(rs, block_box(tx * kTile, ty * kTile, kTile, V.W, V.H), a.eps_o);
+                else keep = tile_keep(a, rs, block_box(tx * kTile, ty * kTile, kTile, V.W, V.H));
             }
             const unsigned m = __ballot_sync(kFull, keep);
             if (keep) {
@@ -412,11 +420,13 @@ __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, bool has, c
 
 __global__ void __launch_bounds__(256) k_preprocess(PipeArgs a)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = i < a.n;
+    const long long t0 = (long long)blockIdx.x * blockDim.x;
+    const SceneDesc S = a.scenes[scene_of(a, t0)];
+    const int i = (int)(t0 - S.thread_off) + threadIdx.x;
+    const bool live = i < S.n;
     GaussIn g;
-    if (live) load_gauss(a, i, g);
-    for (int v = 0; v < a.nviews; v++) {
+    if (live) load_gauss(a, S, i, g);
+    for (int v = S.view_begin; v < S.view_end; v++) {
         const ViewDesc& V = a.views[v];
         Rec r;
         float4 col;
@@ -440,9 +450,12 @@ __global__ void __launch_bounds__(256) k_preprocess(PipeArgs a)
 
 __global__ void __launch_bounds__(256) k_duplicate(PipeArgs a)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = i < a.n;
-    for (int v = 0; v < a.nviews; v++) {
+    const long long t0 = (long long)blockIdx.x * blockDim.x;
+    const SceneDesc& S = a.scenes[scene_of(a, t0)];
+    const int i = (int)(t0 - S.thread_off) + threadIdx.x;
+    const bool live = i < S.n;
+    const int vb = S.view_begin, ve = S.view_end;
+    for (int v = vb; v < ve; v++) {
         const ViewDesc& V = a.views[v];
         const long long o = V.rec_off + i;
         Rec r;
@@ -561,30 +574,37 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* __r
     }
 }
 
-struct ViewPack { ViewDesc v[kMaxViews]; };
+struct TablePack {
+    ViewDesc v[kMaxViews];
+    SceneDesc sc[kMaxScenes];
+};
 
-__global__ void k_views_copy(ViewPack pack, int nviews, ViewDesc* dst)
+__global__ void k_tables_copy(TablePack pack, int nviews, ViewDesc* dv, int nscenes, SceneDesc* ds)
 {
     const int k = threadIdx.x;
-    if (k < nviews) dst[k] = pack.v[k];
+    if (k < nviews) dv[k] = pack.v[k];
+    if (k < nscenes) ds[k] = pack.sc[k];
 }
 
 }  // namespace
 
 size_t scan_partials_count(long long m) { return (size_t)((m + kScanTile - 1) / kScanTile) + 1; }
 
-cudaError_t launch_views_init(const ViewDesc* host_views, int nviews, ViewDesc* dev_views, cudaStream_t s)
+cudaError_t launch_tables_init(const ViewDesc* host_views, int nviews, ViewDesc* dev_views,
+                               const SceneDesc* host_scenes, int nscenes, SceneDesc* dev_scenes, cudaStream_t s)
 {
-    ViewPack pack;
+    static_assert(sizeof(TablePack) <= 32000, "kernel parameter block too large");
+    TablePack pack;
     for (int k = 0; k < nviews && k < kMaxViews; k++) pack.v[k] = host_views[k];
-    k_views_copy<<<1, kMaxViews, 0, s>>>(pack, nviews, dev_views);
+    for (int k = 0; k < nscenes && k < kMaxScenes; k++) pack.sc[k] = host_scenes[k];
+    k_tables_copy<<<1, kMaxViews, 0, s>>>(pack, nviews, dev_views, nscenes, dev_scenes);
     return cudaGetLastError();
 }
 
 cudaError_t launch_preprocess(const PipeArgs& a, cudaStream_t s)
 {
-    if (a.n == 0) return cudaSuccess;
-    k_preprocess<<<(a.n + 255) / 256, 256, 0, s>>>(a);
+    if (a.threads == 0) return cudaSuccess;
+    k_preprocess<<<(unsigned)(a.threads / 256), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -600,7 +620,7 @@ static cudaError_t scan_u32(const uint32_t* in, uint32_t* out, unsigned long lon
 
 cudaError_t launch_scan_counts(const PipeArgs& a, cudaStream_t s)
 {
-    return scan_u32(a.counts, a.offsets, a.scan_partials, (long long)a.n * a.nviews, a.status, s);
+    return scan_u32(a.counts, a.offsets, a.scan_partials, a.m, a.status, s);
 }
 
 cudaError_t launch_scan_tiles(const PipeArgs& a, cudaStream_t s)
@@ -610,8 +630,8 @@ cudaError_t launch_scan_tiles(const PipeArgs& a, cudaStream_t s)
 
 cudaError_t launch_duplicate(const PipeArgs& a, cudaStream_t s)
 {
-    if (a.n == 0) return cudaSuccess;
-    k_duplicate<<<(a.n + 255) / 256, 256, 0, s>>>(a);
+    if (a.threads == 0) return cudaSuccess;
+    k_duplicate<<<(unsigned)(a.threads / 256), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -57,6 +57,7 @@ struct Px {
     float hv[HEAD + 1];          // opacity * G2 at the pixel (before the alpha_max clamp)
     uint32_t nbl;
     unsigned long long hash;
+    float last_t, delta;         // debug: sort error (sum of backward steps of the blended t_opt)
 };
 
 struct PixCtx {
@@ -134,6 +135,10 @@ __device__ __forceinline__ void blend(const PipeArgs& a, const ViewDesc& V, Px<H
         }
     }
     if (!BWD && a.dbg_trace && s.nbl < (uint32_t)kTraceLen) a.dbg_trace[c.pix * kTraceLen + s.nbl] = (int)id;
+    if (!BWD && a.dbg_delta) {
+        if (s.nbl > 0 && s.last_t > t) s.delta += s.last_t - t;
+        s.last_t = t;
+    }
     s.T = Tn;
     s.nbl++;
     if (a.dbg_hash) s.hash = s.hash * kHashMul + (unsigned long long)(id + 1u);
@@ -230,6 +235,7 @@ __device__ void midstage(const PipeArgs& a, const ViewDesc& V, Px<HEAD>& s, cons
     const int cmax = max(c0, c1);
     const int MID = a.mid;
     const bool centre = (a.flags & 2) != 0;
+    const bool nocull = (a.flags & kFlagNoHierCull) != 0;
     // a quad whose four pixels are saturated takes no further part (its results are final)
     const unsigned live = __ballot_sync(kFull, !s.done);
     const bool qlive = qval && ((live >> qbase) & 0xFu) != 0;
@@ -242,7 +248,8 @@ __device__ void midstage(const PipeArgs& a, const ViewDesc& V, Px<HEAD>& s, cons
                 const Rec r = load_rec(a.geom, V.rec_off + gid);
                 const Box bq = bQ;
                 float t;
-                if (box_keep_depth(r, bq, V, a.eps_o, centre, &t)) key = depth_key(t);
+                if (nocull) key = depth_key(box_depth(r, bq, V, centre));
+                else if (box_keep_depth(r, bq, V, a.eps_o, centre, &t)) key = depth_key(t);
             }
         }
         // stable rank of the new entry among the quad's (up to) four
@@ -385,6 +392,8 @@ __global__ void __launch_bounds__(256) k_render(PipeArgs a)
     s.nh = 0;
     s.nbl = 0;
     s.hash = kHashInit;
+    s.last_t = 0.f;
+    s.delta = 0.f;
 #pragma unroll
     for (int j = 0; j <= HEAD; j++) {
         s.hk[j] = kInvalidKey;
@@ -399,6 +408,7 @@ __global__ void __launch_bounds__(256) k_render(PipeArgs a)
     const uint2 rg = a.ranges[gtile];
     const int lst = (int)rg.x, nL = (int)(rg.y - rg.x);
     const bool centre = (a.flags & 2) != 0;
+    const bool nocull = (a.flags & kFlagNoHierCull) != 0;
     const bool count = a.dbg_nblend != nullptr && !BWD;
     unsigned long long n_eval_s = 0, n_surv_s = 0;
     bool finished = false;
@@ -417,8 +427,13 @@ __global__ void __launch_bounds__(256) k_render(PipeArgs a)
         if (in && (s0 || s1)) {
             const Rec r = load_rec(a.geom, V.rec_off + gid);
             float t;
-            if (s0 && box_keep_depth(r, bS[0], V, a.eps_o, centre, &t)) k0 = depth_key(t);
-            if (s1 && box_keep_depth(r, bS[1], V, a.eps_o, centre, &t)) k1 = depth_key(t);
+            if (nocull) {
+                if (s0) k0 = depth_key(box_depth(r, bS[0], V, centre));
+                if (s1) k1 = depth_key(box_depth(r, bS[1], V, centre));
+            } else {
+                if (s0 && box_keep_depth(r, bS[0], V, a.eps_o, centre, &t)) k0 = depth_key(t);
+                if (s1 && box_keep_depth(r, bS[1], V, a.eps_o, centre, &t)) k1 = depth_key(t);
+            }
         }
         uint32_t r0 = 0, r1 = 0;
 #pragma unroll 8
@@ -491,6 +506,7 @@ __global__ void __launch_bounds__(256) k_render(PipeArgs a)
         if (a.tfinal_out) a.tfinal_out[p] = s.T;
         if (a.dbg_nblend) a.dbg_nblend[p] = s.nbl;
         if (a.dbg_hash) a.dbg_hash[p] = s.hash;
+        if (a.dbg_delta) a.dbg_delta[p] = s.delta;
     } else {
         if (a.dbg_nblend && a.dbg_nblend[p] != s.nbl) atomicOr(&a.status->error_bits, 8u);
     }
@@ -499,13 +515,197 @@ __global__ void __launch_bounds__(256) k_render(PipeArgs a)
 template <int HEAD>
 cudaError_t launch_head(const PipeArgs& a, bool bwd, size_t smem, cudaStream_t s)
 {
+    static int set_fwd[64], set_bwd[64];
+    cudaError_t e;
     if (bwd) {
-        cudaFuncSetAttribute(k_render<HEAD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if ((e = ensure_smem_limit(k_render<HEAD, true>, smem, set_bwd, 64)) != cudaSuccess) return e;
         k_render<HEAD, true><<<a.total_tiles, 256, smem, s>>>(a);
     } else {
-        cudaFuncSetAttribute(k_render<HEAD, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if ((e = ensure_smem_limit(k_render<HEAD, false>, smem, set_fwd, 64)) != cudaSuccess) return e;
         k_render<HEAD, false><<<a.total_tiles, 256, smem, s>>>(a);
     }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- flat per-pixel modes
+// The comparison orders of Sec. 3.3 / 4.2 over the same sorted tile lists (forward only):
+//   GLOBAL   blend every entry with alpha >= eps_O in tile-list order (the global sort alone);
+//   WINDOW-k the per-pixel k-buffer alone: insert into a HEAD-entry window in list order and
+//            blend the nearest when it overflows (the hierarchy's head queue without the
+//            tail and mid levels);
+//   FULL     the exact per-ray order: every entry with alpha >= eps_O by (t_opt at the pixel,
+//            list position). Computed by peeling: each pass over the list keeps the HEAD
+//            smallest (key, position) pairs above the last blended one and blends them.
+// One 256-thread block per 16x16 tile, one thread per pixel (row major); the tile's records
+// are staged in shared memory 256 at a time and every pixel evaluates them in list order.
+constexpr int kFlatBatch = 256;
+
+__device__ __forceinline__ void flat_init(const PipeArgs& a, const ViewDesc& V, int pxi, int pyi, PixCtx& c)
+{
+    c.xc = pxi + 0.5f;
+    c.yc = pyi + 0.5f;
+    c.u = to_u(V, c.xc);
+    c.w = to_w(V, c.yc);
+    c.n = ray_norm(c.u, c.w);
+    c.pix = (pxi < V.W && pyi < V.H) ? V.pix_off + (long long)pyi * V.W + pxi : -1;
+    c.g0 = c.g1 = c.g2 = c.gz = c.gbg = 0.f;
+    c.Cf0 = c.Cf1 = c.Cf2 = c.Zf = c.Tf = 0.f;
+}
+
+template <int HEAD>
+__device__ __forceinline__ void px_init(Px<HEAD>& s, bool inside)
+{
+    s.T = 1.f;
+    s.C0 = s.C1 = s.C2 = s.Z = 0.f;
+    s.done = !inside;
+    s.nh = 0;
+    s.nbl = 0;
+    s.hash = kHashInit;
+    s.last_t = 0.f;
+    s.delta = 0.f;
+#pragma unroll
+    for (int j = 0; j <= HEAD; j++) {
+        s.hk[j] = kInvalidKey;
+        s.hid[j] = 0;
+        s.hv[j] = 0.f;
+    }
+}
+
+template <int HEAD>
+__global__ void __launch_bounds__(256) k_render_flat(PipeArgs a)
+{
+    __shared__ float4 srec[kFlatBatch * kRecFloat4];
+    __shared__ uint32_t sid[kFlatBatch];
+    if (a.status->error_bits & 1u) return;
+    const int gtile = blockIdx.x;
+    int lo = 0, hi = a.nviews - 1;
+    while (lo < hi) {
+        const int m = (lo + hi + 1) >> 1;
+        if (a.views[m].tile_off <= gtile) lo = m; else hi = m - 1;
+    }
+    const ViewDesc& V = a.views[lo];
+    const int tile = gtile - V.tile_off;
+    const int tx = tile % V.tiles_x, ty = tile / V.tiles_x;
+    const int pxi = tx * kTile + (threadIdx.x & 15), pyi = ty * kTile + (threadIdx.x >> 4);
+    PixCtx c;
+    flat_init(a, V, pxi, pyi, c);
+    const bool inside = c.pix >= 0;
+    Px<HEAD> s;
+    px_init(s, inside);
+    const uint2 rg = a.ranges[gtile];
+    const int lst = (int)rg.x, nL = (int)(rg.y - rg.x);
+    const int mode = a.mode;
+    const bool evict_first = (a.flags & 1) != 0;
+    const bool count = a.dbg_nblend != nullptr;
+    unsigned long long n_eval = 0;
+    // FULL: the (key << 32 | position) of the last blended entry; peeled candidates
+    unsigned long long last = 0ull;
+    bool has_last = false, more = mode == STP_MODE_FULL_ID && !s.done;
+    // every pass that continues blends HEAD entries of some pixel, so nL / HEAD + 1 passes
+    // exhaust any list; the bound makes that explicit
+    const int max_pass = nL / HEAD + 2;
+    int pass = 0;
+    do {
+        unsigned long long ck[HEAD];
+        uint32_t cid[HEAD];
+        float cv[HEAD];
+        int nc = 0;
+#pragma unroll
+        for (int j = 0; j < HEAD; j++) {
+            ck[j] = ~0ull;
+            cid[j] = 0;
+            cv[j] = 0.f;
+        }
+        for (int b0 = 0; b0 < nL; b0 += kFlatBatch) {
+            if (__syncthreads_and(s.done || (mode == STP_MODE_FULL_ID && !more))) break;
+            const int idx = b0 + (int)threadIdx.x;
+            if (idx < nL) {
+                const uint32_t gid = __ldg(a.svals + lst + idx);
+                sid[threadIdx.x] = gid;
+                const float4* g = a.geom + kRecFloat4 * (V.rec_off + gid);
+#pragma unroll
+                for (int k = 0; k < kRecFloat4; k++) srec[threadIdx.x * kRecFloat4 + k] = __ldg(g + k);
+            }
+            __syncthreads();
+            const int nb = min(kFlatBatch, nL - b0);
+            if (!s.done && (mode != STP_MODE_FULL_ID || more)) {
+                for (int j = 0; j < nb; j++) {
+                    Rec r;
+                    r.r0 = srec[j * kRecFloat4 + 0]; r.r1 = srec[j * kRecFloat4 + 1];
+                    r.r2 = srec[j * kRecFloat4 + 2]; r.r3 = srec[j * kRecFloat4 + 3];
+                    r.r4 = srec[j * kRecFloat4 + 4]; r.r5 = srec[j * kRecFloat4 + 5];
+                    const float val = splat_value(r, c.xc, c.yc);
+                    n_eval++;
+                    if (!(fminf(a.alpha_max, val) >= a.eps_o)) continue;
+                    const uint32_t key = depth_key(depth_uvn(r, c.u, c.w, c.n));
+                    const uint32_t gid = sid[j];
+                    if (mode == STP_MODE_GLOBAL_ID) {
+                        blend<HEAD, false>(a, V, s, c, key, gid, val);
+                        if (s.done) break;
+                    } else if (mode == STP_MODE_WINDOW_ID) {
+                        head_push<HEAD, false>(a, V, s, c, key, gid, val, evict_first);
+                        if (s.done) break;
+                    } else {
+                        const unsigned long long ek = ((unsigned long long)key << 32) | (uint32_t)(b0 + j);
+                        if ((has_last && ek <= last) || ek >= ck[HEAD - 1]) continue;
+                        // keep the HEAD smallest: insert ek into the ascending ck
+#pragma unroll
+                        for (int q = HEAD - 1; q >= 0; q--) {
+                            const bool shift = q > 0 && ck[q - 1] > ek;
+                            const bool here = ck[q] > ek && !shift;
+                            if (shift) { ck[q] = ck[q - 1]; cid[q] = cid[q - 1]; cv[q] = cv[q - 1]; }
+                            else if (here) { ck[q] = ek; cid[q] = gid; cv[q] = val; }
+                        }
+                        nc = min(nc + 1, HEAD);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (mode == STP_MODE_FULL_ID) {
+            if (more) {
+#pragma unroll
+                for (int j = 0; j < HEAD; j++)
+                    if (j < nc && !s.done) blend<HEAD, false>(a, V, s, c, (uint32_t)(ck[j] >> 32), cid[j], cv[j]);
+                if (nc > 0) {
+                    last = ck[nc - 1];
+                    has_last = true;
+                }
+                more = nc == HEAD && !s.done;     // fewer than HEAD found: the list is exhausted
+            }
+            if (++pass >= max_pass) {
+                if (more) atomicOr(&a.status->error_bits, 4u);
+                break;
+            }
+            if (!__syncthreads_or(more)) break;
+        }
+    } while (mode == STP_MODE_FULL_ID);
+    if (mode == STP_MODE_WINDOW_ID) {
+#pragma unroll
+        for (int j = 0; j < HEAD; j++)
+            if (j < s.nh) blend<HEAD, false>(a, V, s, c, s.hk[j], s.hid[j], s.hv[j]);
+    }
+    if (count) {
+        atomicAdd(&a.status->counters[4], n_eval);
+        atomicAdd(&a.status->counters[3], (unsigned long long)s.nbl);
+    }
+    if (!inside) return;
+    const long long p = c.pix;
+    a.rgb[3 * p] = s.C0 + s.T * a.bg[0];
+    a.rgb[3 * p + 1] = s.C1 + s.T * a.bg[1];
+    a.rgb[3 * p + 2] = s.C2 + s.T * a.bg[2];
+    a.depth[p] = s.Z;
+    a.tfinal_ws[p] = s.T;
+    if (a.tfinal_out) a.tfinal_out[p] = s.T;
+    if (a.dbg_nblend) a.dbg_nblend[p] = s.nbl;
+    if (a.dbg_hash) a.dbg_hash[p] = s.hash;
+    if (a.dbg_delta) a.dbg_delta[p] = s.delta;
+}
+
+template <int HEAD>
+cudaError_t launch_flat(const PipeArgs& a, cudaStream_t s)
+{
+    k_render_flat<HEAD><<<a.total_tiles, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -518,6 +718,19 @@ bool render_head_supported(int head) { return head == 1 || head == 2 || head == 
 cudaError_t launch_render(const PipeArgs& a, bool backward, cudaStream_t s)
 {
     if (a.total_tiles == 0) return cudaSuccess;
+    if (a.mode != STP_MODE_HIER_ID) {
+        if (backward) return cudaErrorInvalidValue;
+        if (a.mode == STP_MODE_GLOBAL_ID) return launch_flat<1>(a, s);
+        if (a.mode == STP_MODE_FULL_ID) return launch_flat<16>(a, s);
+        switch (a.window_k) {
+            case 1: return launch_flat<1>(a, s);
+            case 2: return launch_flat<2>(a, s);
+            case 4: return launch_flat<4>(a, s);
+            case 8: return launch_flat<8>(a, s);
+            case 16: return launch_flat<16>(a, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     const size_t smem = render_smem_bytes(a.tail, a.mid);
     switch (a.head) {
         case 1: return launch_head<1>(a, backward, smem, s);

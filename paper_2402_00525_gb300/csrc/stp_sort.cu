@@ -474,7 +474,9 @@ cudaError_t launch_tile_sort(const PipeArgs& a, cudaStream_t s)
 {
     if (a.total_tiles == 0) return cudaSuccess;
     const size_t smem = tile_sort_smem_bytes();
-    cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static int set_dev[64];
+    cudaError_t e = ensure_smem_limit(k_tile_sort, smem, set_dev, 64);
+    if (e != cudaSuccess) return e;
     k_tile_sort<<<a.total_tiles, kSegThreads, smem, s>>>(a);
     return cudaGetLastError();
 }

@@ -42,19 +42,43 @@ def gaussians_struct(g: dict) -> N.Gaussians:
     return s
 
 
-class Renderer:
-    """Renders one scene size from a fixed list of cameras with fixed parameters.
+def _grads_struct(grads: dict) -> N.GaussiansGrad:
+    gs = N.GaussiansGrad()
+    for k in FIELDS:
+        t = grads[k]
+        if t.dtype != torch.float32 or not t.is_contiguous():
+            raise ValueError("gradient %s must be contiguous float32" % k)
+        setattr(gs, k, _ptr(t))
+    return gs
 
+
+class Renderer:
+    """Renders one scene size (or, with views_per_scene, several scenes) from a fixed list of
+    cameras with fixed parameters, in one launch per stage.
+
+    With views_per_scene, n is the list of scene sizes and scene s owns views_per_scene[s]
+    consecutive cameras; forward / backward then take lists of scene dicts (one per scene).
     The workspace is sized for the configuration and grown on demand when the sort-entry
     capacity turns out too small (this needs one host synchronisation; pass check=False in
     a steady-state loop once the capacity is known). A backward pass reuses the workspace of
     the preceding forward pass, so do not interleave forward calls between the two.
     """
 
-    def __init__(self, n: int, cams: Sequence[Camera], prm: RenderParams, device="cuda",
+    def __init__(self, n, cams: Sequence[Camera], prm: RenderParams, device="cuda",
                  backward: bool = False, debug: bool = False, capacity: int | None = None,
-                 headroom: float = 1.15, trace: bool = False):
-        self.n = int(n)
+                 headroom: float = 1.15, trace: bool = False, views_per_scene: Sequence[int] | None = None):
+        self.batched = views_per_scene is not None
+        if self.batched:
+            self.scene_sizes = [int(x) for x in n]
+            self.views_per_scene = [int(x) for x in views_per_scene]
+            if len(self.scene_sizes) != len(self.views_per_scene):
+                raise ValueError("one view count per scene expected")
+            self.n = sum(self.scene_sizes)
+        else:
+            self.scene_sizes = [int(n)]
+            self.views_per_scene = [len(cams)]
+            self.n = int(n)
+        self._vps_arr = (C.c_int32 * len(self.views_per_scene))(*self.views_per_scene)
         self.cams = list(cams)
         self.prm = prm
         self.device = torch.device(device)
@@ -65,6 +89,7 @@ class Renderer:
         self.total_pixels = sum(c.width * c.height for c in self.cams)
         self.pixel_offsets = np.cumsum([0] + [c.width * c.height for c in self.cams])
         self.ws = None
+        self._graphs = 0
         self._alloc(capacity or 0)
 
     # ------------------------------------------------------------------ workspace
@@ -72,9 +97,15 @@ class Renderer:
         return N.params_struct(self.prm, self.flags, self.capacity_req)
 
     def _alloc(self, capacity: int) -> None:
+        if self._graphs:
+            raise N.CapacityError(N.STP_ERR_CAPACITY, "the workspace is bound to a captured CUDA graph and "
+                                  "cannot grow; build the Renderer with a larger capacity")
         self.capacity_req = int(capacity)
         self.p = self._params()
-        self.layout = N.layout(self.n, self.cams, self.p)
+        if self.batched:
+            self.layout = N.layout(self.scene_sizes, self.cams, self.p, self.views_per_scene)
+        else:
+            self.layout = N.layout(self.n, self.cams, self.p)
         self.capacity = int(self.layout.capacity)
         self.ws = None
         torch.cuda.empty_cache() if self.device.type == "cuda" else None
@@ -83,6 +114,21 @@ class Renderer:
     def _region(self, off: int, count: int, dtype) -> torch.Tensor:
         nbytes = count * torch.empty((), dtype=dtype).element_size()
         return self.ws[off:off + nbytes].view(dtype)
+
+    def set_cameras(self, cams: Sequence[Camera]) -> None:
+        """Replace the cameras (same count per scene). The workspace is kept when the image
+        sizes are unchanged, so a captured graph stays valid only in that case: it keeps the
+        camera poses it was recorded with."""
+        cams = list(cams)
+        if len(cams) != len(self.cams):
+            raise ValueError("expected %d cameras, got %d" % (len(self.cams), len(cams)))
+        same = all(a.width == b.width and a.height == b.height for a, b in zip(cams, self.cams))
+        self.cams = cams
+        self._cams_arr = N.cameras_array(self.cams)
+        if not same:
+            self.total_pixels = sum(c.width * c.height for c in self.cams)
+            self.pixel_offsets = np.cumsum([0] + [c.width * c.height for c in self.cams])
+            self._alloc(self.capacity_req)
 
     @property
     def workspace_bytes(self) -> int:
@@ -98,12 +144,16 @@ class Renderer:
                    torch.empty((P,), dtype=torch.float32, device=self.device),
                    torch.empty((P,), dtype=torch.float32, device=self.device))
         rgb, depth, tfin = out
-        s = gaussians_struct(g)
-        if s.n != self.n:
-            raise ValueError("renderer was built for n = %d, got %d" % (self.n, s.n))
+        sc = self._scenes(g)
         strm = stream if stream is not None else torch.cuda.current_stream(self.device)
         for attempt in range(3):
-            N.check(N.lib().stp_render(C.byref(s), C.cast(self._cams_arr, C.c_void_p), len(self.cams),
+            N.check(N.lib().stp_render_batched(C.cast(sc, C.c_void_p), len(sc), C.cast(self._vps_arr, C.c_void_p),
+                                               C.cast(self._cams_arr, C.c_void_p), len(self.cams),
+                                               C.byref(self.p), C.c_void_p(_ptr(self.ws)), self.layout.total,
+                                               C.c_void_p(_ptr(rgb)), C.c_void_p(_ptr(depth)),
+                                               C.c_void_p(_ptr(tfin)), C.c_void_p(strm.cuda_stream))
+                    if self.batched else
+                    N.lib().stp_render(C.byref(sc[0]), C.cast(self._cams_arr, C.c_void_p), len(self.cams),
                                        C.byref(self.p), C.c_void_p(_ptr(self.ws)), self.layout.total,
                                        C.c_void_p(_ptr(rgb)), C.c_void_p(_ptr(depth)),
                                        C.c_void_p(_ptr(tfin)), C.c_void_p(strm.cuda_stream)))
@@ -120,6 +170,17 @@ class Renderer:
             break
         return rgb, depth, tfin
 
+    def _scenes(self, g):
+        gl = list(g) if self.batched else [g]
+        if len(gl) != len(self.scene_sizes):
+            raise ValueError("expected %d scenes, got %d" % (len(self.scene_sizes), len(gl)))
+        arr = (N.Gaussians * len(gl))()
+        for k, (gk, nk) in enumerate(zip(gl, self.scene_sizes)):
+            arr[k] = gaussians_struct(gk)
+            if arr[k].n != nk:
+                raise ValueError("scene %d: renderer was built for n = %d, got %d" % (k, nk, arr[k].n))
+        return arr
+
     def status(self, stream=None) -> N.RunStatus:
         strm = stream if stream is not None else torch.cuda.current_stream(self.device)
         return N.read_status(_ptr(self.ws), strm.cuda_stream, raise_on_error=False)
@@ -131,20 +192,27 @@ class Renderer:
         into grads (dict of tensors shaped like the inputs)."""
         if not (self.flags & N.FLAG_BACKWARD):
             raise RuntimeError("construct the Renderer with backward=True")
-        s = gaussians_struct(g)
-        gs = N.GaussiansGrad()
-        for k in FIELDS:
-            t = grads[k]
-            if t.dtype != torch.float32 or not t.is_contiguous():
-                raise ValueError("gradient %s must be contiguous float32" % k)
-            setattr(gs, k, _ptr(t))
+        sc = self._scenes(g)
+        gl = list(grads) if self.batched else [grads]
+        if len(gl) != len(sc):
+            raise ValueError("one gradient dict per scene expected")
+        gs = (N.GaussiansGrad * len(gl))()
+        for k, gk in enumerate(gl):
+            gs[k] = _grads_struct(gk)
         d_rgb = d_rgb.contiguous()
         d_depth = None if d_depth is None else d_depth.contiguous()
         strm = stream if stream is not None else torch.cuda.current_stream(self.device)
-        N.check(N.lib().stp_render_backward(C.byref(s), C.cast(self._cams_arr, C.c_void_p), len(self.cams),
-                                            C.byref(self.p), C.c_void_p(_ptr(self.ws)), self.layout.total,
-                                            C.c_void_p(_ptr(d_rgb)), C.c_void_p(_ptr(d_depth)),
-                                            C.byref(gs), C.c_void_p(strm.cuda_stream)))
+        if self.batched:
+            N.check(N.lib().stp_render_backward_batched(
+                C.cast(sc, C.c_void_p), len(sc), C.cast(self._vps_arr, C.c_void_p),
+                C.cast(self._cams_arr, C.c_void_p), len(self.cams), C.byref(self.p), C.c_void_p(_ptr(self.ws)),
+                self.layout.total, C.c_void_p(_ptr(d_rgb)), C.c_void_p(_ptr(d_depth)), C.cast(gs, C.c_void_p),
+                C.c_void_p(strm.cuda_stream)))
+        else:
+            N.check(N.lib().stp_render_backward(C.byref(sc[0]), C.cast(self._cams_arr, C.c_void_p), len(self.cams),
+                                                C.byref(self.p), C.c_void_p(_ptr(self.ws)), self.layout.total,
+                                                C.c_void_p(_ptr(d_rgb)), C.c_void_p(_ptr(d_depth)),
+                                                C.byref(gs[0]), C.c_void_p(strm.cuda_stream)))
 
     # ------------------------------------------------------------------ inspection
     def split(self, packed: torch.Tensor) -> List[torch.Tensor]:
@@ -163,6 +231,32 @@ class Renderer:
         h = self._region(L.dbg_hash, P, torch.int64)
         return nbl, h
 
+    def debug_delta(self) -> torch.Tensor:
+        """Per-pixel sort error delta of the last forward (needs debug=True)."""
+        return self._region(self.layout.dbg_delta, int(self.layout.total_pixels), torch.float32)
+
+    def capture(self, g, out, d_rgb=None, d_depth=None, grads=None):
+        """Record forward (and, with d_rgb, backward) into a CUDA graph. The workspace must
+        already be large enough (run forward once with check=True first); from now on it
+        cannot grow (a later overflow raises instead of reallocating). Returns the graph;
+        graph.replay() re-renders with the current contents of the bound tensors, and
+        status() after a replay tells whether the capacity sufficed."""
+        side = torch.cuda.Stream(self.device)
+        side.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(side):
+            self.forward(g, out=out, check=False, stream=side)
+            if d_rgb is not None:
+                self.backward(g, d_rgb, d_depth, grads, stream=side)
+        torch.cuda.current_stream(self.device).wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        self._graphs += 1
+        with torch.cuda.graph(graph):
+            strm = torch.cuda.current_stream(self.device)
+            self.forward(g, out=out, check=False, stream=strm)
+            if d_rgb is not None:
+                self.backward(g, d_rgb, d_depth, grads, stream=strm)
+        return graph
+
     def debug_trace(self) -> torch.Tensor:
         """[P, TRACE_LEN] ids of the first blended Gaussians per pixel (needs trace=True)."""
         P = int(self.layout.total_pixels)
@@ -179,6 +273,9 @@ class Renderer:
         return ranges, keys, vals
 
     def records(self):
+        """(geom [V, N, 24], colour [V, N, 4], rect [V, N, 4], counts [V, N]) of one scene."""
+        if self.batched:
+            raise RuntimeError("records() reads single-scene workspaces")
         L = self.layout
         m = self.n * len(self.cams)
         geom = self._region(L.geom, m * 24, torch.float32).view(len(self.cams), self.n, 24)

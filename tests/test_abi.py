@@ -32,7 +32,7 @@ def test_every_declared_symbol_is_exported(lib):
     for name in declared:
         assert hasattr(lib, name), name
     assert sorted(N.EXPORTS) == declared
-    assert lib.stp_version() == 0x000100
+    assert lib.stp_version() == 0x000200
 
 
 def test_workspace_layout_is_consistent(lib):
@@ -59,7 +59,7 @@ def test_workspace_layout_is_consistent(lib):
 @pytest.mark.parametrize("field,value,code", [
     ("tail", 48, N.STP_ERR_ARG), ("tail", 80, N.STP_ERR_ARG), ("mid", 6, N.STP_ERR_ARG),
     ("mid", 10, N.STP_ERR_ARG), ("head", 5, N.STP_ERR_NOT_SUPPORTED), ("lb_threshold", 0, N.STP_ERR_ARG),
-    ("eps_o", 0.0, N.STP_ERR_ARG), ("mode", 7, N.STP_ERR_NOT_SUPPORTED), ("max_entries", -1, N.STP_ERR_ARG),
+    ("eps_o", 0.0, N.STP_ERR_ARG), ("mode", 7, N.STP_ERR_ARG), ("mode", -1, N.STP_ERR_ARG), ("max_entries", -1, N.STP_ERR_ARG),
 ])
 def test_bad_parameters_rejected_on_host(lib, field, value, code):
     sc, cams, prm = I.plain_forward_workload()
@@ -70,6 +70,17 @@ def test_bad_parameters_rejected_on_host(lib, field, value, code):
                                       C.byref(L))
     assert rc == code
     assert N.last_error()
+
+
+def test_window_sizes_are_the_compiled_ones(lib):
+    sc, cams, prm = I.plain_forward_workload()
+    L = N.Layout()
+    for k, code in ((3, N.STP_ERR_NOT_SUPPORTED), (8, N.STP_OK), (32, N.STP_ERR_NOT_SUPPORTED)):
+        p = N.params_struct(prm)
+        p.mode, p.window_k = I.MODE_WINDOW, k
+        rc = lib.stp_workspace_layout_get(sc.n, C.cast(N.cameras_array(cams), C.c_void_p), 1, C.byref(p),
+                                          C.byref(L))
+        assert rc == code, k
 
 
 def test_render_rejects_bad_arguments_before_launch(lib):
@@ -97,3 +108,60 @@ def test_render_rejects_bad_arguments_before_launch(lib):
     assert lib.stp_sort_pairs(None, None, None, None, 10, None, 0, None, 0, None) == N.STP_ERR_ARG
     assert lib.stp_sort_pairs(None, None, None, None, 10, None, 40, None, 0, None) == N.STP_ERR_ARG
     assert lib.stp_sort_temp_bytes(1000) > 12000
+
+
+def test_batched_layout_adds_up_over_scenes(lib):
+    cams = I.orbit_cameras(6, 15.0, 2.0, I.C4_SIZES, 50.0)
+    p = N.params_struct(I.RenderParams(), N.FLAG_BACKWARD, max_entries=1 << 20)
+    ns, vps = [1000, 0, 70001], [2, 1, 3]
+    L = N.layout(ns, cams, p, vps)
+    # one scene through the batched call equals the single-scene layout
+    L1 = N.layout(5000, cams, p, [6])
+    assert L1.as_dict() == N.layout(5000, cams, p).as_dict()
+    m = sum(n * v for n, v in zip(ns, vps))
+    assert L.total_tiles == sum(c.num_tiles for c in cams)
+    assert L.total_pixels == sum(c.num_pixels for c in cams)
+    assert L.color + m * 16 <= L.rect                  # colour region holds one record per (view, Gaussian)
+    assert L.grad_geom and L.total >= L.grad_geom + m * 24 * 4
+    arr_n = (C.c_int64 * 3)(*ns)
+    arr_v = (C.c_int32 * 3)(*vps)
+    size = lib.stp_workspace_size_batched(C.cast(arr_n, C.c_void_p), C.cast(arr_v, C.c_void_p), 3,
+                                          C.cast(N.cameras_array(cams), C.c_void_p), 6, C.byref(p))
+    assert size == L.total
+
+
+@pytest.mark.parametrize("ns,vps,nviews,msg", [
+    ([10, 10], [3, 2], 6, "sum to"),
+    ([10], [-1], 6, "negative"),
+    ([-5], [6], 6, "out of range"),
+    ([1] * 65, [0] * 64 + [6], 6, "nscenes"),
+])
+def test_batched_layout_rejects_bad_scene_tables(lib, ns, vps, nviews, msg):
+    cams = I.orbit_cameras(nviews, 15.0, 2.0, I.C4_SIZES, 50.0)
+    p = N.params_struct(I.RenderParams())
+    arr_n = (C.c_int64 * len(ns))(*ns)
+    arr_v = (C.c_int32 * len(vps))(*vps)
+    out = N.Layout()
+    rc = lib.stp_workspace_layout_batched(C.cast(arr_n, C.c_void_p), C.cast(arr_v, C.c_void_p), len(ns),
+                                          C.cast(N.cameras_array(cams), C.c_void_p), nviews, C.byref(p),
+                                          C.byref(out))
+    assert rc == N.STP_ERR_ARG and msg in N.last_error()
+
+
+def test_batched_render_checks_scene_pointers_before_launch(lib):
+    cams = I.orbit_cameras(2, 15.0, 2.0, I.C4_SIZES, 50.0)
+    p = N.params_struct(I.RenderParams())
+    scenes = (N.Gaussians * 2)()
+    scenes[0].n, scenes[0].sh_degree = 10, 0
+    scenes[0].means = scenes[0].log_scales = scenes[0].quats = scenes[0].opacity_logits = scenes[0].sh = 256
+    scenes[1].n, scenes[1].sh_degree = 10, 0          # null arrays in scene 1
+    vps = (C.c_int32 * 2)(1, 1)
+    rc = lib.stp_render_batched(C.cast(scenes, C.c_void_p), 2, C.cast(vps, C.c_void_p),
+                                C.cast(N.cameras_array(cams), C.c_void_p), 2, C.byref(p), C.c_void_p(256),
+                                1 << 40, C.c_void_p(256), C.c_void_p(256), None, None)
+    assert rc == N.STP_ERR_ARG and "scene 1" in N.last_error()
+    scenes[1].sh_degree = 4
+    rc = lib.stp_render_batched(C.cast(scenes, C.c_void_p), 2, C.cast(vps, C.c_void_p),
+                                C.cast(N.cameras_array(cams), C.c_void_p), 2, C.byref(p), C.c_void_p(256),
+                                1 << 40, C.c_void_p(256), C.c_void_p(256), None, None)
+    assert rc == N.STP_ERR_ARG and "sh_degree" in N.last_error()

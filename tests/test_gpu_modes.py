@@ -1,0 +1,71 @@
+"""The comparison orders of Sec. 3.3 / 4.2 (FULL per-ray sort, GLOBAL list order, WINDOW-k
+k-buffer) and the alternative readings / ablation switches on the GPU, each against the oracle
+run with the same setting: equal blend count and order hash on every decided pixel, colour
+within 1e-4 (the bar of the hierarchical mode)."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from paper_2402_00525_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2402_00525_gb300 import _native as N  # noqa: E402
+from paper_2402_00525_gb300 import renderer as R  # noqa: E402
+from gpu_helpers import compare_view, gpu_render  # noqa: E402
+
+CASES = {
+    "full": dict(mode=I.MODE_FULL),
+    "global": dict(mode=I.MODE_GLOBAL),
+    "window-1": dict(mode=I.MODE_WINDOW, window_k=1),
+    "window-4": dict(mode=I.MODE_WINDOW, window_k=4),
+    "window-16": dict(mode=I.MODE_WINDOW, window_k=16),
+    "window-8-evict-first": dict(mode=I.MODE_WINDOW, window_k=8, flags=I.FLAG_HEAD_EVICT_FIRST),
+    "hier-evict-first": dict(flags=I.FLAG_HEAD_EVICT_FIRST),
+    "hier-level-centre-rays": dict(flags=I.FLAG_LEVEL_CENTRE_RAYS),
+    "hier-tile-centre-key": dict(flags=I.FLAG_TILE_CENTRE_KEY),
+    "hier-view-depth-key": dict(flags=I.FLAG_VIEW_DEPTH_KEY),
+    "hier-no-tile-cull": dict(flags=I.FLAG_NO_TILE_CULL),
+    "hier-no-hier-cull": dict(flags=I.FLAG_NO_HIER_CULL),
+    "hier-128-20-8": dict(tail=128, mid=20, head=8),
+    "hier-96-12-1": dict(tail=96, mid=12, head=1),
+    "hier-256-16-2-global-sort": dict(tail=256, mid=16, head=2, flags=I.FLAG_GLOBAL_SORT),
+}
+
+
+def _scenes():
+    sc, cams, prm = I.plain_forward_workload()
+    yield "plain", sc, cams[0], prm
+    sc2 = I.cluster_scene(20000, 77, nclusters=6, centre_range=1.5, scale_range=(0.003, 0.2))
+    cam2 = I.look_at((0.5, -0.3, -6), (0, 0, 0), (0, 1, 0), 200, 136, 50.0)
+    yield "clusters", sc2, cam2, I.RenderParams()
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_mode_matches_oracle(oracle, case):
+    for name, sc, cam, base in _scenes():
+        prm = dataclasses.replace(base, **CASES[case])
+        gpu = gpu_render(sc, [cam], prm)
+        ora = oracle.render(sc, cam, prm)
+        frac = compare_view(gpu, 0, ora, min_decided=0.9, label="%s / %s" % (case, name))
+        st = gpu["renderer"].status()
+        assert st.error_bits == 0 and st.num_entries == ora["num_entries"]
+        print(case, name, "decided %.4f" % frac, "delta avg %.4f" % ora["delta"].mean())
+        if prm.mode == I.MODE_FULL:
+            assert gpu["delta"][0].max() == 0.0 and ora["delta"].max() == 0.0
+
+
+def test_backward_of_a_comparison_order_is_rejected():
+    sc, cams, prm = I.plain_forward_workload()
+    g = R.scene_to_device(sc)
+    r = R.Renderer(sc.n, cams, dataclasses.replace(prm, mode=I.MODE_GLOBAL), backward=True)
+    r.forward(g)
+    grads = {k: torch.zeros_like(g[k]) for k in R.FIELDS}
+    with pytest.raises(N.StpError) as e:
+        r.backward(g, torch.zeros((cams[0].num_pixels, 3), device="cuda"), None, grads)
+    assert e.value.code == N.STP_ERR_NOT_SUPPORTED

@@ -23,42 +23,7 @@ if not torch.cuda.is_available():
 
 from paper_2402_00525_gb300 import _native as N  # noqa: E402
 from paper_2402_00525_gb300 import renderer as R  # noqa: E402
-
-
-def gpu_render(scene, cams, prm, debug=True, capacity=None):
-    g = R.scene_to_device(scene)
-    r = R.Renderer(scene.n, cams, prm, debug=debug, capacity=capacity)
-    rgb, depth, tf = r.forward(g)
-    torch.cuda.synchronize()
-    out = dict(rgb=[x.cpu().numpy() for x in r.split(rgb)], depth=[x.cpu().numpy() for x in r.split(depth)],
-               tfinal=[x.cpu().numpy() for x in r.split(tf)], renderer=r, g=g)
-    if debug:
-        nbl, h = r.debug_stats()
-        out["nblend"] = [x.cpu().numpy() for x in r.split(nbl)]
-        out["hash"] = [x.cpu().numpy().view(np.uint64) for x in r.split(h)]
-    return out
-
-
-def compare_view(gpu, k, ora, tiles_mask=None, min_decided=0.99, label=""):
-    dec = ora["decided"].copy()
-    if tiles_mask is not None:
-        dec &= tiles_mask
-        denom = tiles_mask.sum()
-    else:
-        denom = dec.size
-    frac = dec.sum() / max(denom, 1)
-    assert frac >= min_decided, "%s decided fraction %.4f" % (label, frac)
-    nb = gpu["nblend"][k]
-    hs = gpu["hash"][k]
-    bad = dec & ((nb != ora["nblend"]) | (hs != ora["hash"]))
-    assert bad.sum() == 0, "%s: %d decided pixels differ in blend order (of %d)" % (label, bad.sum(), dec.sum())
-    drgb = np.abs(gpu["rgb"][k] - ora["rgb"])[dec]
-    assert drgb.size == 0 or drgb.max() <= 1e-4, "%s rgb max diff %g" % (label, drgb.max())
-    dd = np.abs(gpu["depth"][k] - ora["depth"])[dec]
-    assert dd.size == 0 or (dd / (1 + np.abs(ora["depth"][dec]))).max() <= 1e-4
-    dt = np.abs(gpu["tfinal"][k] - ora["tfinal"])[dec]
-    assert dt.size == 0 or dt.max() <= 1e-5
-    return frac
+from gpu_helpers import compare_view, gpu_render, tile_mask  # noqa: E402
 
 
 def test_plain_forward_256_matches_oracle(oracle):
@@ -262,14 +227,6 @@ def test_sort_primitive_is_stable_and_exact():
         assert np.array_equal(kd.cpu().numpy().view(np.uint64), keys)      # input preserved
 
 
-def _tile_mask(cam, tiles):
-    m = np.zeros((cam.height, cam.width), bool)
-    for t in tiles:
-        tx, ty = t % cam.tiles_x, t // cam.tiles_x
-        m[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16] = True
-    return m
-
-
 def test_full_hd_3m_sampled_tiles_match_oracle(oracle):
     """The 3M-Gaussian Full-HD workload in the launch configuration the bench times (16 views
     in one batch), sampled: the oracle renders 40 random tiles of two views one by one."""
@@ -280,7 +237,7 @@ def test_full_hd_3m_sampled_tiles_match_oracle(oracle):
         tiles = rng.choice(cams[k].num_tiles, 40, replace=False)
         with oracle.OracleRun(sc, cams[k], prm, tiles=tiles) as r:
             ora = r.render()
-        frac = compare_view(gpu, k, ora, tiles_mask=_tile_mask(cams[k], tiles), min_decided=0.75,
+        frac = compare_view(gpu, k, ora, tiles_mask=tile_mask(cams[k], tiles), min_decided=0.75,
                             label="full hd view %d" % k)
         print("view", k, "decided fraction in sampled tiles", frac)
     st = gpu["renderer"].status()
