@@ -42,6 +42,7 @@ FP32_LANES_PER_SM = 128
 # algorithmic FP32 operations per work unit of the forward Render (cull by Algorithm 1 + G2 +
 # t_opt at a 4x4 or 2x2 box; alpha + t_opt at a pixel)
 FLOP_PER_SUBTILE_EVAL, FLOP_PER_QUAD_EVAL, FLOP_PER_PIXEL_EVAL = 80, 80, 45
+FLOP_PER_BLEND_GRAD = 40
 
 
 def dist_env():
@@ -134,6 +135,134 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def batching_leg(torch, R, N, g, n):
+    """64 views of the 3M scene at 320x240 .. 2560x1440: the batched forward recorded in one
+    CUDA graph with the autotuned setting, against 64 single-view launch sequences at the
+    default setting (outputs compared bit for bit)."""
+    from paper_2402_00525_gb300 import autotune as A
+    cams = I.orbit_cameras(64, 15.0, 2.0, I.C4_SIZES, 50.0)
+    base = I.RenderParams()
+    prm_t = A.tuned_params("batching", base)
+    P = sum(c.num_pixels for c in cams)
+    rb = R.Renderer(n, cams, prm_t, headroom=1.1)
+    out = tuple(torch.empty(sh, device="cuda") for sh in ((P, 3), (P,), (P,)))
+    rb.forward(g, out=out)
+    graph = rb.capture(g, out)
+    for _ in range(2):
+        graph.replay()
+    ms = []
+    for _ in range(3):
+        a, b = _events(torch)
+        a.record()
+        graph.replay()
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    assert rb.status().error_bits == 0
+    g_ms = float(np.median(ms))
+    per = {}
+    for c in cams:
+        key = (c.width, c.height)
+        if key not in per:
+            per[key] = R.Renderer(n, [c], base)
+    outs = [tuple(torch.empty(sh, device="cuda") for sh in ((c.num_pixels, 3), (c.num_pixels,), (c.num_pixels,)))
+            for c in cams]
+    for c, o in zip(cams, outs):
+        r1 = per[(c.width, c.height)]
+        r1.set_cameras([c])
+        r1.forward(g, out=o)
+    torch.cuda.synchronize()
+    pv = []
+    l0 = N.kernel_launches()
+    for it in range(3):
+        a, b = _events(torch)
+        a.record()
+        for c, o in zip(cams, outs):
+            r1 = per[(c.width, c.height)]
+            r1.set_cameras([c])
+            r1.forward(g, out=o, check=False)
+        b.record()
+        torch.cuda.synchronize()
+        if it:
+            pv.append(a.elapsed_time(b))
+    pv_ms = float(np.mean(pv))
+    same = all(torch.equal(out[0][int(rb.pixel_offsets[k]):int(rb.pixel_offsets[k + 1])], outs[k][0])
+               for k in range(len(cams)))
+    kernels = N.kernel_launches() - l0
+    res = {"workload": "3M Gaussians, 64 orbit views, 13/13/13/13/12 at 320x240/640x480/1280x720/1920x1080/2560x1440",
+           "pixels": P, "graph_fwd_ms": g_ms, "graph_mpix_s": P / (g_ms * 1e-3) / 1e6,
+           "per_view_fwd_ms": pv_ms, "per_view_mpix_s": P / (pv_ms * 1e-3) / 1e6, "batched_speedup": pv_ms / g_ms,
+           "identical_to_per_view": bool(same),
+           "tuned": {k: getattr(prm_t, k) for k in ("tail", "mid", "head", "lb_threshold", "flags")},
+           "per_view_launch_kernels": kernels // 3}
+    del rb, out, graph, per, outs
+    torch.cuda.empty_cache()
+    return res
+
+
+def training_leg(torch, R, N):
+    """8 scenes (100k .. 3M Gaussians, SH3), 4 views each at 640x480 .. 1920x1080: one training
+    step (forward + backward, gradients per scene) recorded in one CUDA graph, against the same
+    step as one eager launch sequence per scene."""
+    scenes, cams, prm = I.batched_training_workload()
+    gs = [R.scene_to_device(sc) for sc in scenes]
+    allc = [c for cs in cams for c in cs]
+    P = sum(c.num_pixels for c in allc)
+    gen = torch.Generator(device="cuda").manual_seed(99)
+    d_rgb = (torch.randint(0, 2, (P, 3), device="cuda", generator=gen).float() * 2 - 1) / (3 * P)
+    rb = R.Renderer([sc.n for sc in scenes], allc, prm, backward=True, views_per_scene=[len(cs) for cs in cams],
+                    headroom=1.1)
+    out = tuple(torch.empty(sh, device="cuda") for sh in ((P, 3), (P,), (P,)))
+    grads = [{k: torch.zeros_like(g[k]) for k in R.FIELDS} for g in gs]
+    rb.forward(gs, out=out)
+    graph = rb.capture(gs, out, d_rgb=d_rgb, grads=grads)
+    for _ in range(2):
+        graph.replay()
+    ms = []
+    for _ in range(3):
+        a, b = _events(torch)
+        a.record()
+        graph.replay()
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    assert rb.status().error_bits == 0
+    g_ms = float(np.median(ms))
+    del rb, graph
+    torch.cuda.empty_cache()
+    singles, offs, o = [], [], 0
+    for sc, cs in zip(scenes, cams):
+        r1 = R.Renderer(sc.n, cs, prm, backward=True)
+        n1 = sum(c.num_pixels for c in cs)
+        singles.append((r1, slice(o, o + n1)))
+        o += n1
+    for (r1, sl), g, gr in zip(singles, gs, grads):
+        r1.forward(g)
+        r1.backward(g, d_rgb[sl], None, gr)
+    torch.cuda.synchronize()
+    pv = []
+    for _ in range(2):
+        a, b = _events(torch)
+        a.record()
+        for (r1, sl), g, gr in zip(singles, gs, grads):
+            r1.forward(g, check=False)
+            r1.backward(g, d_rgb[sl], None, gr)
+        b.record()
+        torch.cuda.synchronize()
+        pv.append(a.elapsed_time(b))
+    pv_ms = float(np.mean(pv))
+    del singles, gs, grads, out
+    torch.cuda.empty_cache()
+    return {"workload": "8 scenes of 100k/250k/500k/750k/1M/1.5M/2M/3M Gaussians (SH3), 4 views each at "
+                        "640x480/1280x720/1600x900/1920x1080",
+            "pixels": P, "graph_step_ms": g_ms, "per_scene_step_ms": pv_ms, "batched_speedup": pv_ms / g_ms,
+            "fwd_bwd_ms_per_view": g_ms / len(allc)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -143,6 +272,7 @@ def main():
     ap.add_argument("--n", type=int, default=3_000_000, help="Gaussians (default: the workload's 3M)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--per-view-rounds", type=int, default=2)
+    ap.add_argument("--no-extra", action="store_true", help="skip the 64-view and 8-scene legs")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -196,6 +326,7 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    launches0 = N.kernel_launches()
     for k in range(K):
         ev[k][0].record()
         rnd.forward(g, out=out, check=False)
@@ -203,6 +334,7 @@ def main():
         rnd.backward(g, d_rgb, None, grads)
         ev[k][2].record()
     torch.cuda.synchronize()
+    launches = N.kernel_launches() - launches0
     if dist:
         dist.barrier()
     clk = clocks.stop()
@@ -278,9 +410,10 @@ def main():
     sm_max = clk.get("sm_max_mhz") or 2070.0
     peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved = flops / (render_ms * 1e-3) / 1e12
-    passes = (int(rnd.layout.key_bits) + 7) // 8
-    launches_fwd = 1 + 1 + 1 + 3 + 1 + 3 * passes + 1 + 1
-    launches_bwd = 2
+    bwd_render_ms = float(bwd_stage[6])
+    # backward Render: the forward's decisions again plus, per blend, the gradient terms
+    bflops = flops + FLOP_PER_BLEND_GRAD * cnt[3]
+    bachieved = bflops / (bwd_render_ms * 1e-3) / 1e12
 
     line = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": K,
@@ -297,14 +430,25 @@ def main():
         "entries_per_step": entries,
         "e2e": {"value": e2e_val, "unit": "Mpix/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_ms},
-        "gpu_launches": K * (launches_fwd + launches_bwd),
+        "gpu_launches": launches,
         "clocks": clk,
         "roofline": {"bound": "alu", "kernel": "k_render (forward)", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                      "work_units": {"subtile_evals": cnt[0], "subtile_survivors": cnt[1], "quad_evals": cnt[2],
                                     "blends": cnt[3], "pixel_evals": cnt[4]},
                      "peak_basis": "FP32 FMA issue: %d SMs x 128 lanes x 2 x %.0f MHz" % (props.multi_processor_count, sm_max)},
+        "roofline_backward": {"bound": "alu", "kernel": "k_render (backward replay)", "achieved": bachieved,
+                              "peak": peak, "unit": "TFLOP/s", "frac": bachieved / peak, "traffic": None,
+                              "note": "the replay's decision FLOPs plus %d FLOP per blend for the gradient "
+                                      "terms; its time is dominated by the float atomics" % FLOP_PER_BLEND_GRAD},
     }
+    if world == 1 and not args.no_extra:
+        del rnd, out, grads
+        torch.cuda.empty_cache()
+        line["batching"] = batching_leg(torch, R, N, g, scene.n)
+        del g
+        torch.cuda.empty_cache()
+        line["training"] = training_leg(torch, R, N)
     if rank == 0 and not args.no_cpu_baseline:
         from oracle import build as OB
         OB.build()

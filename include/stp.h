@@ -279,6 +279,10 @@ stp_status stp_profile_enable(int32_t max_calls);
 stp_status stp_profile_read(float* ms /* host, [max_calls * STP_NUM_STAGES] */, int32_t max_calls,
                             int32_t* ncalls /* host */);
 
+/* Number of kernels the library has enqueued in this process so far (all threads, all
+ * devices; memsets and copies are not counted; a replayed CUDA graph is not counted again). */
+uint64_t stp_kernel_launches(void);
+
 /* Thread-local message of the last error on this host thread (empty if none).            */
 const char* stp_last_error(void);
 

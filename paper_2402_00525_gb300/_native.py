@@ -90,7 +90,7 @@ EXPORTS = ["stp_workspace_size", "stp_workspace_layout_get", "stp_render", "stp_
            "stp_workspace_size_batched", "stp_workspace_layout_batched", "stp_render_batched",
            "stp_render_backward_batched", "stp_read_status", "stp_sort_temp_bytes", "stp_sort_pairs", "stp_sort_pairs_noalloc",
            "stp_profile_enable",
-           "stp_profile_read", "stp_last_error", "stp_version"]
+           "stp_profile_read", "stp_last_error", "stp_version", "stp_kernel_launches"]
 
 NUM_STAGES = 8
 STAGE_NAMES = ["setup", "preprocess", "scan", "duplicate", "sort", "ranges", "render", "bwd_preprocess"]
@@ -136,9 +136,15 @@ def lib():
         L.stp_last_error.restype = C.c_char_p
         L.stp_last_error.argtypes = []
         L.stp_version.restype = C.c_int32
+        L.stp_kernel_launches.restype = C.c_uint64
+        L.stp_kernel_launches.argtypes = []
         L.stp_version.argtypes = []
         _lib = L
     return _lib
+
+
+def kernel_launches() -> int:
+    return int(lib().stp_kernel_launches())
 
 
 def last_error() -> str:

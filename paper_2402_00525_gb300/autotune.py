@@ -25,6 +25,7 @@ import argparse
 import dataclasses
 import itertools
 import json
+import os
 import sys
 from typing import List, Sequence
 
@@ -37,6 +38,35 @@ from . import renderer as R
 
 SPACE = dict(tail=(64, 96, 128), mid=(8, 12, 16, 20), head=(4, 8, 16), lb_threshold=(16, 32, 64))
 POLICIES = ("same-result", "no-worse", "fastest")
+TABLE_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
+_TABLE_KEYS = ("tail", "mid", "head", "lb_threshold", "flags")
+
+
+def table(workload: str) -> dict | None:
+    """The stored tuned setting of a workload (written by `--save-table`), or None."""
+    if not os.path.exists(TABLE_PATH):
+        return None
+    with open(TABLE_PATH) as f:
+        return json.load(f).get(workload)
+
+
+def tuned_params(workload: str, base: I.RenderParams) -> I.RenderParams:
+    """base with the stored tuned setting of `workload` applied (base itself if none)."""
+    t = table(workload)
+    if not t:
+        return base
+    return dataclasses.replace(base, **{k: int(t[k]) for k in _TABLE_KEYS if k in t})
+
+
+def save_table(workload: str, prm: I.RenderParams, note: str) -> None:
+    data = {}
+    if os.path.exists(TABLE_PATH):
+        with open(TABLE_PATH) as f:
+            data = json.load(f)
+    data[workload] = dict({k: int(getattr(prm, k)) for k in _TABLE_KEYS}, note=note)
+    with open(TABLE_PATH, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+        f.write("\n")
 
 
 @dataclasses.dataclass
@@ -218,6 +248,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--out", default=None, help="write the markdown report here")
     ap.add_argument("--json", default=None, help="write the chosen parameters here")
+    ap.add_argument("--save-table", action="store_true", help="store the choice in the package's tuned table")
     a = ap.parse_args(argv)
     scenes, cams, prm, vps = _load(a.workload)
     chosen, trials, bd = tune(scenes, cams, prm, vps, policy=a.policy, reps=a.reps, warmup=a.warmup,
@@ -231,6 +262,10 @@ def main(argv=None):
         with open(a.json, "w") as f:
             json.dump(dict(tail=chosen.tail, mid=chosen.mid, head=chosen.head, lb_threshold=chosen.lb_threshold,
                            flags=chosen.flags), f)
+    if a.save_table:
+        best = min(trials, key=lambda t: t.ms if t.params(prm) == chosen else float("inf"))
+        save_table(a.workload, chosen, "policy %s, %.3f ms forward (%s)" % (a.policy, best.ms,
+                                                                           torch.cuda.get_device_name()))
     return 0
 
 

@@ -2,6 +2,7 @@
 // workspace layout, and the launch sequence of the forward and backward passes.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -16,6 +17,7 @@
 namespace {
 
 thread_local std::string g_err;
+std::atomic<unsigned long long> g_launches{0};
 
 // ---- stage timing (stp_profile_enable / stp_profile_read)
 struct Profiler {
@@ -335,6 +337,7 @@ stp_status render_impl(const stp_gaussians* scenes, int32_t nscenes, const int32
     cudaError_t e;
     prof_mark(0, s);
     k_status_init<<<1, 1, 0, s>>>(a.status, a.capacity);
+    stp::note_launches(1);
     if ((e = stp::launch_tables_init(P.views.data(), nviews, const_cast<stp::ViewDesc*>(a.views), P.scenes.data(),
                                      nscenes, const_cast<stp::SceneDesc*>(a.scenes), s)) != cudaSuccess)
         return cuda_fail(e, "view and scene tables");
@@ -413,7 +416,13 @@ stp_status backward_impl(const stp_gaussians* scenes, int32_t nscenes, const int
 
 }  // namespace
 
+namespace stp {
+void note_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+}  // namespace stp
+
 extern "C" {
+
+uint64_t stp_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 const char* stp_last_error(void) { return g_err.c_str(); }
 

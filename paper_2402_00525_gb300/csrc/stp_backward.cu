@@ -255,6 +255,7 @@ cudaError_t launch_backward_preprocess(const PipeArgs& a, cudaStream_t s)
 {
     if (a.threads == 0) return cudaSuccess;
     k_backward_pre<<<(unsigned)(a.threads / 128), 128, 0, s>>>(a);
+    note_launches(1);
     return cudaGetLastError();
 }
 

@@ -82,6 +82,9 @@ constexpr int kGradStride = 24;   // dmean2(2) dconic(3) dopacity(1) dcolour(3) 
 cudaError_t launch_tables_init(const ViewDesc* host_views, int nviews, ViewDesc* dev_views,
                                const SceneDesc* host_scenes, int nscenes, SceneDesc* dev_scenes,
                                cudaStream_t s);
+// count of kernel launches the library has enqueued (stp_kernel_launches)
+void note_launches(int n);
+
 cudaError_t launch_preprocess(const PipeArgs& a, cudaStream_t s);
 cudaError_t launch_scan_counts(const PipeArgs& a, cudaStream_t s);
 cudaError_t launch_scan_tiles(const PipeArgs& a, cudaStream_t s);

@@ -210,6 +210,11 @@ __device__ __forceinline__ Rec shfl_rec(const Rec& r, int src)
     return o;
 }
 
+__device__ __forceinline__ float tile_cull_eps(const PipeArgs& a)
+{
+    return (a.flags & kFlagNoTileCull) ? -1.f : a.eps_o;
+}
+
 // Depth key of one (Gaussian, tile) pair if the tile is kept: ordered bits of t_opt on the ray
 // through the tile's x_hat (or the tile centre / the view-space depth, by flag).
 __device__ __forceinline__ bool tile_depth_key(const PipeArgs& a, const ViewDesc& V, const Rec& r,
@@ -217,18 +222,17 @@ __device__ __forceinline__ bool tile_depth_key(const PipeArgs& a, const ViewDesc
 {
     const Box b = block_box(tx * kTile, ty * kTile, kTile, V.W, V.H);
     float t = 0.f;
-    if (a.flags & kFlagNoTileCull) t = box_depth(r, b, V, (a.flags & 4) != 0);
-    else if (!box_keep_depth(r, b, V, a.eps_o, (a.flags & 4) != 0, &t)) return false;
+    if (!box_keep_depth(r, b, V, tile_cull_eps(a), (a.flags & 4) != 0, &t)) return false;
     if (a.flags & 8) t = r.r5.y;
     *dkey = fkey(t);
     return true;
 }
 
 // Tile-based culling decision (Sec. 3.4); flag kFlagNoTileCull keeps every tile of the
-// rectangle (ablation D of the paper's performance table).
+// rectangle (ablation D of the paper's performance table) through a threshold of -1.
 __device__ __forceinline__ bool tile_keep(const PipeArgs& a, const Rec& r, const Box& b)
 {
-    return (a.flags & kFlagNoTileCull) != 0 || box_keep(r, b, a.eps_o);
+    return box_keep(r, b, tile_cull_eps(a));
 }
 
 // Partitioned sort (appendix B.3): count a kept entry of global tile `gt`. Lanes of the
@@ -598,6 +602,7 @@ cudaError_t launch_tables_init(const ViewDesc* host_views, int nviews, ViewDesc*
     for (int k = 0; k < nviews && k < kMaxViews; k++) pack.v[k] = host_views[k];
     for (int k = 0; k < nscenes && k < kMaxScenes; k++) pack.sc[k] = host_scenes[k];
     k_tables_copy<<<1, kMaxViews, 0, s>>>(pack, nviews, dev_views, nscenes, dev_scenes);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -605,6 +610,7 @@ cudaError_t launch_preprocess(const PipeArgs& a, cudaStream_t s)
 {
     if (a.threads == 0) return cudaSuccess;
     k_preprocess<<<(unsigned)(a.threads / 256), 256, 0, s>>>(a);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -615,6 +621,7 @@ static cudaError_t scan_u32(const uint32_t* in, uint32_t* out, unsigned long lon
     if (nb > 0) k_scan_reduce<<<nb, kScanThreads, 0, s>>>(in, m, partials);
     k_scan_partials<<<1, 1024, 0, s>>>(partials, nb, st);
     if (nb > 0) k_scan_apply<<<nb, kScanThreads, 0, s>>>(in, m, partials, out);
+    note_launches(nb > 0 ? 3 : 1);
     return cudaGetLastError();
 }
 
@@ -632,6 +639,7 @@ cudaError_t launch_duplicate(const PipeArgs& a, cudaStream_t s)
 {
     if (a.threads == 0) return cudaSuccess;
     k_duplicate<<<(unsigned)(a.threads / 256), 256, 0, s>>>(a);
+    note_launches(1);
     return cudaGetLastError();
 }
 

@@ -47,6 +47,13 @@ __device__ __forceinline__ uint32_t depth_key(float t)
     return k == kInvalidKey ? kInvalidKey - 1u : k;
 }
 
+// cull threshold of the 4x4 / 2x2 levels: eps_O, or -1 (nothing culled, ablation E) since
+// opacity * G2 >= 0
+__device__ __forceinline__ float level_cull_eps(const PipeArgs& a)
+{
+    return (a.flags & kFlagNoHierCull) ? -1.f : a.eps_o;
+}
+
 template <int HEAD>
 struct Px {
     float T, C0, C1, C2, Z;
@@ -135,34 +142,20 @@ __device__ __forceinline__ void blend(const PipeArgs& a, const ViewDesc& V, Px<H
         }
     }
     if (!BWD && a.dbg_trace && s.nbl < (uint32_t)kTraceLen) a.dbg_trace[c.pix * kTraceLen + s.nbl] = (int)id;
-    if (!BWD && a.dbg_delta) {
+    if (!BWD && a.dbg_hash) {          // debug statistics: order hash and sort error
+        s.hash = s.hash * kHashMul + (unsigned long long)(id + 1u);
         if (s.nbl > 0 && s.last_t > t) s.delta += s.last_t - t;
         s.last_t = t;
     }
     s.T = Tn;
     s.nbl++;
-    if (a.dbg_hash) s.hash = s.hash * kHashMul + (unsigned long long)(id + 1u);
 }
 
-// insert (key, id, val) after equal keys; when more than HEAD entries are held blend the
-// smallest (Sec. 3.3 k-buffer; evict_first = the alternative "blend before insert" reading)
-template <int HEAD, bool BWD>
-__device__ __forceinline__ void head_push(const PipeArgs& a, const ViewDesc& V, Px<HEAD>& s,
-                                          const PixCtx& c, uint32_t key, uint32_t id, float val,
-                                          bool evict_first)
+// head (per-pixel k-buffer, Sec. 3.3) primitives on register arrays with static indices
+template <int HEAD>
+__device__ __forceinline__ void head_insert(Px<HEAD>& s, uint32_t key, uint32_t id, float val)
 {
-    if (evict_first && s.nh == HEAD) {
-        blend<HEAD, BWD>(a, V, s, c, s.hk[0], s.hid[0], s.hv[0]);
-#pragma unroll
-        for (int j = 0; j < HEAD; j++) {
-            s.hk[j] = s.hk[j + 1];
-            s.hid[j] = s.hid[j + 1];
-            s.hv[j] = s.hv[j + 1];
-        }
-        s.hk[HEAD] = kInvalidKey;
-        s.nh--;
-        if (s.done) return;
-    }
+    // insert after equal keys (stable)
     uint32_t nk[HEAD + 1], ni[HEAD + 1];
     float nv[HEAD + 1];
 #pragma unroll
@@ -180,16 +173,53 @@ __device__ __forceinline__ void head_push(const PipeArgs& a, const ViewDesc& V, 
         s.hv[j] = nv[j];
     }
     s.nh++;
-    if (s.nh > HEAD) {
-        blend<HEAD, BWD>(a, V, s, c, s.hk[0], s.hid[0], s.hv[0]);
+}
+
+template <int HEAD>
+__device__ __forceinline__ void head_pop(Px<HEAD>& s, uint32_t& key, uint32_t& id, float& val)
+{
+    key = s.hk[0];
+    id = s.hid[0];
+    val = s.hv[0];
 #pragma unroll
-        for (int j = 0; j < HEAD; j++) {
-            s.hk[j] = s.hk[j + 1];
-            s.hid[j] = s.hid[j + 1];
-            s.hv[j] = s.hv[j + 1];
-        }
-        s.hk[HEAD] = kInvalidKey;
-        s.nh--;
+    for (int j = 0; j < HEAD; j++) {
+        s.hk[j] = s.hk[j + 1];
+        s.hid[j] = s.hid[j + 1];
+        s.hv[j] = s.hv[j + 1];
+    }
+    s.hk[HEAD] = kInvalidKey;
+    s.nh--;
+}
+
+// Insert (key, id, val); when more than HEAD entries are held blend the smallest (Sec. 3.3
+// k-buffer; evict_first = the alternative "blend before insert" reading). The blend sits at one
+// call site so that its body (large in the backward replay) is inlined once.
+template <int HEAD, bool BWD>
+__device__ __forceinline__ void head_push(const PipeArgs& a, const ViewDesc& V, Px<HEAD>& s,
+                                          const PixCtx& c, uint32_t key, uint32_t id, float val,
+                                          bool evict_first)
+{
+    const bool pop_first = evict_first && s.nh == HEAD;
+    if (!pop_first) head_insert(s, key, id, val);
+    if (pop_first || s.nh > HEAD) {
+        uint32_t k, i;
+        float v;
+        head_pop(s, k, i, v);
+        blend<HEAD, BWD>(a, V, s, c, k, i, v);
+        if (pop_first && !s.done) head_insert(s, key, id, val);
+    }
+}
+
+// blend what the head still holds, nearest first
+template <int HEAD, bool BWD>
+__device__ __forceinline__ void head_flush(const PipeArgs& a, const ViewDesc& V, Px<HEAD>& s, const PixCtx& c)
+{
+#pragma unroll 1
+    while (s.nh > 0 && !s.done) {
+        uint32_t k, i;
+        float v;
+        head_pop(s, k, i, v);
+        blend<HEAD, BWD>(a, V, s, c, k, i, v);
     }
 }
 
@@ -203,23 +233,21 @@ __device__ __forceinline__ void headstage(const PipeArgs& a, const ViewDesc& V, 
                                           const PixCtx& c, Warp& wq, uint2* mq, bool pop, int cap)
 {
     const int pc = pop ? min(cap, wq.nm) : 0;
-    uint2 el[4];
-#pragma unroll
-    for (int k = 0; k < 4; k++) el[k] = k < pc ? mq[wq.ms + k] : make_uint2(0u, 0u);
+    const int ms0 = wq.ms;
     wq.ms += pc;
     wq.nm -= pc;
     const bool evict_first = (a.flags & 1) != 0;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        if (k < pc && !s.done) {
-            const uint32_t gid = el[k].y;
-            const Rec r = load_rec(a.geom, V.rec_off + gid);
-            const float val = splat_value(r, c.xc, c.yc);
-            if (a.dbg_nblend != nullptr && !BWD) atomicAdd(&a.status->counters[4], 1ull);
-            if (fminf(a.alpha_max, val) >= a.eps_o) {
-                const float t = depth_uvn(r, c.u, c.w, c.n);
-                head_push<HEAD, BWD>(a, V, s, c, depth_key(t), gid, val, evict_first);
-            }
+    // not unrolled: one inlined copy of the head step (and of its blend); the entries are read
+    // from the quad's mid queue, which nothing writes until the warp's next merge
+#pragma unroll 1
+    for (int k = 0; k < pc && !s.done; k++) {
+        const uint32_t gid = mq[ms0 + k].y;
+        const Rec r = load_rec(a.geom, V.rec_off + gid);
+        const float val = splat_value(r, c.xc, c.yc);
+        if (a.dbg_nblend != nullptr && !BWD) atomicAdd(&a.status->counters[4], 1ull);
+        if (fminf(a.alpha_max, val) >= a.eps_o) {
+            const float t = depth_uvn(r, c.u, c.w, c.n);
+            head_push<HEAD, BWD>(a, V, s, c, depth_key(t), gid, val, evict_first);
         }
     }
 }
@@ -235,7 +263,7 @@ __device__ void midstage(const PipeArgs& a, const ViewDesc& V, Px<HEAD>& s, cons
     const int cmax = max(c0, c1);
     const int MID = a.mid;
     const bool centre = (a.flags & 2) != 0;
-    const bool nocull = (a.flags & kFlagNoHierCull) != 0;
+    const float cull_eps = level_cull_eps(a);
     // a quad whose four pixels are saturated takes no further part (its results are final)
     const unsigned live = __ballot_sync(kFull, !s.done);
     const bool qlive = qval && ((live >> qbase) & 0xFu) != 0;
@@ -248,8 +276,7 @@ __device__ void midstage(const PipeArgs& a, const ViewDesc& V, Px<HEAD>& s, cons
                 const Rec r = load_rec(a.geom, V.rec_off + gid);
                 const Box bq = bQ;
                 float t;
-                if (nocull) key = depth_key(box_depth(r, bq, V, centre));
-                else if (box_keep_depth(r, bq, V, a.eps_o, centre, &t)) key = depth_key(t);
+                if (box_keep_depth(r, bq, V, cull_eps, centre, &t)) key = depth_key(t);
             }
         }
         // stable rank of the new entry among the quad's (up to) four
@@ -408,7 +435,7 @@ __global__ void __launch_bounds__(256) k_render(PipeArgs a)
     const uint2 rg = a.ranges[gtile];
     const int lst = (int)rg.x, nL = (int)(rg.y - rg.x);
     const bool centre = (a.flags & 2) != 0;
-    const bool nocull = (a.flags & kFlagNoHierCull) != 0;
+    const float cull_eps = level_cull_eps(a);
     const bool count = a.dbg_nblend != nullptr && !BWD;
     unsigned long long n_eval_s = 0, n_surv_s = 0;
     bool finished = false;
@@ -427,13 +454,8 @@ __global__ void __launch_bounds__(256) k_render(PipeArgs a)
         if (in && (s0 || s1)) {
             const Rec r = load_rec(a.geom, V.rec_off + gid);
             float t;
-            if (nocull) {
-                if (s0) k0 = depth_key(box_depth(r, bS[0], V, centre));
-                if (s1) k1 = depth_key(box_depth(r, bS[1], V, centre));
-            } else {
-                if (s0 && box_keep_depth(r, bS[0], V, a.eps_o, centre, &t)) k0 = depth_key(t);
-                if (s1 && box_keep_depth(r, bS[1], V, a.eps_o, centre, &t)) k1 = depth_key(t);
-            }
+            if (s0 && box_keep_depth(r, bS[0], V, cull_eps, centre, &t)) k0 = depth_key(t);
+            if (s1 && box_keep_depth(r, bS[1], V, cull_eps, centre, &t)) k1 = depth_key(t);
         }
         uint32_t r0 = 0, r1 = 0;
 #pragma unroll 8
@@ -483,9 +505,7 @@ __global__ void __launch_bounds__(256) k_render(PipeArgs a)
             headstage<HEAD, BWD>(a, V, s, c, wq, mq, wq.nm > 0, 4);
             __syncwarp();
         }
-#pragma unroll
-        for (int j = 0; j < HEAD; j++)
-            if (j < s.nh) blend<HEAD, BWD>(a, V, s, c, s.hk[j], s.hid[j], s.hv[j]);
+        head_flush<HEAD, BWD>(a, V, s, c);
     }
     if (count) {
         if (lane == 0) {
@@ -520,9 +540,11 @@ cudaError_t launch_head(const PipeArgs& a, bool bwd, size_t smem, cudaStream_t s
     if (bwd) {
         if ((e = ensure_smem_limit(k_render<HEAD, true>, smem, set_bwd, 64)) != cudaSuccess) return e;
         k_render<HEAD, true><<<a.total_tiles, 256, smem, s>>>(a);
+        note_launches(1);
     } else {
         if ((e = ensure_smem_limit(k_render<HEAD, false>, smem, set_fwd, 64)) != cudaSuccess) return e;
         k_render<HEAD, false><<<a.total_tiles, 256, smem, s>>>(a);
+        note_launches(1);
     }
     return cudaGetLastError();
 }
@@ -664,12 +686,22 @@ __global__ void __launch_bounds__(256) k_render_flat(PipeArgs a)
         }
         if (mode == STP_MODE_FULL_ID) {
             if (more) {
-#pragma unroll
-                for (int j = 0; j < HEAD; j++)
-                    if (j < nc && !s.done) blend<HEAD, false>(a, V, s, c, (uint32_t)(ck[j] >> 32), cid[j], cv[j]);
                 if (nc > 0) {
-                    last = ck[nc - 1];
+#pragma unroll
+                    for (int q = 0; q < HEAD; q++)
+                        if (q == nc - 1) last = ck[q];
                     has_last = true;
+                }
+                // blend the peeled entries nearest first (shifting keeps the indices static)
+#pragma unroll 1
+                for (int j = 0; j < nc && !s.done; j++) {
+                    blend<HEAD, false>(a, V, s, c, (uint32_t)(ck[0] >> 32), cid[0], cv[0]);
+#pragma unroll
+                    for (int q = 0; q + 1 < HEAD; q++) {
+                        ck[q] = ck[q + 1];
+                        cid[q] = cid[q + 1];
+                        cv[q] = cv[q + 1];
+                    }
                 }
                 more = nc == HEAD && !s.done;     // fewer than HEAD found: the list is exhausted
             }
@@ -680,11 +712,7 @@ __global__ void __launch_bounds__(256) k_render_flat(PipeArgs a)
             if (!__syncthreads_or(more)) break;
         }
     } while (mode == STP_MODE_FULL_ID);
-    if (mode == STP_MODE_WINDOW_ID) {
-#pragma unroll
-        for (int j = 0; j < HEAD; j++)
-            if (j < s.nh) blend<HEAD, false>(a, V, s, c, s.hk[j], s.hid[j], s.hv[j]);
-    }
+    if (mode == STP_MODE_WINDOW_ID) head_flush<HEAD, false>(a, V, s, c);
     if (count) {
         atomicAdd(&a.status->counters[4], n_eval);
         atomicAdd(&a.status->counters[3], (unsigned long long)s.nbl);
@@ -706,6 +734,7 @@ template <int HEAD>
 cudaError_t launch_flat(const PipeArgs& a, cudaStream_t s)
 {
     k_render_flat<HEAD><<<a.total_tiles, 256, 0, s>>>(a);
+    note_launches(1);
     return cudaGetLastError();
 }
 

@@ -356,6 +356,7 @@ static void sort_pass(const uint64_t* sk, const uint32_t* sv, uint64_t* dk, uint
     k_hist<<<G, kThreads, 0, s>>>(sk, n, n_dev, shift, hist, G);
     k_scan<<<1, 1024, 0, s>>>(hist, kRadix * G);
     k_scatter<<<G, kThreads, 0, s>>>(sk, sv, dk, dv, n, n_dev, shift, hist, G);
+    note_launches(3);
 }
 
 // Sort with explicit scratch: hist holds kRadix x grid counters, (kalt, valt) is the ping-pong
@@ -478,6 +479,7 @@ cudaError_t launch_tile_sort(const PipeArgs& a, cudaStream_t s)
     cudaError_t e = ensure_smem_limit(k_tile_sort, smem, set_dev, 64);
     if (e != cudaSuccess) return e;
     k_tile_sort<<<a.total_tiles, kSegThreads, smem, s>>>(a);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -488,6 +490,7 @@ cudaError_t launch_ranges(const PipeArgs& a, cudaStream_t s)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     k_ranges<<<sms * 8, 256, 0, s>>>(a.skeys, (long long)a.capacity, a.status, a.total_tiles, a.ranges);
+    note_launches(1);
     return cudaGetLastError();
 }
 
