@@ -439,68 +439,82 @@ __global__ void __launch_bounds__(256) k_render(PipeArgs a)
     const bool count = a.dbg_nblend != nullptr && !BWD;
     unsigned long long n_eval_s = 0, n_surv_s = 0;
     bool finished = false;
-    for (int b0 = 0; b0 < nL; b0 += 32) {
+    // One loop for the batches and the drain, so that the mid stage (and the head stage and
+    // blend inside it) is inlined once. While batches remain, a batch is loaded and merged and
+    // the tails pop 16 while they hold more than TAIL-32; afterwards each iteration pops one
+    // chunk of at most 16 per subtile until the tails are empty.
+    int b0 = 0;
+    for (;;) {
+        const bool batch = b0 < nL;
         if (__all_sync(kFull, s.done)) {
-            finished = true;
+            finished = batch;
             break;
         }
-        const int idx = b0 + lane;
-        const bool in = idx < nL;
-        const uint32_t gid = in ? __ldg(a.svals + lst + idx) : 0u;
-        uint32_t k0 = kInvalidKey, k1 = kInvalidKey;
-        // a subtile whose sixteen pixels are saturated takes no further part
-        const unsigned live = __ballot_sync(kFull, !s.done);
-        const bool s0 = sval[0] && (live & 0xFFFFu) != 0, s1 = sval[1] && (live >> 16) != 0;
-        if (in && (s0 || s1)) {
-            const Rec r = load_rec(a.geom, V.rec_off + gid);
-            float t;
-            if (s0 && box_keep_depth(r, bS[0], V, cull_eps, centre, &t)) k0 = depth_key(t);
-            if (s1 && box_keep_depth(r, bS[1], V, cull_eps, centre, &t)) k1 = depth_key(t);
-        }
-        uint32_t r0 = 0, r1 = 0;
+        if (batch) {
+            const int idx = b0 + lane;
+            const bool in = idx < nL;
+            const uint32_t gid = in ? __ldg(a.svals + lst + idx) : 0u;
+            uint32_t k0 = kInvalidKey, k1 = kInvalidKey;
+            // a subtile whose sixteen pixels are saturated takes no further part
+            const unsigned live = __ballot_sync(kFull, !s.done);
+            const bool s0 = sval[0] && (live & 0xFFFFu) != 0, s1 = sval[1] && (live >> 16) != 0;
+            if (in && (s0 || s1)) {
+                const Rec r = load_rec(a.geom, V.rec_off + gid);
+                float t;
+                if (s0 && box_keep_depth(r, bS[0], V, cull_eps, centre, &t)) k0 = depth_key(t);
+                if (s1 && box_keep_depth(r, bS[1], V, cull_eps, centre, &t)) k1 = depth_key(t);
+            }
+            uint32_t r0 = 0, r1 = 0;
 #pragma unroll 8
-        for (int j = 0; j < 32; j++) {
-            const uint32_t o0 = __shfl_sync(kFull, k0, j), o1 = __shfl_sync(kFull, k1, j);
-            r0 += (o0 < k0) || (o0 == k0 && j < lane);
-            r1 += (o1 < k1) || (o1 == k1 && j < lane);
-        }
-        const int nn0 = __popc(__ballot_sync(kFull, k0 != kInvalidKey));
-        const int nn1 = __popc(__ballot_sync(kFull, k1 != kInvalidKey));
-        if (count && lane == 0) {
-            const int nin = min(32, nL - b0);
-            n_eval_s += (unsigned long long)nin * ((sval[0] ? 1 : 0) + (sval[1] ? 1 : 0));
-            n_surv_s += (unsigned long long)(nn0 + nn1);
-        }
-        if (k0 != kInvalidKey) stage[r0] = make_uint2(k0, gid);
-        if (k1 != kInvalidKey) stage[32 + r1] = make_uint2(k1, gid);
-        __syncwarp();
-        merge_tail(tailb + (0 * 2 + wq.tb[0]) * TAIL + wq.ts[0], wq.nt[0], stage, nn0,
-                   tailb + (0 * 2 + (wq.tb[0] ^ 1)) * TAIL, lane);
-        merge_tail(tailb + (1 * 2 + wq.tb[1]) * TAIL + wq.ts[1], wq.nt[1], stage + 32, nn1,
-                   tailb + (1 * 2 + (wq.tb[1] ^ 1)) * TAIL, lane);
-        __syncwarp();
-        wq.nt[0] += nn0;
-        wq.nt[1] += nn1;
-        wq.ts[0] = wq.ts[1] = 0;
-        wq.tb[0] ^= 1;
-        wq.tb[1] ^= 1;
-        while (wq.nt[0] > TAIL - 32 || wq.nt[1] > TAIL - 32) {
-            const int c0 = wq.nt[0] > TAIL - 32 ? 16 : 0, c1 = wq.nt[1] > TAIL - 32 ? 16 : 0;
-            midstage<HEAD, BWD>(a, V, s, c, wq, tailb, mq, bQ, qval, c0, c1, lane);
-            wq.ts[0] += c0; wq.nt[0] -= c0;
-            wq.ts[1] += c1; wq.nt[1] -= c1;
-        }
-    }
-    if (!finished) {
-        while ((wq.nt[0] > 0 || wq.nt[1] > 0) && !__all_sync(kFull, s.done)) {
+            for (int j = 0; j < 32; j++) {
+                const uint32_t o0 = __shfl_sync(kFull, k0, j), o1 = __shfl_sync(kFull, k1, j);
+                r0 += (o0 < k0) || (o0 == k0 && j < lane);
+                r1 += (o1 < k1) || (o1 == k1 && j < lane);
+            }
+            const int nn0 = __popc(__ballot_sync(kFull, k0 != kInvalidKey));
+            const int nn1 = __popc(__ballot_sync(kFull, k1 != kInvalidKey));
+            if (count && lane == 0) {
+                const int nin = min(32, nL - b0);
+                n_eval_s += (unsigned long long)nin * ((sval[0] ? 1 : 0) + (sval[1] ? 1 : 0));
+                n_surv_s += (unsigned long long)(nn0 + nn1);
+            }
+            if (k0 != kInvalidKey) stage[r0] = make_uint2(k0, gid);
+            if (k1 != kInvalidKey) stage[32 + r1] = make_uint2(k1, gid);
+            __syncwarp();
+            merge_tail(tailb + (0 * 2 + wq.tb[0]) * TAIL + wq.ts[0], wq.nt[0], stage, nn0,
+                       tailb + (0 * 2 + (wq.tb[0] ^ 1)) * TAIL, lane);
+            merge_tail(tailb + (1 * 2 + wq.tb[1]) * TAIL + wq.ts[1], wq.nt[1], stage + 32, nn1,
+                       tailb + (1 * 2 + (wq.tb[1] ^ 1)) * TAIL, lane);
+            __syncwarp();
+            wq.nt[0] += nn0;
+            wq.nt[1] += nn1;
+            wq.ts[0] = wq.ts[1] = 0;
+            wq.tb[0] ^= 1;
+            wq.tb[1] ^= 1;
+            b0 += 32;
+        } else {
+            if (wq.nt[0] == 0 && wq.nt[1] == 0) break;
             const unsigned live = __ballot_sync(kFull, !s.done);
             if ((live & 0xFFFFu) == 0) wq.nt[0] = 0;
             if ((live >> 16) == 0) wq.nt[1] = 0;
-            const int c0 = min(16, wq.nt[0]), c1 = min(16, wq.nt[1]);
+        }
+        for (;;) {
+            int c0, c1;
+            if (batch) {
+                c0 = wq.nt[0] > TAIL - 32 ? 16 : 0;
+                c1 = wq.nt[1] > TAIL - 32 ? 16 : 0;
+                if (c0 == 0 && c1 == 0) break;
+            } else {
+                c0 = min(16, wq.nt[0]);
+                c1 = min(16, wq.nt[1]);
+            }
             midstage<HEAD, BWD>(a, V, s, c, wq, tailb, mq, bQ, qval, c0, c1, lane);
             wq.ts[0] += c0; wq.nt[0] -= c0;
             wq.ts[1] += c1; wq.nt[1] -= c1;
+            if (!batch) break;
         }
+    }
+    if (!finished) {
         while (__any_sync(kFull, wq.nm > 0) && !__all_sync(kFull, s.done)) {
             headstage<HEAD, BWD>(a, V, s, c, wq, mq, wq.nm > 0, 4);
             __syncwarp();
