@@ -95,7 +95,7 @@ stp_status check(const int64_t* ns, const int32_t* vps, int32_t nscenes, const s
         m += ns[s] * (long long)vps[s];
     }
     if (vsum != nviews) return fail(STP_ERR_ARG, "views per scene sum to %lld, nviews = %d", vsum, nviews);
-    if (threads / 256 >= (1LL << 31) || m >= (1LL << 40))
+    if (threads / 256 >= (1LL << 31) || (m + 256LL * nscenes) / 256 >= (1LL << 31))
         return fail(STP_ERR_ARG, "scenes too large for one launch sequence");
     for (int v = 0; v < nviews; v++) {
         const stp_camera& c = cams[v];
@@ -130,6 +130,7 @@ struct Plan {
     stp_workspace_layout L;
     long long m;                       // render records: sum over views of the view's scene size
     long long threads;                 // per-Gaussian threads (scenes aligned to kSceneAlign)
+    long long rec_threads;             // per-(Gaussian, view) threads (likewise)
     std::vector<stp::ViewDesc> views;
     std::vector<stp::SceneDesc> scenes;   // sizes and view ranges; pointers filled per call
 };
@@ -140,7 +141,7 @@ void make_plan(const int64_t* ns, const int32_t* vps, int32_t nscenes, const stp
     std::memset(&P.L, 0, sizeof P.L);
     P.views.resize(nviews);
     P.scenes.resize(nscenes);
-    long long tiles = 0, pixels = 0, rec = 0, threads = 0;
+    long long tiles = 0, pixels = 0, rec = 0, threads = 0, rec_threads = 0;
     int v = 0;
     for (int sc = 0; sc < nscenes; sc++) {
         stp::SceneDesc& S = P.scenes[sc];
@@ -149,7 +150,9 @@ void make_plan(const int64_t* ns, const int32_t* vps, int32_t nscenes, const stp
         S.view_begin = v;
         S.view_end = v + vps[sc];
         S.thread_off = threads;
+        S.rec_thread_off = rec_threads;
         threads += (ns[sc] + stp::kSceneAlign - 1) / stp::kSceneAlign * stp::kSceneAlign;
+        rec_threads += (ns[sc] * vps[sc] + stp::kSceneAlign - 1) / stp::kSceneAlign * stp::kSceneAlign;
         for (; v < S.view_end; v++) {
             const stp_camera& c = cams[v];
             stp::ViewDesc& d = P.views[v];
@@ -175,6 +178,7 @@ void make_plan(const int64_t* ns, const int32_t* vps, int32_t nscenes, const stp
     }
     P.m = rec;
     P.threads = threads;
+    P.rec_threads = rec_threads;
     long long cap = p->max_entries > 0 ? p->max_entries : std::max<long long>(1LL << 20, 4LL * P.m);
     if (cap > 0xFFFFFFFELL) cap = 0xFFFFFFFELL;
     stp_workspace_layout& L = P.L;
@@ -231,6 +235,7 @@ stp::PipeArgs make_args(const stp_params* p, const Plan& P, void* ws)
     a.scenes = (const stp::SceneDesc*)(b + L.scenes);
     a.nscenes = (int)P.scenes.size();
     a.threads = P.threads;
+    a.rec_threads = P.rec_threads;
     a.m = P.m;
     a.nviews = (int)P.views.size();
     a.lb_threshold = p->lb_threshold; a.flags = p->flags; a.mode = p->mode; a.window_k = p->window_k;

@@ -51,9 +51,9 @@ struct ViewDesc {
 };
 
 // ---------------------------------------------------------------- per-scene constants
-// The per-Gaussian kernels run one thread per (scene, Gaussian); each scene starts on a
-// kSceneAlign boundary of the thread index space, so a thread block never straddles two scenes
-// and every warp loops over the same views.
+// The per-Gaussian kernels run one thread per (scene, Gaussian), the per-record kernels one
+// thread per (scene, Gaussian, view); each scene starts on a kSceneAlign boundary of either
+// thread index space, so a thread block never straddles two scenes.
 struct SceneDesc {
     const float* means;          // [n][3]
     const float* log_scales;     // [n][3]
@@ -67,7 +67,10 @@ struct SceneDesc {
     float* g_sh;
     int n, sh_k;
     int view_begin, view_end;    // the scene's views [view_begin, view_end)
-    long long thread_off;        // first thread of the scene (multiple of kSceneAlign)
+    long long thread_off;        // per-Gaussian kernels: first thread (multiple of kSceneAlign)
+    long long rec_thread_off;    // per-(Gaussian, view) kernels: first thread (multiple of
+                                 // kSceneAlign); thread t of the scene takes Gaussian t / nv of
+                                 // view view_begin + t % nv (views fastest within a warp)
 };
 
 // ---------------------------------------------------------------- render record

@@ -14,6 +14,7 @@ struct PipeArgs {
     const SceneDesc* scenes;
     int nscenes;
     long long threads;       // per-Gaussian thread count: sum over scenes of n rounded up to kSceneAlign
+    long long rec_threads;   // per-record thread count: sum over scenes of n * views, rounded likewise
     long long m;             // render records: sum over views of the view's scene size
     int nviews, lb_threshold, flags, mode, window_k, tail, mid, head;
     float eps_o, t_min, alpha_max, inv_scale_max, dilation, znear;
@@ -71,6 +72,18 @@ __device__ __forceinline__ int scene_of(const PipeArgs& a, long long t0)
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (a.scenes[mid].thread_off <= t0) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Scene of the per-record thread block whose first thread is t0.
+__device__ __forceinline__ int scene_of_rec(const PipeArgs& a, long long t0)
+{
+    int lo = 0, hi = a.nscenes - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.scenes[mid].rec_thread_off <= t0) lo = mid;
         else hi = mid - 1;
     }
     return lo;

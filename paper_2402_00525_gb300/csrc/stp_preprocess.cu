@@ -287,7 +287,7 @@ __device__ __forceinline__ uint32_t kept_depth_key(const PipeArgs& a, const View
 // With the global radix sort the keys go to the Gaussian's own range [off, off + want) in
 // tile order; with the partitioned sort they go to their tiles' ranges.
 template <bool EMIT>
-__device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, bool has, const Rec& r,
+__device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, int vidx, bool has, const Rec& r,
                                ushort4 rc, uint32_t off, uint32_t want, uint32_t gid, uint32_t* mask_io)
 {
     const int lane = threadIdx.x & 31;
@@ -387,6 +387,7 @@ __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, bool has, c
         const int x0 = __shfl_sync(kFull, (int)rc.x, src), y0 = __shfl_sync(kFull, (int)rc.y, src);
         const uint32_t offs = __shfl_sync(kFull, off, src), wants = __shfl_sync(kFull, want, src);
         const uint32_t gids = __shfl_sync(kFull, gid, src);
+        const ViewDesc& Vs = a.views[__shfl_sync(kFull, vidx, src)];    // the source lane's view
         uint32_t base = 0;
         for (int k0 = 0; k0 < nc; k0 += 32) {
             const int k = k0 + lane;
@@ -394,9 +395,9 @@ __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, bool has, c
             uint32_t dk = 0, gt = 0;
             if (k < nc) {
                 const int tx = x0 + k % ws, ty = y0 + k / ws;
-                gt = (uint32_t)(V.tile_off + ty * V.tiles_x + tx);
-                if (EMIT) keep = tile_depth_key(a, V, rs, tx, ty, &dk);
-                else keep = tile_keep(a, rs, block_box(tx * kTile, ty * kTile, kTile, V.W, V.H));
+                gt = (uint32_t)(Vs.tile_off + ty * Vs.tiles_x + tx);
+                if (EMIT) keep = tile_depth_key(a, Vs, rs, tx, ty, &dk);
+                else keep = tile_keep(a, rs, block_box(tx * kTile, ty * kTile, kTile, Vs.W, Vs.H));
             }
             const unsigned m = __ballot_sync(kFull, keep);
             if (keep) {
@@ -422,70 +423,97 @@ __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, bool has, c
     return cnt;
 }
 
-__global__ void __launch_bounds__(256) k_preprocess(PipeArgs a)
+// One thread per (Gaussian, view), the scene's views fastest within a warp: lanes that share a
+// Gaussian see it from different cameras, so their tile counts are alike (little divergence).
+// 128-thread blocks (scenes start on 256-thread boundaries, so a block never straddles two)
+// keep more warps resident per SM than 256-thread blocks at these register counts.
+struct RecThread {
+    SceneDesc S;
+    int i, v;                    // Gaussian (scene-local) and view (global index)
+    bool live;
+};
+
+__device__ __forceinline__ RecThread rec_thread(const PipeArgs& a)
 {
+    RecThread t;
     const long long t0 = (long long)blockIdx.x * blockDim.x;
-    const SceneDesc S = a.scenes[scene_of(a, t0)];
-    const int i = (int)(t0 - S.thread_off) + threadIdx.x;
-    const bool live = i < S.n;
-    GaussIn g;
-    if (live) load_gauss(a, S, i, g);
-    for (int v = S.view_begin; v < S.view_end; v++) {
-        const ViewDesc& V = a.views[v];
-        Rec r;
-        float4 col;
-        ushort4 rc = make_ushort4(0, 0, 0, 0);
-        bool vis = false;
-        if (live) vis = make_record(a, V, g, i, r, col, rc);
-        else r.r0 = r.r1 = r.r2 = r.r3 = r.r4 = r.r5 = make_float4(0.f, 0.f, 0.f, 0.f);
-        uint32_t mask = 0;
-        const uint32_t cnt = tiles_pass<false>(a, V, vis, r, rc, 0, 0, 0, &mask);
-        if (live) {
-            a.keep_mask[V.rec_off + i] = mask;
-            const long long o = V.rec_off + i;
-            float4* gp = a.geom + kRecFloat4 * o;
-            gp[0] = r.r0; gp[1] = r.r1; gp[2] = r.r2; gp[3] = r.r3; gp[4] = r.r4; gp[5] = r.r5;
-            a.color[o] = col;
-            a.rect[o] = rc;
-            a.counts[o] = cnt;
+    t.S = a.scenes[scene_of_rec(a, t0)];
+    const int nv = t.S.view_end - t.S.view_begin;
+    const long long lt = t0 - t.S.rec_thread_off + threadIdx.x;
+    long long q = 0, rm = 0;
+    if (nv > 0) {
+        if (lt < 0xFFFFFFFFll) {         // 32-bit division when it fits (the common case)
+            q = (uint32_t)lt / (uint32_t)nv;
+            rm = (uint32_t)lt - (uint32_t)q * (uint32_t)nv;
+        } else {
+            q = lt / nv;
+            rm = lt - q * nv;
         }
+    }
+    t.i = q < (1LL << 31) ? (int)q : 0x7FFFFFFF;
+    t.v = t.S.view_begin + (int)rm;
+    t.live = nv > 0 && t.i < t.S.n;
+    return t;
+}
+
+__global__ void __launch_bounds__(128) k_preprocess(PipeArgs a)
+{
+    const RecThread th = rec_thread(a);
+    const int i = th.i;
+    const ViewDesc& V = a.views[th.v];
+    Rec r;
+    float4 col;
+    ushort4 rc = make_ushort4(0, 0, 0, 0);
+    bool vis = false;
+    if (th.live) {
+        GaussIn g;
+        load_gauss(a, th.S, i, g);
+        vis = make_record(a, V, g, i, r, col, rc);
+    } else {
+        r.r0 = r.r1 = r.r2 = r.r3 = r.r4 = r.r5 = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    uint32_t mask = 0;
+    const uint32_t cnt = tiles_pass<false>(a, V, th.v, vis, r, rc, 0, 0, 0, &mask);
+    if (th.live) {
+        const long long o = V.rec_off + i;
+        a.keep_mask[o] = mask;
+        float4* gp = a.geom + kRecFloat4 * o;
+        gp[0] = r.r0; gp[1] = r.r1; gp[2] = r.r2; gp[3] = r.r3; gp[4] = r.r4; gp[5] = r.r5;
+        a.color[o] = col;
+        a.rect[o] = rc;
+        a.counts[o] = cnt;
     }
 }
 
-__global__ void __launch_bounds__(256) k_duplicate(PipeArgs a)
+__global__ void __launch_bounds__(128) k_duplicate(PipeArgs a)
 {
-    const long long t0 = (long long)blockIdx.x * blockDim.x;
-    const SceneDesc& S = a.scenes[scene_of(a, t0)];
-    const int i = (int)(t0 - S.thread_off) + threadIdx.x;
-    const bool live = i < S.n;
-    const int vb = S.view_begin, ve = S.view_end;
-    for (int v = vb; v < ve; v++) {
-        const ViewDesc& V = a.views[v];
-        const long long o = V.rec_off + i;
-        Rec r;
-        ushort4 rc = make_ushort4(0, 0, 0, 0);
-        uint32_t off = 0, want = 0, mask = 0;
-        if (live) {
-            r = load_rec(a.geom, o);
-            rc = a.rect[o];
-            off = a.partitioned ? 0u : a.offsets[o];
-            want = a.counts[o];
-            mask = a.keep_mask[o];
-        } else {
-            r.r0 = r.r1 = r.r2 = r.r3 = r.r4 = r.r5 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const RecThread th = rec_thread(a);
+    const int i = th.i;
+    const ViewDesc& V = a.views[th.v];
+    const long long o = V.rec_off + i;
+    Rec r;
+    ushort4 rc = make_ushort4(0, 0, 0, 0);
+    uint32_t off = 0, want = 0, mask = 0;
+    if (th.live) {
+        r = load_rec(a.geom, o);
+        rc = a.rect[o];
+        off = a.partitioned ? 0u : a.offsets[o];
+        want = a.counts[o];
+        mask = a.keep_mask[o];
+    } else {
+        r.r0 = r.r1 = r.r2 = r.r3 = r.r4 = r.r5 = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const uint32_t got = tiles_pass<true>(a, V, th.v, th.live && want > 0, r, rc, off, want, (uint32_t)i, &mask);
+    if (th.live && got != want && !a.partitioned) {
+        // Preprocess and Duplicate disagree (cannot happen with the shared rounding of the
+        // decision arithmetic; kept as the paper's safety net, appendix B.4): pad with
+        // dummy keys that sort behind every tile.
+        for (uint32_t k = got; k < want; k++) {
+            const unsigned long long pos = (unsigned long long)off + k;
+            if (pos < a.capacity) { a.dup_keys[pos] = ~0ull; a.dup_vals[pos] = (uint32_t)i; }
         }
-        const uint32_t got = tiles_pass<true>(a, V, live && want > 0, r, rc, off, want, (uint32_t)i, &mask);
-        if (live && got != want && !a.partitioned) {
-            // Preprocess and Duplicate disagree (cannot happen with the shared rounding of the
-            // decision arithmetic; kept as the paper's safety net, appendix B.4): pad with
-            // dummy keys that sort behind every tile.
-            for (uint32_t k = got; k < want; k++) {
-                const unsigned long long pos = (unsigned long long)off + k;
-                if (pos < a.capacity) { a.dup_keys[pos] = ~0ull; a.dup_vals[pos] = (uint32_t)i; }
-            }
-            atomicOr(&a.status->error_bits, 2u);
-            atomicAdd(&a.status->mismatched, 1u);
-        }
+        atomicOr(&a.status->error_bits, 2u);
+        atomicAdd(&a.status->mismatched, 1u);
     }
 }
 
@@ -608,8 +636,8 @@ cudaError_t launch_tables_init(const ViewDesc* host_views, int nviews, ViewDesc*
 
 cudaError_t launch_preprocess(const PipeArgs& a, cudaStream_t s)
 {
-    if (a.threads == 0) return cudaSuccess;
-    k_preprocess<<<(unsigned)(a.threads / 256), 256, 0, s>>>(a);
+    if (a.rec_threads == 0) return cudaSuccess;
+    k_preprocess<<<(unsigned)(a.rec_threads / 128), 128, 0, s>>>(a);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -637,8 +665,8 @@ cudaError_t launch_scan_tiles(const PipeArgs& a, cudaStream_t s)
 
 cudaError_t launch_duplicate(const PipeArgs& a, cudaStream_t s)
 {
-    if (a.threads == 0) return cudaSuccess;
-    k_duplicate<<<(unsigned)(a.threads / 256), 256, 0, s>>>(a);
+    if (a.rec_threads == 0) return cudaSuccess;
+    k_duplicate<<<(unsigned)(a.rec_threads / 128), 128, 0, s>>>(a);
     note_launches(1);
     return cudaGetLastError();
 }

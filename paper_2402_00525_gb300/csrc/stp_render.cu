@@ -103,7 +103,12 @@ __device__ __forceinline__ void blend(const PipeArgs& a, const ViewDesc& V, Px<H
         float da = c.g0 * (col.x * s.T - (c.Cf0 - s.C0) * inv) + c.g1 * (col.y * s.T - (c.Cf1 - s.C1) * inv) +
                    c.g2 * (col.z * s.T - (c.Cf2 - s.C2) * inv) - c.gbg * c.Tf * inv;
         da += c.gz * (t * s.T - (c.Zf - s.Z) * inv);
-        const Rec r = load_rec(a.geom, ri);
+        // mean, conic and opacity (the depth factors r3..r5 only for a depth gradient below)
+        Rec r;
+        const float4* rp = a.geom + kRecFloat4 * ri;
+        r.r0 = __ldg(rp);
+        r.r1 = __ldg(rp + 1);
+        r.r2 = __ldg(rp + 2);
         float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f);
         float4 q1 = make_float4(0.f, 0.f, c.g0 * wgt, c.g1 * wgt);
         if (val < a.alpha_max) {
@@ -124,6 +129,9 @@ __device__ __forceinline__ void blend(const PipeArgs& a, const ViewDesc& V, Px<H
         atomicAdd(gg + 8, c.g2 * wgt);
         if (c.gz != 0.f) {
             // t = |d| N / D with a_k = m_k . d, N = sum a_k c_k, D = sum a_k^2 (record layout)
+            r.r3 = __ldg(rp + 3);
+            r.r4 = __ldg(rp + 4);
+            r.r5 = __ldg(rp + 5);
             const float u = c.u, w = c.w;
             const float m[3][3] = {{r.r3.x, r.r3.y, r.r3.z}, {r.r3.w, r.r4.x, r.r4.y}, {r.r4.z, r.r4.w, r.r5.x}};
             const float cc[3] = {r.r2.y, r.r2.z, r.r2.w};
