@@ -41,6 +41,30 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
+// Block shape of the hierarchical Render: a tile's eight warps (two subtiles each) are
+// independent, so a tile is split over 8 / kRenderWarps blocks. The kernel is latency bound at
+// low occupancy, so each instantiation is given the resident-block count (register cap) that
+// measured fastest on 16 Full-HD views of 3M Gaussians with 4-warp blocks: HEAD <= 4 forward
+// 6 blocks (80 registers, 32.8 ms against 37.6 ms at 111 registers and 2 x 8-warp blocks),
+// backward 5 (96 registers, 54.8 ms against 59.8 ms); wider heads hold more registers.
+// Build-time knobs: -DSTP_RENDER_WARPS=..., -DSTP_RENDER_MIN_BLOCKS=... (all instantiations).
+#ifndef STP_RENDER_WARPS
+#define STP_RENDER_WARPS 4
+#endif
+constexpr int kRenderWarps = STP_RENDER_WARPS;
+constexpr int kBlocksPerTile = 8 / kRenderWarps;
+static_assert(kRenderWarps == 1 || kRenderWarps == 2 || kRenderWarps == 4 || kRenderWarps == 8, "warps per block");
+
+template <int HEAD, bool BWD>
+constexpr int render_min_blocks()
+{
+#ifdef STP_RENDER_MIN_BLOCKS
+    return STP_RENDER_MIN_BLOCKS;
+#else
+    return (HEAD <= 4 ? (BWD ? 5 : 6) : HEAD <= 8 ? 4 : 2) * 4 / kRenderWarps;
+#endif
+}
+
 __device__ __forceinline__ uint32_t depth_key(float t)
 {
     const uint32_t k = fkey(t);
@@ -362,17 +386,18 @@ __device__ __forceinline__ void merge_tail(const uint2* src, int ne, const uint2
 }
 
 template <int HEAD, bool BWD>
-__global__ void __launch_bounds__(256) k_render(PipeArgs a)
+__global__ void __launch_bounds__(32 * kRenderWarps, (render_min_blocks<HEAD, BWD>())) k_render(PipeArgs a)
 {
     extern __shared__ uint2 sm[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int warp = (int)(blockIdx.x % kBlocksPerTile) * kRenderWarps + wib;   // warp of the tile
     const int TAIL = a.tail, MID = a.mid;
-    uint2* tailb = sm + warp * (4 * TAIL + 64 + 8 * MID);
+    uint2* tailb = sm + wib * (4 * TAIL + 64 + 8 * MID);
     uint2* stage = tailb + 4 * TAIL;
     uint2* midb = stage + 64;
     if (a.status->error_bits & 1u) return;
 
-    const int gtile = blockIdx.x;
+    const int gtile = (int)(blockIdx.x / kBlocksPerTile);
     int lo = 0, hi = a.nviews - 1;
     while (lo < hi) {
         const int m = (lo + hi + 1) >> 1;
@@ -561,11 +586,11 @@ cudaError_t launch_head(const PipeArgs& a, bool bwd, size_t smem, cudaStream_t s
     cudaError_t e;
     if (bwd) {
         if ((e = ensure_smem_limit(k_render<HEAD, true>, smem, set_bwd, 64)) != cudaSuccess) return e;
-        k_render<HEAD, true><<<a.total_tiles, 256, smem, s>>>(a);
+        k_render<HEAD, true><<<a.total_tiles * kBlocksPerTile, 32 * kRenderWarps, smem, s>>>(a);
         note_launches(1);
     } else {
         if ((e = ensure_smem_limit(k_render<HEAD, false>, smem, set_fwd, 64)) != cudaSuccess) return e;
-        k_render<HEAD, false><<<a.total_tiles, 256, smem, s>>>(a);
+        k_render<HEAD, false><<<a.total_tiles * kBlocksPerTile, 32 * kRenderWarps, smem, s>>>(a);
         note_launches(1);
     }
     return cudaGetLastError();
@@ -762,7 +787,7 @@ cudaError_t launch_flat(const PipeArgs& a, cudaStream_t s)
 
 }  // namespace
 
-size_t render_smem_bytes(int tail, int mid) { return (size_t)8 * (4 * tail + 64 + 8 * mid) * sizeof(uint2); }
+size_t render_smem_bytes(int tail, int mid) { return (size_t)kRenderWarps * (4 * tail + 64 + 8 * mid) * sizeof(uint2); }
 
 bool render_head_supported(int head) { return head == 1 || head == 2 || head == 4 || head == 8 || head == 16; }
 
