@@ -203,11 +203,11 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // ---------------------------------------------------------------- partitioned per-tile sort
 // Appendix B.3's alternative to the global sort: Preprocess counted the entries of every tile
 // with atomics, a scan gave each tile its range, and Duplicate placed (depth << 32 | id) words
-// into the ranges through atomic cursors. One block per tile now sorts its range by depth
-// with four stable 8-bit passes and orders equal depths by Gaussian id, which reproduces the
-// stable global sort exactly (ties by id), independently of the atomic placement order.
-// Ranges of at most kSegCap entries are sorted in shared memory; longer ones in place in global
-// memory (the second buffer of the range serves as the ping-pong partner).
+// into the ranges through atomic cursors. One block per tile now sorts its range by (depth,
+// id), which reproduces the stable global sort exactly (ties by id), independently of the
+// atomic placement order: ranges of at most kSegCap entries by the bucket-and-rank scheme of
+// k_tile_sort in shared memory, longer ones (and badly skewed ones) with four stable 8-bit
+// passes in place in global memory (the second buffer of the range is the ping-pong partner).
 constexpr int kSegThreads = 256, kSegWarps = kSegThreads / 32, kSegCap = 4096;
 
 __device__ __forceinline__ uint32_t seg_digit(unsigned long long x, int shift)
@@ -302,11 +302,120 @@ __device__ void seg_fix_ties(unsigned long long* x, int n)
     __syncthreads();
 }
 
+// Per-tile sort by (depth, id), exact. The (depth, id) words of a tile are distinct, so no
+// pass needs to be stable: the tile's depth range is split into NB equal key intervals (one
+// shared-memory atomic histogram), the words are scattered into their buckets, and each word's
+// place inside its bucket is the number of smaller words there. Buckets hold a few words on
+// average. Ranges of at most kSegCap words work in shared memory (1024 buckets); longer ones
+// scatter into the range's partner buffer in global memory (4096 buckets). A range whose
+// fullest bucket exceeds kBucketMax takes four stable 8-bit radix passes in global memory.
+constexpr int kBucketsSmall = 1024, kBucketsLarge = 4096, kBucketMax = 512;
+
+template <int NB>
+__device__ __forceinline__ uint32_t bucket_of(uint32_t d, uint32_t kmin, unsigned long long span)
+{
+    return (uint32_t)(((unsigned long long)(d - kmin) * NB) / span);
+}
+
+// Histogram + scan of the bucket counts; returns false (nothing written) if a bucket is too
+// full. On success bcur[b] holds the start of bucket b.
+template <int NB>
+__device__ bool bucket_plan(const unsigned long long* src, uint32_t n, uint32_t* bcnt, uint32_t* bcur,
+                            uint32_t* red, uint32_t& kmin, unsigned long long& span)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t lo = 0xFFFFFFFFu, hi = 0u;
+    for (uint32_t i = threadIdx.x; i < n; i += kSegThreads) {
+        const uint32_t d = (uint32_t)(src[i] >> 32);
+        lo = min(lo, d);
+        hi = max(hi, d);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(kFull, lo, o));
+        hi = max(hi, __shfl_xor_sync(kFull, hi, o));
+    }
+    if (lane == 0) {
+        red[warp] = lo;
+        red[kSegWarps + warp] = hi;
+    }
+    for (int k = threadIdx.x; k < NB; k += kSegThreads) bcnt[k] = 0;
+    __syncthreads();
+    lo = red[0];
+    hi = red[kSegWarps];
+    for (int w = 1; w < kSegWarps; w++) {
+        lo = min(lo, red[w]);
+        hi = max(hi, red[kSegWarps + w]);
+    }
+    kmin = lo;
+    span = (unsigned long long)(hi - lo) + 1ull;
+    for (uint32_t i = threadIdx.x; i < n; i += kSegThreads)
+        atomicAdd(&bcnt[bucket_of<NB>((uint32_t)(src[i] >> 32), kmin, span)], 1u);
+    __syncthreads();
+    // exclusive scan of the counts: thread j owns buckets kPer*j .. kPer*j + kPer - 1
+    constexpr int kPer = NB / kSegThreads;
+    uint32_t c[kPer], sum = 0, mx = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; k++) {
+        c[k] = bcnt[threadIdx.x * kPer + k];
+        sum += c[k];
+        mx = max(mx, c[k]);
+    }
+    uint32_t inc = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += y;
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+    __syncthreads();                      // red[] is reused
+    if (lane == 31) red[warp] = inc;
+    if (lane == 0) red[2 * kSegWarps + warp] = mx;
+    __syncthreads();
+    uint32_t base = inc - sum, fullest = 0;
+    for (int w = 0; w < kSegWarps; w++) {
+        if (w < warp) base += red[w];
+        fullest = max(fullest, red[2 * kSegWarps + w]);
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; k++) {
+        bcur[threadIdx.x * kPer + k] = base;
+        base += c[k];
+    }
+    __syncthreads();
+    return fullest <= (uint32_t)kBucketMax;
+}
+
+// Scatter src into its buckets in `scat`, then rank each word inside its bucket. With `keys`
+// set, the ranked words go straight to the output pair arrays; otherwise to ranked[].
+template <int NB>
+__device__ void bucket_rank(const unsigned long long* src, unsigned long long* scat, uint32_t n,
+                            const uint32_t* bcnt, uint32_t* bcur, uint32_t kmin, unsigned long long span,
+                            unsigned long long hi, uint64_t* keys, uint32_t* vals, unsigned long long* ranked)
+{
+    for (uint32_t i = threadIdx.x; i < n; i += kSegThreads) {
+        const unsigned long long x = src[i];
+        scat[atomicAdd(&bcur[bucket_of<NB>((uint32_t)(x >> 32), kmin, span)], 1u)] = x;
+    }
+    __syncthreads();
+    // bcur[b] is now the end of bucket b
+    for (uint32_t i = threadIdx.x; i < n; i += kSegThreads) {
+        const unsigned long long x = scat[i];
+        const uint32_t b = bucket_of<NB>((uint32_t)(x >> 32), kmin, span);
+        const uint32_t end = bcur[b], beg = end - bcnt[b];
+        uint32_t r = beg;
+        for (uint32_t j = beg; j < end; j++) r += scat[j] < x;
+        if (keys) {
+            keys[r] = hi | (x >> 32);
+            vals[r] = (uint32_t)x;
+        } else {
+            ranked[r] = x;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kSegThreads) k_tile_sort(PipeArgs a)
 {
-    extern __shared__ unsigned long long seg_smem[];
-    __shared__ uint32_t whist[kSegWarps][kRadix];
-    __shared__ uint32_t dtot[kRadix];
+    extern __shared__ unsigned long long seg_smem[];               // [kSegCap] words + counters
+    __shared__ uint32_t red[3 * kSegWarps];
     const int t = blockIdx.x;
     if (a.status->error_bits & 1u) {
         if (threadIdx.x == 0) a.ranges[t] = make_uint2(0u, 0u);
@@ -319,22 +428,39 @@ __global__ void __launch_bounds__(kSegThreads) k_tile_sort(PipeArgs a)
     if (n == 0) return;
     unsigned long long* g0 = (unsigned long long*)a.dup_keys + off;   // placed words (buffer A)
     unsigned long long* g1 = (unsigned long long*)a.keys + off;   // partner (buffer B)
-    unsigned long long* x;
-    if (n <= (uint32_t)kSegCap) {
-        unsigned long long* s0 = seg_smem;
-        unsigned long long* s1 = seg_smem + kSegCap;
-        for (uint32_t i = threadIdx.x; i < n; i += kSegThreads) s0[i] = g0[i];
-        __syncthreads();
-        for (int p = 0; p < 4; p++) seg_pass(p % 2 ? s1 : s0, p % 2 ? s0 : s1, (int)n, 8 * p, whist, dtot);
-        x = s0;
-    } else {
-        for (int p = 0; p < 4; p++) seg_pass(p % 2 ? g1 : g0, p % 2 ? g0 : g1, (int)n, 8 * p, whist, dtot);
-        x = g0;
-    }
-    seg_fix_ties(x, (int)n);
     const unsigned long long hi = (unsigned long long)t << 32;
+    uint32_t kmin;
+    unsigned long long span;
+    if (n <= (uint32_t)kSegCap) {
+        uint32_t* bcnt = reinterpret_cast<uint32_t*>(seg_smem + kSegCap);
+        uint32_t* bcur = bcnt + kBucketsSmall;
+        if (bucket_plan<kBucketsSmall>(g0, n, bcnt, bcur, red, kmin, span)) {
+            bucket_rank<kBucketsSmall>(g0, seg_smem, n, bcnt, bcur, kmin, span, hi, a.keys + off, a.vals + off, nullptr);
+            return;
+        }
+    } else {
+        uint32_t* bcnt = reinterpret_cast<uint32_t*>(seg_smem);      // 2 x 4096 counters
+        uint32_t* bcur = bcnt + kBucketsLarge;
+        if (bucket_plan<kBucketsLarge>(g0, n, bcnt, bcur, red, kmin, span)) {
+            // scatter into the partner range, rank back into the placed range, then write out
+            bucket_rank<kBucketsLarge>(g0, g1, n, bcnt, bcur, kmin, span, hi, nullptr, nullptr, g0);
+            __syncthreads();
+            for (uint32_t i = threadIdx.x; i < n; i += kSegThreads) {
+                const unsigned long long v = g0[i];
+                a.keys[off + i] = hi | (v >> 32);
+                a.vals[off + i] = (uint32_t)v;
+            }
+            return;
+        }
+    }
+    __syncthreads();                      // shared memory is reused by the radix passes
+    // four stable 8-bit passes in global memory, then ties ordered by id
+    uint32_t (*whist)[kRadix] = reinterpret_cast<uint32_t (*)[kRadix]>(seg_smem);
+    uint32_t* dtot = reinterpret_cast<uint32_t*>(seg_smem) + kSegWarps * kRadix;
+    for (int p = 0; p < 4; p++) seg_pass(p % 2 ? g1 : g0, p % 2 ? g0 : g1, (int)n, 8 * p, whist, dtot);
+    seg_fix_ties(g0, (int)n);
     for (uint32_t i = threadIdx.x; i < n; i += kSegThreads) {
-        const unsigned long long v = x[i];
+        const unsigned long long v = g0[i];
         a.keys[off + i] = hi | (v >> 32);
         a.vals[off + i] = (uint32_t)v;
     }
@@ -469,7 +595,7 @@ cudaError_t pipeline_sort(const PipeArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-size_t tile_sort_smem_bytes() { return (size_t)2 * kSegCap * sizeof(unsigned long long); }
+size_t tile_sort_smem_bytes() { return (size_t)kSegCap * sizeof(unsigned long long) + 2 * kBucketsSmall * sizeof(uint32_t); }
 
 cudaError_t launch_tile_sort(const PipeArgs& a, cudaStream_t s)
 {

@@ -292,3 +292,38 @@ def test_partitioned_sort_equals_global_radix_sort():
     assert big > 4096          # at least one tile took the long-range (global memory) path
     for k in range(len(cams)):
         assert np.array_equal(a["rgb"][k], b["rgb"][k]) and np.array_equal(a["hash"][k], b["hash"][k])
+
+
+def _skewed_scene(n_near, seed):
+    """n_near small Gaussians within one tile at almost the same depth, plus a few large ones
+    far behind: the tile's depth range is wide but nearly all keys fall in one narrow band."""
+    rng = np.random.default_rng(seed)
+    near = np.stack([rng.uniform(-0.02, 0.02, n_near), rng.uniform(-0.02, 0.02, n_near),
+                     5.0 + rng.uniform(-1e-4, 1e-4, n_near)], 1)
+    far = np.array([[0.0, 0.0, 60.0], [0.5, 0.3, 45.0], [-0.4, 0.2, 80.0]])
+    means = np.concatenate([near, far])
+    n = len(means)
+    log_scales = np.concatenate([np.full((n_near, 3), np.log(0.004)), np.full((3, 3), np.log(3.0))])
+    quats = np.tile([1.0, 0.0, 0.0, 0.0], (n, 1))
+    logits = np.full(n, 2.0)
+    sh = rng.uniform(-1.0, 1.0, (n, 1, 3))
+    return I.Scene(means=means, log_scales=log_scales, quats=quats, opacity_logits=logits, sh=sh, sh_degree=0)
+
+
+@pytest.mark.parametrize("n_near", [1500, 6000])
+def test_per_tile_sort_falls_back_on_skewed_depths(n_near):
+    """A tile whose keys crowd into one bucket (and, with 6000, one that is also longer than the
+    shared-memory capacity) takes the radix fallback of the per-tile sort; lists and images stay
+    identical to the global radix sort."""
+    sc = _skewed_scene(n_near, 90 + n_near)
+    cam = I.look_at((0, 0, 0), (0, 0, 5), (0, 1, 0), 64, 64, 40.0)
+    prm = I.RenderParams()
+    a = gpu_render(sc, [cam], prm)
+    b = gpu_render(sc, [cam], dataclasses.replace(prm, flags=I.FLAG_GLOBAL_SORT))
+    ra, ka, va = [x.cpu().numpy() for x in a["renderer"].sorted_lists()]
+    rb, kb, vb = [x.cpu().numpy() for x in b["renderer"].sorted_lists()]
+    na = np.diff(ra, axis=1)[:, 0]
+    assert na.max() >= n_near // 2          # the crowded tile holds most of the near Gaussians
+    assert np.array_equal(na, np.diff(rb, axis=1)[:, 0])
+    assert np.array_equal(ka, kb) and np.array_equal(va, vb)
+    assert np.array_equal(a["rgb"][0], b["rgb"][0]) and np.array_equal(a["hash"][0], b["hash"][0])
