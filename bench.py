@@ -49,6 +49,26 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def shard_views(all_cams, rank: int, world: int):
+    """Views are independent: rank r renders views r, r + world, ... (no data-path collective)."""
+    return list(all_cams)[rank::world]
+
+
+def max_over_ranks(values, dist=None, device="cpu"):
+    """Element-wise maximum of per-rank timings (the job is as slow as its slowest rank)."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def job_mpix_per_s(pixels_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job throughput: the pixels of all ranks over the slowest rank's time."""
+    return pixels_per_rank * world / (ms * 1e-3) / 1e6
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -115,7 +135,7 @@ def run_reference(args, rank, world):
         return
     from oracle import build as OB
     OB.build()
-    scene, cams, prm = I.full_hd_workload()
+    scene, cams, prm = I.full_hd_workload(n=args.n)
     ntiles = 24
     for w in range(args.warmup):
         oracle_sample(scene, cams[w % len(cams)], prm, ntiles, 100 + w)
@@ -269,7 +289,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="stp", choices=["stp", "reference"])
-    ap.add_argument("--n", type=int, default=3_000_000, help="Gaussians (default: the workload's 3M)")
+    ap.add_argument("--gaussians", dest="n", type=int, default=3_000_000, help="Gaussians (default: the workload's 3M)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--per-view-rounds", type=int, default=2)
     ap.add_argument("--no-extra", action="store_true", help="skip the 64-view and 8-scene legs")
@@ -296,7 +316,7 @@ def main():
 
     scene, _, prm = I.full_hd_workload(n=args.n, nviews=1)
     all_cams = I.orbit_cameras(16 * world, 15.0, 2.0, I.C2_SIZES, 50.0)
-    cams = all_cams[rank::world]
+    cams = shard_views(all_cams, rank, world)
     V = len(cams)
     P = sum(c.num_pixels for c in cams)
     g = R.scene_to_device(scene)
@@ -346,12 +366,9 @@ def main():
     assert st.error_bits == 0, "status %d after the timed region" % st.error_bits
     fwd_stage = stages[0::2].mean(0)
     bwd_stage = stages[1::2].mean(0)
-    if dist:
-        t = torch.tensor([fwd_ms, step_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        fwd_ms, step_ms = float(t[0]), float(t[1])
+    fwd_ms, step_ms = max_over_ranks([fwd_ms, step_ms], dist, "cuda")
     total_px = P * world
-    value = total_px / (fwd_ms * 1e-3) / 1e6
+    value = job_mpix_per_s(P, world, fwd_ms)
 
     # ---------------------------------------------------------------- per-view launches
     single = [R.Renderer(scene.n, [c], prm) for c in cams]
@@ -394,8 +411,8 @@ def main():
         torch.cuda.synchronize()
         if it:
             e2e_ms.append(e0.elapsed_time(e1))
-    e2e_ms = float(np.mean(e2e_ms))
-    e2e_val = total_px / (e2e_ms * 1e-3) / 1e6
+    e2e_ms = max_over_ranks([float(np.mean(e2e_ms))], dist, "cuda")[0]
+    e2e_val = job_mpix_per_s(P, world, e2e_ms)
 
     # ---------------------------------------------------------------- work counters (untimed)
     dbg = R.Renderer(scene.n, cams, prm, debug=True, capacity=rnd.capacity)
