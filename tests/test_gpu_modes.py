@@ -69,3 +69,35 @@ def test_backward_of_a_comparison_order_is_rejected():
     with pytest.raises(N.StpError) as e:
         r.backward(g, torch.zeros((cams[0].num_pixels, 3), device="cuda"), None, grads)
     assert e.value.code == N.STP_ERR_NOT_SUPPORTED
+
+
+@pytest.mark.parametrize("flags", [I.FLAG_HEAD_EVICT_FIRST, I.FLAG_LEVEL_CENTRE_RAYS, I.FLAG_VIEW_DEPTH_KEY,
+                                   I.FLAG_NO_TILE_CULL, I.FLAG_NO_HIER_CULL])
+def test_backward_under_readings_and_ablations_matches_adjoint(oracle, flags):
+    """The backward replay follows whatever order the forward took: under each reading / ablation
+    switch its gradients match the FP64 adjoint of the oracle run with the same switch (colour
+    and depth losses, weights zero on undecided pixels)."""
+    sc, _, cam, prm = I.fd_subcase()
+    prm = dataclasses.replace(prm, flags=flags)
+    rng = np.random.default_rng(40 + flags)
+    with oracle.OracleRun(sc, cam, prm, record=True) as r:
+        ora = r.render()
+        w = rng.normal(size=(cam.height, cam.width, 3)) / cam.num_pixels
+        wz = rng.normal(size=(cam.height, cam.width)) / cam.num_pixels * 0.1
+        w[~ora["decided"]] = 0
+        wz[~ora["decided"]] = 0
+        adj = r.backward(w, wz)
+    g = R.scene_to_device(sc)
+    rr = R.Renderer(sc.n, [cam], prm, backward=True, debug=True)
+    rr.forward(g)
+    grads = {k: torch.zeros_like(g[k]) for k in R.FIELDS}
+    rr.backward(g, torch.from_numpy(w.reshape(-1, 3).astype(np.float32)).cuda(),
+                torch.from_numpy(wz.reshape(-1).astype(np.float32)).cuda(), grads)
+    torch.cuda.synchronize()
+    assert rr.status().error_bits == 0
+    for k in R.FIELDS:
+        a = grads[k].cpu().numpy().astype(np.float64).ravel()
+        b = adj[k].ravel()
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        cos = a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30)
+        assert rel <= 1e-3 and cos >= 0.9999, (k, rel, cos)
