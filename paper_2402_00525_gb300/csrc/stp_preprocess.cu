@@ -178,13 +178,22 @@ __device__ bool make_record(const PipeArgs& a, const ViewDesc& V, const GaussIn&
     float rgb[3];
     sh_colour(g.sh, g.sh_k, d[0] * dl, d[1] * dl, d[2] * dl, rgb);
     col = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
-    // opacity-aware radius (appendix B.2) and the rectangle of tiles holding a pixel centre
-    // within [mean2 - r, mean2 + r]
+    // Candidate tiles. With the opacity-aware radius of appendix B.2, o G >= eps_O holds only on
+    // the ellipse (x - mean2)^T A (x - mean2) <= t_O^2, whose axis-aligned half-widths are
+    // t_O sqrt(Sigma2_xx) and t_O sqrt(Sigma2_yy) -- never more than the paper's square radius
+    // ceil(t_O sqrt(lambda_max)), often far less for anisotropic splats. Every tile this box
+    // drops would fail Algorithm 1's test, so the kept entries are the same; only fewer tiles
+    // are tested. The box takes the tiles holding a pixel centre within it (small slack for
+    // rounding). Without tile-based culling (ablation D) every tile of the paper's square is kept,
+    // so that case keeps the square.
     const float tO = sqrtf(2.f * logf(g.opacity / a.eps_o));
     const float rad = ceilf(tO * sqrtf(lmax));
+    const bool square = (a.flags & kFlagNoTileCull) != 0;
+    const float hx = square ? rad : fminf(rad, fmaf(tO * sqrtf(ca), 1.0001f, 0.01f));
+    const float hy = square ? rad : fminf(rad, fmaf(tO * sqrtf(cc), 1.0001f, 0.01f));
     const float mx = (float)mxd, my = (float)myd;
-    const float fx0 = ceilf((mx - rad - 15.5f) * (1.f / 16.f)), fx1 = floorf((mx + rad - 0.5f) * (1.f / 16.f));
-    const float fy0 = ceilf((my - rad - 15.5f) * (1.f / 16.f)), fy1 = floorf((my + rad - 0.5f) * (1.f / 16.f));
+    const float fx0 = ceilf((mx - hx - 15.5f) * (1.f / 16.f)), fx1 = floorf((mx + hx - 0.5f) * (1.f / 16.f));
+    const float fy0 = ceilf((my - hy - 15.5f) * (1.f / 16.f)), fy1 = floorf((my + hy - 0.5f) * (1.f / 16.f));
     const int tx0 = (int)fmaxf(0.f, fx0), ty0 = (int)fmaxf(0.f, fy0);
     const int tx1 = (int)fminf((float)(V.tiles_x - 1), fx1), ty1 = (int)fminf((float)(V.tiles_y - 1), fy1);
     if (tx1 >= tx0 && ty1 >= ty0)

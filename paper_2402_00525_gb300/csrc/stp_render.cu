@@ -47,7 +47,8 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 // measured fastest on 16 Full-HD views of 3M Gaussians with 4-warp blocks: HEAD <= 4 forward
 // 6 blocks (80 registers, 32.8 ms against 37.6 ms at 111 registers and 2 x 8-warp blocks),
 // backward 5 (96 registers, 54.8 ms against 59.8 ms); wider heads hold more registers.
-// Build-time knobs: -DSTP_RENDER_WARPS=..., -DSTP_RENDER_MIN_BLOCKS=... (all instantiations).
+// Build-time knobs: -DSTP_RENDER_WARPS=..., -DSTP_RENDER_MIN_BLOCKS_FWD / _BWD=... (HEAD <= 4),
+// -DSTP_RENDER_MIN_BLOCKS=... (all instantiations).
 #ifndef STP_RENDER_WARPS
 #define STP_RENDER_WARPS 4
 #endif
@@ -55,13 +56,19 @@ constexpr int kRenderWarps = STP_RENDER_WARPS;
 constexpr int kBlocksPerTile = 8 / kRenderWarps;
 static_assert(kRenderWarps == 1 || kRenderWarps == 2 || kRenderWarps == 4 || kRenderWarps == 8, "warps per block");
 
+#ifndef STP_RENDER_MIN_BLOCKS_FWD
+#define STP_RENDER_MIN_BLOCKS_FWD 6
+#endif
+#ifndef STP_RENDER_MIN_BLOCKS_BWD
+#define STP_RENDER_MIN_BLOCKS_BWD 5
+#endif
 template <int HEAD, bool BWD>
 constexpr int render_min_blocks()
 {
 #ifdef STP_RENDER_MIN_BLOCKS
     return STP_RENDER_MIN_BLOCKS;
 #else
-    return (HEAD <= 4 ? (BWD ? 5 : 6) : HEAD <= 8 ? 4 : 2) * 4 / kRenderWarps;
+    return (HEAD <= 4 ? (BWD ? STP_RENDER_MIN_BLOCKS_BWD : STP_RENDER_MIN_BLOCKS_FWD) : HEAD <= 8 ? 4 : 2) * 4 / kRenderWarps;
 #endif
 }
 

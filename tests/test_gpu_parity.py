@@ -87,10 +87,27 @@ def test_preprocess_records_match_oracle(oracle):
     t_ora = np.einsum("ni,ni->n", dw, pp["v"][v]) / np.einsum("ni,nij,nj->n", dw, Sw, dw)
     assert np.allclose(t_gpu, t_ora, rtol=2e-6)
     assert np.allclose(g[:, 21], pp["pcam"][v][:, 2], rtol=1e-6)
+    # candidate tiles: the GPU tests the tiles of the ellipse o G >= eps_O's axis-aligned box
+    # (never more than the paper's square rectangle, which the oracle uses); the kept counts agree
     rr = rect[0][v].astype(np.int64)
     orc = pp["rect"][v]
-    same_rect = (rr[:, 0] == orc[:, 0]) & (rr[:, 1] == orc[:, 1]) & (rr[:, 2] == orc[:, 2] + 1) & (rr[:, 3] == orc[:, 3] + 1)
-    assert same_rect.mean() > 0.999
+    inside_square = ((rr[:, 0] >= orc[:, 0]) & (rr[:, 1] >= orc[:, 1]) & (rr[:, 2] <= orc[:, 2] + 1)
+                     & (rr[:, 3] <= orc[:, 3] + 1)) | (rr[:, 2] <= rr[:, 0])
+    assert inside_square.mean() > 0.999
+    A = pp["conic"][v]
+    dA = A[:, 0] * A[:, 2] - A[:, 1] ** 2
+    tO = np.sqrt(2 * np.log(pp["opacity"][v] / prm.eps_o))
+    hx, hy = tO * np.sqrt(A[:, 2] / dA), tO * np.sqrt(A[:, 0] / dA)
+    mx, my = pp["mean2"][v][:, 0], pp["mean2"][v][:, 1]
+    ex0 = np.maximum(0, np.ceil((mx - hx - 15.5) / 16)).astype(np.int64)
+    ex1 = np.minimum(cam.tiles_x - 1, np.floor((mx + hx - 0.5) / 16)).astype(np.int64)
+    ey0 = np.maximum(0, np.ceil((my - hy - 15.5) / 16)).astype(np.int64)
+    ey1 = np.minimum(cam.tiles_y - 1, np.floor((my + hy - 0.5) / 16)).astype(np.int64)
+    live = (ex1 >= ex0) & (ey1 >= ey0) & (pp["margin"][v] > 1e-4)
+    covers = (rr[:, 0] <= ex0) & (rr[:, 1] <= ey0) & (rr[:, 2] >= ex1 + 1) & (rr[:, 3] >= ey1 + 1)
+    assert covers[live].all()
+    assert (((rr[:, 2] - rr[:, 0]) * (rr[:, 3] - rr[:, 1]))[live].sum()
+            <= ((orc[:, 2] - orc[:, 0] + 1) * (orc[:, 3] - orc[:, 1] + 1))[live].sum())
     same_cnt = counts[0][v] == pp["ntiles"][v]
     assert same_cnt.mean() > 0.999
     assert gpu["renderer"].status().mismatched == 0
