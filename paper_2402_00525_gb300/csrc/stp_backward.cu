@@ -137,8 +137,8 @@ __global__ void __launch_bounds__(128) k_backward_pre(PipeArgs a)
         }
         const float dd = ddir[0] * dir[0] + ddir[1] * dir[1] + ddir[2] * dir[2];
         for (int k = 0; k < 3; k++) dmu[k] += (ddir[k] - dd * dir[k]) / dl;
-        // opacity -> logit
-        dlogit += g[5] * opac * (1.f - opac);
+        // opacity -> logit (the scratch holds sum dGG = opacity * dL/dopacity)
+        dlogit += g[5] * (1.f - opac);
         // projection quantities
         const float iz = 1.f / p[2];
         const float ux = p[0] * iz, uy = p[1] * iz;
@@ -190,10 +190,11 @@ __global__ void __launch_bounds__(128) k_backward_pre(PipeArgs a)
         else dp[2] += Jb[0][2] * (V.fx * cx * iz2);
         if (!cly) { dp[1] += Jb[1][2] * (-V.fy * iz2); dp[2] += Jb[1][2] * (2.f * V.fy * p[1] * iz2 * iz); }
         else dp[2] += Jb[1][2] * (V.fy * cy * iz2);
-        // mean2
-        dp[0] += g[0] * V.fx * iz;
-        dp[1] += g[1] * V.fy * iz;
-        dp[2] -= (g[0] * V.fx * p[0] + g[1] * V.fy * p[1]) * iz2;
+        // mean2 (the scratch holds sum dGG (x - mean2); dL/dmean2 = A of it)
+        const float gm0 = A[0][0] * g[0] + A[0][1] * g[1], gm1 = A[1][0] * g[0] + A[1][1] * g[1];
+        dp[0] += gm0 * V.fx * iz;
+        dp[1] += gm1 * V.fy * iz;
+        dp[2] -= (gm0 * V.fx * p[0] + gm1 * V.fy * p[1]) * iz2;
         // depth factors: m_k = si_k R_c Rq e_k, c_k = m_k . p
         bool depth_nz = false;
         for (int k = 12; k < 24; k++) depth_nz |= g[k] != 0.f;

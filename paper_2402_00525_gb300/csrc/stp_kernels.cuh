@@ -90,7 +90,7 @@ __device__ __forceinline__ int scene_of_rec(const PipeArgs& a, long long t0)
 }
 
 constexpr int kTraceLen = 64;
-constexpr int kGradStride = 24;   // dmean2(2) dconic(3) dopacity(1) dcolour(3) pad(3) dm(9) dc(3)
+constexpr int kGradStride = 24;   // sum dGG d(2) dconic(3) sum dGG(1) dcolour(3) pad(3) dm(9) dc(3)
 
 cudaError_t launch_tables_init(const ViewDesc* host_views, int nviews, ViewDesc* dev_views,
                                const SceneDesc* host_scenes, int nscenes, SceneDesc* dev_scenes,

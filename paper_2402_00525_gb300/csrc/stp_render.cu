@@ -126,41 +126,38 @@ __device__ __forceinline__ void blend(const PipeArgs& a, const ViewDesc& V, Px<H
     s.C2 += col.z * wgt;
     s.Z += t * wgt;
     if (BWD) {
-        // per-(view, Gaussian) scratch, 24 floats: [0..7] (dmean2.xy, dA00, dA01, dA11,
-        // dopacity, dcolour.rg), [8] dcolour.b, [12..23] depth factors (dm_k 9, dc_k 3);
+        // per-(view, Gaussian) scratch, 24 floats: [0..7] (sum dGG d.xy, dA00, dA01, dA11,
+        // sum dGG, dcolour.rg), [8] dcolour.b, [12..23] depth factors (dm_k 9, dc_k 3);
         // accumulated with vector reductions (red.global.add.v4.f32)
         float* gg = a.grad_geom + ri * kGradStride;
         const float inv = __fdividef(1.f, 1.f - alpha);     // 1 - alpha >= 1 - alpha_max > 0
         float da = c.g0 * (col.x * s.T - (c.Cf0 - s.C0) * inv) + c.g1 * (col.y * s.T - (c.Cf1 - s.C1) * inv) +
                    c.g2 * (col.z * s.T - (c.Cf2 - s.C2) * inv) - c.gbg * c.Tf * inv;
         da += c.gz * (t * s.T - (c.Zf - s.Z) * inv);
-        // mean, conic and opacity (the depth factors r3..r5 only for a depth gradient below)
+        // the projected mean (the depth factors r2..r5 only for a depth gradient below)
         Rec r;
         const float4* rp = a.geom + kRecFloat4 * ri;
         r.r0 = __ldg(rp);
-        r.r1 = __ldg(rp + 1);
-        r.r2 = __ldg(rp + 2);
         float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f);
         float4 q1 = make_float4(0.f, 0.f, c.g0 * wgt, c.g1 * wgt);
         if (val < a.alpha_max) {
-            // val = opacity * G at this pixel (computed when the entry reached the pixel), so
-            // d/d(opacity) = da G = da val / opacity and the conic / mean terms scale da val
+            // val = opacity * G at this pixel, so with dGG = da * val: dL/dopacity gets dGG /
+            // opacity, dL/dA gets -dGG d d^T / 2 and dL/dmean2 gets A dGG d (d = x - mean2).
+            // The factors A and 1 / opacity are the same for every pixel of this (view,
+            // Gaussian), so the scratch sums dGG d and dGG, and the backward Preprocess
+            // applies them once.
             const float dx = off_x(r, c.xc), dy = off_y(r, c.yc);
-            const float o = rec_opacity(r);
-            // conic entries (A00, A01, A11) from the eigen form
-            const float ex = r.r1.x, ey = r.r1.y, l0 = r.r1.z, l1 = r.r1.w;
-            const float A00 = l0 * ex * ex + l1 * ey * ey, A01 = (l0 - l1) * ex * ey, A11 = l0 * ey * ey + l1 * ex * ex;
             const float dGG = da * val;
-            q0 = make_float4(dGG * (A00 * dx + A01 * dy), dGG * (A01 * dx + A11 * dy), dGG * (-0.5f * dx * dx),
-                             dGG * (-dx * dy));
+            q0 = make_float4(dGG * dx, dGG * dy, dGG * (-0.5f * dx * dx), dGG * (-dx * dy));
             q1.x = dGG * (-0.5f * dy * dy);
-            q1.y = __fdividef(dGG, o);
+            q1.y = dGG;
         }
         atomicAdd(reinterpret_cast<float4*>(gg), q0);
         atomicAdd(reinterpret_cast<float4*>(gg + 4), q1);
         atomicAdd(gg + 8, c.g2 * wgt);
         if (c.gz != 0.f) {
             // t = |d| N / D with a_k = m_k . d, N = sum a_k c_k, D = sum a_k^2 (record layout)
+            r.r2 = __ldg(rp + 2);
             r.r3 = __ldg(rp + 3);
             r.r4 = __ldg(rp + 4);
             r.r5 = __ldg(rp + 5);
