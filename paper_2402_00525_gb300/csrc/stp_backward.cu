@@ -27,6 +27,7 @@ __device__ __forceinline__ void sh_basis_grad(float x, float y, float z, int K, 
     const float k2a = 1.0925484305920792f, k2b = 0.31539156525252005f, k2c = 0.5462742152960396f;
     const float k3a = 0.5900435899266435f, k3b = 2.890611442640554f, k3c = 0.4570457994644658f;
     const float k3d = 0.3731763325901154f, k3e = 1.445305721320277f;
+#pragma unroll
     for (int j = 0; j < 16; j++) { Y[j] = 0.f; dY[j][0] = dY[j][1] = dY[j][2] = 0.f; }
     Y[0] = k0;
     if (K > 1) {
@@ -60,7 +61,10 @@ __device__ __forceinline__ void sh_basis_grad(float x, float y, float z, int K, 
     }
 }
 
-__global__ void __launch_bounds__(128) k_backward_pre(PipeArgs a)
+#ifndef STP_BWDPRE_MIN_BLOCKS
+#define STP_BWDPRE_MIN_BLOCKS 3
+#endif
+__global__ void __launch_bounds__(128, STP_BWDPRE_MIN_BLOCKS) k_backward_pre(PipeArgs a)
 {
     const long long t0 = (long long)blockIdx.x * blockDim.x;
     const SceneDesc& S = a.scenes[scene_of(a, t0)];
@@ -97,6 +101,7 @@ __global__ void __launch_bounds__(128) k_backward_pre(PipeArgs a)
     float dSig[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
     float dsi[3] = {0.f, 0.f, 0.f};
     float dsh[48];
+#pragma unroll
     for (int k = 0; k < 48; k++) dsh[k] = 0.f;
     bool any = false;
 
@@ -104,13 +109,19 @@ __global__ void __launch_bounds__(128) k_backward_pre(PipeArgs a)
         const ViewDesc& V = a.views[v];
         const long long ri = V.rec_off + i;
         if (a.geom[kRecFloat4 * ri + 2].x == 0.f) continue;      // invisible in this view
-        const float* gg = a.grad_geom + ri * kGradStride;
+        const float4* gg = reinterpret_cast<const float4*>(a.grad_geom + ri * kGradStride);
         float g[24];
         bool nz = false;
-        for (int k = 0; k < 24; k++) {
-            g[k] = gg[k];
-            nz |= g[k] != 0.f;
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            const float4 q = gg[k];
+            g[4 * k] = q.x;
+            g[4 * k + 1] = q.y;
+            g[4 * k + 2] = q.z;
+            g[4 * k + 3] = q.w;
         }
+#pragma unroll
+        for (int k = 0; k < 24; k++) nz |= g[k] != 0.f;
         if (!nz) continue;
         any = true;
         float p[3];
@@ -122,17 +133,24 @@ __global__ void __launch_bounds__(128) k_backward_pre(PipeArgs a)
         float Y[16], dY[16][3];
         sh_basis_grad(dir[0], dir[1], dir[2], K, Y, dY);
         float ddir[3] = {0.f, 0.f, 0.f};
+        // static indices throughout (j < 16 unrolled, K tested inside), so the basis and the
+        // accumulators stay in registers instead of local memory
+#pragma unroll
         for (int ch = 0; ch < 3; ch++) {
             float raw = 0.5f;
-            for (int j = 0; j < K; j++) raw += Y[j] * shc[3 * j + ch];
+#pragma unroll
+            for (int j = 0; j < 16; j++)
+                if (j < K) raw += Y[j] * shc[3 * j + ch];
             const float dr = raw > 0.f ? g[6 + ch] : 0.f;
-            if (dr == 0.f) continue;
-            for (int j = 0; j < K; j++) {
-                dsh[3 * j + ch] += dr * Y[j];
-                const float cf = dr * shc[3 * j + ch];
-                ddir[0] += cf * dY[j][0];
-                ddir[1] += cf * dY[j][1];
-                ddir[2] += cf * dY[j][2];
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                if (j < K) {
+                    dsh[3 * j + ch] += dr * Y[j];
+                    const float cf = dr * shc[3 * j + ch];
+                    ddir[0] += cf * dY[j][0];
+                    ddir[1] += cf * dY[j][1];
+                    ddir[2] += cf * dY[j][2];
+                }
             }
         }
         const float dd = ddir[0] * dir[0] + ddir[1] * dir[1] + ddir[2] * dir[2];
@@ -247,7 +265,9 @@ __global__ void __launch_bounds__(128) k_backward_pre(PipeArgs a)
     }
     for (int k = 0; k < 4; k++) S.g_quats[4 * i + k] += (gq[k] - dot * qn[k]) / ql;
     S.g_logits[i] += dlogit;
-    for (int k = 0; k < 3 * K; k++) S.g_sh[(long long)i * K * 3 + k] += dsh[k];
+#pragma unroll
+    for (int k = 0; k < 48; k++)
+        if (k < 3 * K) S.g_sh[(long long)i * K * 3 + k] += dsh[k];
 }
 
 }  // namespace
