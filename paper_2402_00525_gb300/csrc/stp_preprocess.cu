@@ -53,10 +53,13 @@ __device__ __forceinline__ void sh_colour(const float* __restrict__ c, int K, fl
         }
     }
     float s0 = 0.5f, s1 = 0.5f, s2 = 0.5f;
-    for (int j = 0; j < K; j++) {
-        s0 += Y[j] * __ldg(c + 3 * j);
-        s1 += Y[j] * __ldg(c + 3 * j + 1);
-        s2 += Y[j] * __ldg(c + 3 * j + 2);
+#pragma unroll
+    for (int j = 0; j < 16; j++) {           // static indices: Y stays in registers
+        if (j < K) {
+            s0 += Y[j] * __ldg(c + 3 * j);
+            s1 += Y[j] * __ldg(c + 3 * j + 1);
+            s2 += Y[j] * __ldg(c + 3 * j + 2);
+        }
     }
     out[0] = fmaxf(s0, 0.f);
     out[1] = fmaxf(s1, 0.f);
@@ -435,11 +438,11 @@ __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, int vidx, b
 // One thread per (Gaussian, view), the scene's views fastest within a warp: lanes that share a
 // Gaussian see it from different cameras, so their tile counts are alike (little divergence).
 // 128-thread blocks (scenes start on 256-thread boundaries, so a block never straddles two),
-// twelve resident per SM: the 40-register cap spills to L1, but the occupancy hides the
-// latency of the tile-counter atomics (measured on 16 Full-HD views of 3M Gaussians: 11.6 /
-// 12.7 ms, against 12.0 / 13.5 ms with eight blocks and 13.5 / 17.0 ms at 80 / 91 registers).
+// ten (Preprocess) and twelve (Duplicate) resident per SM: the register caps spill to L1, but
+// the occupancy hides the latency of the loads and tile-counter atomics (chosen by sweeping
+// 8..16 blocks on 16 Full-HD views of 3M Gaussians).
 #ifndef STP_PRE_MIN_BLOCKS
-#define STP_PRE_MIN_BLOCKS 12
+#define STP_PRE_MIN_BLOCKS 10
 #endif
 #ifndef STP_DUP_MIN_BLOCKS
 #define STP_DUP_MIN_BLOCKS 12
