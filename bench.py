@@ -45,6 +45,35 @@ FLOP_PER_SUBTILE_EVAL, FLOP_PER_QUAD_EVAL, FLOP_PER_PIXEL_EVAL = 80, 80, 45
 FLOP_PER_BLEND_GRAD = 40
 
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "render_traffic_fullhd_3m_16views.md")
+RENDER_SOURCES = ["stp_render.cu", "stp_common.cuh", "stp_kernels.cuh"]
+
+
+def render_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in RENDER_SOURCES:
+        with open(os.path.join(ROOT, "paper_2402_00525_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel: str, n: int, views: int):
+    """DRAM bytes per launch of a Render kernel from the committed ncu capture of this workload,
+    or None when the capture is of other kernel sources or another workload size."""
+    if n != 3_000_000 or views != 16 or not os.path.exists(TRAFFIC_FILE):
+        return None
+    vals = {}
+    for line in open(TRAFFIC_FILE):
+        if ":" in line and line.startswith("- `"):
+            k, v = line[3:].split("`", 1)[0], line.split(":", 1)[1].strip()
+            vals[k] = v
+    if vals.get("render source sha256") != render_source_hash():
+        return None
+    v = vals.get(kernel + " DRAM bytes per launch")
+    return int(v) if v else None
+
+
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -450,14 +479,16 @@ def main():
         "gpu_launches": launches,
         "clocks": clk,
         "roofline": {"bound": "alu", "kernel": "k_render (forward)", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": measured_traffic("k_render<4,0>", scene.n, V),
                      "work_units": {"subtile_evals": cnt[0], "subtile_survivors": cnt[1], "quad_evals": cnt[2],
                                     "blends": cnt[3], "pixel_evals": cnt[4]},
                      "peak_basis": "FP32 FMA issue: %d SMs x 128 lanes x 2 x %.0f MHz" % (props.multi_processor_count, sm_max)},
         "roofline_backward": {"bound": "alu", "kernel": "k_render (backward replay)", "achieved": bachieved,
-                              "peak": peak, "unit": "TFLOP/s", "frac": bachieved / peak, "traffic": None,
+                              "peak": peak, "unit": "TFLOP/s", "frac": bachieved / peak,
+                              "traffic": measured_traffic("k_render<4,1>", scene.n, V),
                               "note": "the replay's decision FLOPs plus %d FLOP per blend for the gradient "
-                                      "terms; its time is dominated by the float atomics" % FLOP_PER_BLEND_GRAD},
+                                      "terms" % FLOP_PER_BLEND_GRAD},
     }
     if world == 1 and not args.no_extra:
         del rnd, out, grads
