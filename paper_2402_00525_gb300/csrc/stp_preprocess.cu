@@ -10,7 +10,6 @@
 //
 // One thread per Gaussian loops over all views of the launch, so the Gaussian's parameters
 // (236 bytes at SH degree 3) are read from HBM once for every view of the batch.
-#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "stp_common.cuh"
@@ -18,7 +17,6 @@
 
 namespace stp {
 
-namespace cg = cooperative_groups;
 
 namespace {
 
@@ -247,34 +245,18 @@ __device__ __forceinline__ bool tile_keep(const PipeArgs& a, const Rec& r, const
     return box_keep(r, b, tile_cull_eps(a));
 }
 
-// Partitioned sort (appendix B.3): count a kept entry of global tile `gt`. Lanes of the
-// calling (possibly divergent) group that hit the same tile add once (labelled partition).
-__device__ __forceinline__ void count_entry(const PipeArgs& a, uint32_t gt, bool aggregate)
+// Partitioned sort (appendix B.3): count a kept entry of global tile `gt`. (Aggregating the
+// lanes of a warp that hit the same tile measured slower than plain atomics here.)
+__device__ __forceinline__ void count_entry(const PipeArgs& a, uint32_t gt)
 {
-    if (!aggregate) {
-        atomicAdd(&a.tile_counts[gt], 1u);
-        return;
-    }
-    cg::coalesced_group act = cg::coalesced_threads();
-    cg::coalesced_group same = cg::labeled_partition(act, gt);
-    if (same.thread_rank() == 0) atomicAdd(&a.tile_counts[gt], same.size());
+    atomicAdd(&a.tile_counts[gt], 1u);
 }
 
 // Partitioned sort: place an entry in its tile's range through the tile's atomic cursor. The
 // order inside a range is arbitrary here and fixed by the per-tile sort on (depth, id).
-__device__ __forceinline__ void place_entry(const PipeArgs& a, uint32_t gt, uint32_t dkey, uint32_t gid,
-                                            bool aggregate)
+__device__ __forceinline__ void place_entry(const PipeArgs& a, uint32_t gt, uint32_t dkey, uint32_t gid)
 {
-    uint32_t slot;
-    if (aggregate) {
-        cg::coalesced_group act = cg::coalesced_threads();
-        cg::coalesced_group same = cg::labeled_partition(act, gt);
-        uint32_t base = 0;
-        if (same.thread_rank() == 0) base = atomicAdd(&a.tile_cursor[gt], same.size());
-        slot = same.shfl(base, 0) + same.thread_rank();
-    } else {
-        slot = atomicAdd(&a.tile_cursor[gt], 1u);
-    }
+    const uint32_t slot = atomicAdd(&a.tile_cursor[gt], 1u);
     if (slot >= a.tile_counts[gt]) {   // more entries than Preprocess counted: cannot happen
         atomicOr(&a.status->error_bits, 2u);
         return;
@@ -317,7 +299,7 @@ __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, int vidx, b
                 if (tile_keep(a, r, b)) {
                     cnt++;
                     if (k < 32) mask |= 1u << k;
-                    if (part) count_entry(a, (uint32_t)(V.tile_off + ty * V.tiles_x + tx), false);
+                    if (part) count_entry(a, (uint32_t)(V.tile_off + ty * V.tiles_x + tx));
                 }
             }
             *mask_io = mask;
@@ -377,7 +359,7 @@ __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, int vidx, b
                 uint32_t dk;
                 if (tile_depth_key(a, V, r, tx, ty, &dk)) {
                     if (part) {
-                        place_entry(a, gt, dk, gid, false);
+                        place_entry(a, gt, dk, gid);
                     } else {
                         const unsigned long long pos = (unsigned long long)off + cnt;
                         if (cnt < want && pos < a.capacity) {
@@ -415,7 +397,7 @@ __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, int vidx, b
             if (keep) {
                 if (EMIT) {
                     if (part) {
-                        place_entry(a, gt, dk, gids, false);
+                        place_entry(a, gt, dk, gids);
                     } else {
                         const uint32_t rank = base + __popc(m & lanemask_lt());
                         const unsigned long long pos = (unsigned long long)offs + rank;
@@ -425,7 +407,7 @@ __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, int vidx, b
                         }
                     }
                 } else if (part) {
-                    count_entry(a, gt, false);
+                    count_entry(a, gt);
                 }
             }
             base += __popc(m);

@@ -3,11 +3,12 @@
 // StopThePop (arXiv 2402.00525) Sec. 3.4 "Hierarchically sorted rendering", Fig. "pipeline",
 // appendix B.4 "Render"; backward Sec. 3.5.
 //
-// One 256-thread block renders one 16x16 tile. Warp w owns the two horizontally adjacent
-// 4x4 subtiles 2w and 2w+1 (an 8x4 pixel strip); half-warp h owns subtile 2w+h, its 4-lane
-// groups own the subtile's four 2x2 quads, and every lane owns one pixel. Each warp walks the
-// tile's sorted list on its own -- the subtiles are independent -- so no block-wide barrier is
-// needed and a warp whose 32 pixels are all saturated retires early.
+// A 16x16 tile is rendered by eight warps (two 4-warp blocks by default). Warp w of the tile
+// owns the two horizontally adjacent 4x4 subtiles 2w and 2w+1 (an 8x4 pixel strip); half-warp
+// h owns subtile 2w+h, its 4-lane groups own the subtile's four 2x2 quads, and every lane owns
+// one pixel. Each warp walks the tile's sorted list on its own -- the subtiles are independent
+// -- so no block-wide barrier is needed and a warp whose 32 pixels are all saturated retires
+// early.
 //
 // Queues (per warp, shared memory; entries are (ordered depth key, Gaussian id)):
 //   tail  : per subtile, double-buffered, TAIL = 32n + 32 entries (the paper's 4x4 queue)
