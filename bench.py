@@ -50,11 +50,16 @@ RENDER_SOURCES = ["stp_render.cu", "stp_common.cuh", "stp_kernels.cuh"]
 
 
 def render_source_hash() -> str:
+    """SHA-256 of the Render sources with comments and whitespace removed (code changes only)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in RENDER_SOURCES:
-        with open(os.path.join(ROOT, "paper_2402_00525_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2402_00525_gb300", "csrc", f)) as fh:
+            txt = fh.read()
+        txt = re.sub(r"/\*.*?\*/", " ", txt, flags=re.S)
+        txt = re.sub(r"//[^\n]*", " ", txt)
+        h.update(" ".join(txt.split()).encode())
     return h.hexdigest()
 
 
