@@ -277,3 +277,28 @@ def test_autotuner_keeps_the_image_under_same_result_policy():
     assert big and big[0].delta_avg <= 1.1 * bd["delta_avg"] + 1e-6
     chosen2, _, _ = A.tune(sc, cams, prm, policy="no-worse", space=space, reps=2, warmup=1)
     assert chosen2.head == 16
+
+
+def test_graph_bound_workspace_reports_overflow_and_refuses_to_grow():
+    """A workspace recorded into a CUDA graph cannot move: when a replay needs more sort entries
+    than it holds, the status block says so (the kernels stay in bounds) and a checked forward
+    raises instead of reallocating under the graph."""
+    sc = I.uniform_scene(2000, 31, scale_range=(0.01, 0.05))
+    cam = I.look_at((0, 0, -3), (0, 0, 0), (0, 1, 0), 128, 128, 60.0)
+    prm = I.RenderParams()
+    g = R.scene_to_device(sc)
+    probe = R.Renderer(sc.n, [cam], prm)
+    probe.forward(g)
+    need = int(probe.status().num_entries)
+    r = R.Renderer(sc.n, [cam], prm, capacity=need + 16)
+    r.forward(g)
+    assert r.status().error_bits == 0
+    out = tuple(torch.empty(sh, device="cuda") for sh in ((cam.num_pixels, 3), (cam.num_pixels,), (cam.num_pixels,)))
+    graph = r.capture(g, out)
+    g["log_scales"].add_(0.7)                        # twice the size: many more (Gaussian, tile) entries
+    graph.replay()
+    torch.cuda.synchronize()
+    st = r.status()
+    assert st.error_bits & 1 and st.num_entries > st.capacity
+    with pytest.raises(R.N.CapacityError):
+        r.forward(g)
