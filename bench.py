@@ -170,7 +170,7 @@ def run_reference(args, rank, world):
     from oracle import build as OB
     OB.build()
     scene, cams, prm = I.full_hd_workload(n=args.n)
-    ntiles = 24
+    ntiles = 96
     for w in range(args.warmup):
         oracle_sample(scene, cams[w % len(cams)], prm, ntiles, 100 + w)
     px, secs = 0, 0.0
@@ -535,7 +535,7 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         from oracle import build as OB
         OB.build()
-        ntiles = 640          # about 10-20 s of FP64 work on the host cores
+        ntiles = 3000         # about 10-20 s of FP64 work on 16 host cores
         px, secs = oracle_sample(scene, cams[0], prm, ntiles, 7)
         line["cpu_baseline"] = {"value": px / secs / 1e6, "unit": "Mpix/s", "cores": oracle_threads(),
                                 "kind": "oracle",
