@@ -160,6 +160,21 @@ def oracle_sample(scene, cam, prm, ntiles, seed):
     return ntiles * 256, dt
 
 
+def single_thread_oracle(n: int, ntiles: int = 64):
+    """The same oracle sample on one host thread (OpenMP fixed at load, so a child process)."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; from paper_2402_00525_gb300 import inputs as I; "
+            "sc, cams, prm = I.full_hd_workload(n=%d, nviews=1); px, t = bench.oracle_sample(sc, cams[0], prm, %d, 7); "
+            "print(json.dumps([px, t]))" % (ROOT, n, ntiles))
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300,
+                           env=dict(os.environ, OMP_NUM_THREADS="1"))
+        px, t = json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception as e:                      # reported, never fatal for the benchmark
+        return {"value": None, "error": str(e)[:200]}
+    return {"value": px / t / 1e6, "unit": "Mpix/s", "cores": 1,
+            "sample": "%d random tiles of view 0, incl. the preprocess of all Gaussians, %.1f s" % (ntiles, t)}
+
+
 def oracle_threads() -> int:
     return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
@@ -539,7 +554,8 @@ def main():
         px, secs = oracle_sample(scene, cams[0], prm, ntiles, 7)
         line["cpu_baseline"] = {"value": px / secs / 1e6, "unit": "Mpix/s", "cores": oracle_threads(),
                                 "kind": "oracle",
-                                "sample": "%d random 16x16 tiles of view 0 (%d px), FP64, incl. the preprocess of all 3M Gaussians, %.1f s" % (ntiles, px, secs)}
+                                "sample": "%d random 16x16 tiles of view 0 (%d px), FP64, incl. the preprocess of all 3M Gaussians, %.1f s" % (ntiles, px, secs),
+                                "single_thread": single_thread_oracle(args.n)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
