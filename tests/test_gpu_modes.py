@@ -101,3 +101,19 @@ def test_backward_under_readings_and_ablations_matches_adjoint(oracle, flags):
         rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
         cos = a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30)
         assert rel <= 1e-3 and cos >= 0.9999, (k, rel, cos)
+
+
+@pytest.mark.parametrize("mode,k", [(I.MODE_GLOBAL, 16), (I.MODE_WINDOW, 16)])
+def test_list_orders_on_full_hd_3m_sampled_tiles(oracle, mode, k):
+    """The list-order comparison modes at the benchmark's scale (3M Gaussians, 1920x1080): one
+    view rendered on the GPU, 30 random tiles by the oracle in the same mode."""
+    from gpu_helpers import tile_mask
+    sc, cams, prm = I.full_hd_workload(nviews=1)
+    prm = dataclasses.replace(prm, mode=mode, window_k=k)
+    gpu = gpu_render(sc, cams, prm)
+    tiles = np.random.default_rng(11 + mode).choice(cams[0].num_tiles, 30, replace=False)
+    with oracle.OracleRun(sc, cams[0], prm, tiles=tiles) as r:
+        ora = r.render()
+    frac = compare_view(gpu, 0, ora, tiles_mask=tile_mask(cams[0], tiles), min_decided=0.7,
+                        label="mode %d full hd" % mode)
+    print("mode", mode, "decided", frac)
