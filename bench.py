@@ -550,7 +550,7 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         from oracle import build as OB
         OB.build()
-        ntiles = 3000         # about 10-20 s of FP64 work on 16 host cores
+        ntiles = 6000         # about 10-20 s of FP64 work on 16 host cores
         px, secs = oracle_sample(scene, cams[0], prm, ntiles, 7)
         line["cpu_baseline"] = {"value": px / secs / 1e6, "unit": "Mpix/s", "cores": oracle_threads(),
                                 "kind": "oracle",
