@@ -344,3 +344,19 @@ def test_per_tile_sort_falls_back_on_skewed_depths(n_near):
     assert np.array_equal(na, np.diff(rb, axis=1)[:, 0])
     assert np.array_equal(ka, kb) and np.array_equal(va, vb)
     assert np.array_equal(a["rgb"][0], b["rgb"][0]) and np.array_equal(a["hash"][0], b["hash"][0])
+
+
+def test_forward_is_deterministic_despite_atomic_placement():
+    """Duplicate places entries through atomic cursors in whatever order the hardware runs
+    them; the per-tile sort by (depth, id) makes the lists, and so the images, identical run
+    to run (the backward's float atomics are not: their gradients agree to rounding)."""
+    sc, cams, prm = I.full_hd_workload(n=400_000, nviews=3)
+    g = R.scene_to_device(sc)
+    r = R.Renderer(sc.n, cams, prm, debug=True)
+    first = [t.clone() for t in r.forward(g)] + [x.clone() for x in r.debug_stats()]
+    ra, ka, va = [x.clone() for x in r.sorted_lists()]
+    for _ in range(3):
+        again = list(r.forward(g)) + list(r.debug_stats())
+        assert all(torch.equal(a, b) for a, b in zip(first, again))
+        rb, kb, vb = r.sorted_lists()
+        assert torch.equal(ra, rb) and torch.equal(ka, kb) and torch.equal(va, vb)
