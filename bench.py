@@ -540,6 +540,14 @@ def main():
                               "note": "the replay's decision FLOPs plus %d FLOP per blend for the gradient "
                                       "terms" % FLOP_PER_BLEND_GRAD},
     }
+    # the paper's own figure, for context only (other GPU, other scenes: not a baseline)
+    line["paper_context"] = {
+        "fwd_mpix_s": 2073600 / 4.986e-3 / 1e6, "ms_per_1080p_view": 4.986,
+        "hardware": "NVIDIA RTX 4090, CUDA 11.8",
+        "workload": "13 trained scenes (Mip-NeRF 360, Tanks & Temples, Deep Blending), avg 2.98M Gaussians, "
+                    "1.7-2.9M sort entries per view",
+        "entries_per_view_here": entries / V,
+    }
     if world == 1 and not args.no_extra:
         del rnd, out, grads
         torch.cuda.empty_cache()
