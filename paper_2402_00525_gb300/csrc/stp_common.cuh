@@ -75,7 +75,7 @@ struct SceneDesc {
 
 // ---------------------------------------------------------------- render record
 // 96-byte per-(view, Gaussian) record written by Preprocess:
-//   r0 = (mean2.x hi, mean2.y hi, mean2.x lo, mean2.y lo)   mean2 = hi + lo (FP64 projection)
+//   r0 = (mean2.x hi, mean2.y hi, mean2.x lo, mean2.y lo)   mean2 = hi + lo (projected in FP64)
 //   r1 = (e.x, e.y, 1/lambda_max, 1/lambda_min)             conic A = Sigma2^-1 in eigen form
 //   r2 = (opacity, c0, c1, c2)
 //   r3 = (m0.x, m0.y, m0.z, m1.x)

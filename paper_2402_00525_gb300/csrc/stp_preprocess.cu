@@ -1,15 +1,17 @@
 // stp_preprocess.cu -- Preprocess, the scan of tile counts, and Duplicate.
 //
 // StopThePop (arXiv 2402.00525) Sec. 3.4 and appendix B: per Gaussian and view, the EWA 2D
-// splat, SH colour, Sigma^-1 with the S^-1 clamp packed with Sigma^-1 (mu - o) for the depth
-// evaluation, the opacity-aware bounding rectangle t_O sqrt(lambda_max), and the number of
-// tiles that survive exact culling (Algorithm 1). Duplicate re-takes the same cull decisions
-// and writes one (tile, t_opt) key per surviving tile. Both stages use the paper's two-phase
-// load balancing: a Gaussian with at most `lb_threshold` candidate tiles is handled by its own
-// thread; larger ones are handled by the whole warp (ballot / shuffle / popc offsets).
+// splat, SH colour, Sigma^-1 with the S^-1 clamp in factored form for the depth evaluation,
+// the candidate tiles from the opacity-aware extent (appendix B.2; here the axis-aligned box
+// of the ellipse o G >= eps_O), and the number of tiles that survive exact culling (Algorithm
+// 1), with the kept candidates of small rectangles recorded in a bit mask. Duplicate writes
+// one (tile, t_opt) key per kept tile (computing depths only for the masked tiles, or taking
+// the same cull decisions again for larger rectangles). Both stages use the paper's two-phase
+// load balancing: a record with at most `lb_threshold` candidate tiles is handled by its own
+// thread; larger ones by the whole warp (ballot / shuffle / popc offsets).
 //
-// One thread per Gaussian loops over all views of the launch, so the Gaussian's parameters
-// (236 bytes at SH degree 3) are read from HBM once for every view of the batch.
+// One thread per (Gaussian, view), the views of a Gaussian in neighbouring lanes, so the
+// Gaussian's parameters (236 bytes at SH degree 3) are read from HBM once for all its views.
 #include <cuda_runtime.h>
 
 #include "stp_common.cuh"

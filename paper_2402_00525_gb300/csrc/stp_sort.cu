@@ -1,8 +1,10 @@
-// stp_sort.cu -- global sort of (tile, depth) keys and the per-tile ranges.
+// stp_sort.cu -- the sorts of (tile, depth) entries and the per-tile ranges.
 //
-// StopThePop (arXiv 2402.00525) keeps 3DGS's single global sort of combined keys, tile id in
-// the high bits and depth in the low bits (Sec. 2.1, appendix B.3), and relies on a stable
-// order so that forward and backward see the same list (Sec. 3.5). This is a stable LSD radix
+// Two ways to the same lists: the per-tile sort of appendix B.3 (k_tile_sort, the default;
+// described further below) and the global sort of combined keys that StopThePop keeps from
+// 3DGS, tile id in the high bits and depth in the low bits (Sec. 2.1, appendix B.3). Both
+// give the stable order (ties by Gaussian id) that forward and backward share (Sec. 3.5).
+// The global sort (STP_FLAG_GLOBAL_SORT, and stp_sort_pairs) is a stable LSD radix
 // sort with 8-bit digits over only the key bits in use (32 depth bits + the bits of the tile
 // count), three kernels per digit:
 //   hist    -- every block counts the digits of a fixed contiguous range of the input;
