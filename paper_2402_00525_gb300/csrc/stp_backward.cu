@@ -1,9 +1,11 @@
 // stp_backward.cu -- adjoint of Preprocess.
 //
 // StopThePop (arXiv 2402.00525) Sec. 3.5 keeps 3DGS's gradient flow: the backward Render
-// (stp_render.cu, BWD = true) accumulates per (view, Gaussian) the gradients of the 2D mean,
-// the conic, the opacity, the colour and -- when a depth gradient is given -- of the depth
-// factors (m_k, c_k) of the record; this kernel chains them back to the inputs:
+// (stp_render.cu, BWD = true) accumulates per (view, Gaussian) the gradient of the conic and of
+// the colour, the sums dGG (x - mean2) and dGG from which this kernel forms the gradients of
+// the 2D mean (A times the first) and of the opacity (the second over the opacity), and --
+// when a depth gradient is given -- those of the depth factors (m_k, c_k) of the record; this
+// kernel chains them back to the inputs:
 //   colour  -> SH coefficients, and through the view direction -> mean
 //   opacity -> logit
 //   conic   -> Sigma2 -> (Sigma, J) -> (scale, rotation) and the camera-space mean -> mean
