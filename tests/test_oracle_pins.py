@@ -490,3 +490,52 @@ def test_without_hierarchical_culling_every_entry_reaches_the_pixels(oracle):
     assert np.array_equal(e["hash"][d], full["hash"][d])
     assert e["counters"]["surv_subtile"] == e["counters"]["eval_subtile"] > h["counters"]["surv_subtile"]
     assert e["counters"]["eval_quad"] > h["counters"]["eval_quad"]
+
+
+def test_global_order_decided_pixels_have_a_clear_termination_order(oracle):
+    """Reading R9 for the list orders: a pixel counts as decided only if the entry that ends its
+    ray and the next contributing entry of the tile list are more than the depth-gap threshold
+    apart (swapped, the other one would be taken first). Recomputed here from the oracle's own
+    tile lists and preprocess: GLOBAL blending per pixel in numpy."""
+    base = I.cluster_scene(3000, 41, nclusters=4, centre_range=1.0, scale_range=(0.01, 0.1))
+    base.opacity_logits[:] = 4.0                     # opaque: rays end after a few blends
+    cam = I.look_at((0.2, -0.1, -4), (0, 0, 0), (0, 1, 0), 128, 96, 50.0)
+    # a tenth of the Gaussians get a twin 1e-7 of their depth further along their view ray, so
+    # some rays end on an entry whose twin follows it in the list at a near-equal key
+    eye = -cam.R.T @ cam.t
+    pick = np.random.default_rng(5).random(base.n) < 0.1
+    d = base.means[pick] - eye
+    twin = I.Scene(base.means[pick] + 1e-7 * d, base.log_scales[pick], base.quats[pick],
+                   base.opacity_logits[pick], base.sh[pick], base.sh_degree)
+    sc = I.Scene(*[np.concatenate([getattr(base, f), getattr(twin, f)]) for f in
+                   ("means", "log_scales", "quats", "opacity_logits", "sh")], base.sh_degree)
+    prm = I.RenderParams(mode=I.MODE_GLOBAL)
+    with oracle.OracleRun(sc, cam, prm) as r:
+        pp = r.preprocess()
+        start, ids, ts = r.tile_lists()
+        out = r.render()
+    checked = tied = 0
+    for y in range(cam.height):
+        for x in range(cam.width):
+            t = (y // 16) * cam.tiles_x + x // 16
+            L, K = ids[start[t]:start[t + 1]], ts[start[t]:start[t + 1]]
+            m = pp["mean2"][L]
+            a_, b_, c_ = pp["conic"][L].T
+            dx, dy = x + 0.5 - m[:, 0], y + 0.5 - m[:, 1]
+            al = np.minimum(prm.alpha_max, pp["opacity"][L] * np.exp(-0.5 * (a_ * dx * dx + 2 * b_ * dx * dy + c_ * dy * dy)))
+            contrib = np.nonzero(al >= prm.eps_o)[0]
+            T, stop = 1.0, None
+            for k, j in enumerate(contrib):
+                if T * (1 - al[j]) < prm.t_min:
+                    stop = k
+                    break
+                T *= 1 - al[j]
+            if stop is None or stop + 1 >= len(contrib):
+                continue
+            k0, k1 = K[contrib[stop]], K[contrib[stop + 1]]
+            gap = abs(k0 - k1) / max(abs(k0), abs(k1), 1e-30)
+            if out["decided"][y, x]:
+                assert gap > oracle.GAP_THR, (x, y, gap)
+            checked += 1
+            tied += gap <= oracle.GAP_THR
+    assert checked > 200 and tied > 20
