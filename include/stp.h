@@ -5,7 +5,8 @@
  * The forward pass is the paper's four stages (Sec. 3, Fig. "pipeline"): Preprocess,
  * Duplicate (with exact tile culling and the per-tile t_opt key), a global sort of
  * (tile, depth) keys, and the hierarchical Render with tail / mid / head queues. The backward
- * pass replays the same blend order front to back (Sec. 3.5).
+ * pass walks the same blend order front to back (Sec. 3.5): the order the forward stored per
+ * pixel, or a replay of the queues where it did not fit.
  *
  * Conventions shared by every entry point:
  *   - Every array pointer is a DEVICE pointer owned by the caller unless the comment says
@@ -116,12 +117,21 @@ typedef struct {
     int32_t mode;                /* STP_MODE_*                                              */
     int32_t window_k;            /* k of STP_MODE_WINDOW                                    */
     int32_t flags;               /* STP_FLAG_* */
-    int32_t reserved;
+    int32_t blend_cap;           /* 0..4096. With STP_FLAG_BACKWARD in STP_MODE_HIER the forward
+                                    Render stores, per pixel, the ids of the first blend_cap
+                                    Gaussians it blends, in blend order (workspace regions
+                                    blend_ids / blend_count: 1 KB per pixel at 256); the backward
+                                    then walks those ids instead of replaying the queues, and
+                                    only warps (8x4 pixel strips) with a pixel that blended more
+                                    replay the schedule. Same gradients either way (up to the
+                                    order of float atomics). 0 = every warp replays.        */
     int64_t max_entries;         /* capacity of (Gaussian, tile) sort entries for one call  */
 } stp_params;
 
 typedef struct {                 /* device status block, read back by stp_read_status        */
-    uint32_t error_bits;         /* 1 capacity exceeded, 2 count mismatch padded, 4 timeout   */
+    uint32_t error_bits;         /* 1 capacity exceeded, 2 count mismatch padded, 4 timeout,
+                                    8 the backward's blend sequence disagreed with the forward
+                                    (recomputed final T or blend count)                      */
     uint32_t mismatched;         /* Gaussians whose Duplicate count differed from Preprocess  */
     uint64_t num_entries;        /* entries the last forward needed (may exceed capacity)    */
     uint64_t capacity;           /* entries the workspace holds                              */
@@ -162,6 +172,10 @@ typedef struct {                 /* byte offsets of workspace regions (for inspe
     size_t tile_offsets;         /* [total tiles] uint32 first entry of each tile            */
     size_t tile_cursor;          /* [total tiles] uint32 placement cursors                   */
     size_t tile_partials;        /* scan scratch of the tile counts                          */
+    size_t blend_ids;            /* [total tiles * 8 warps][blend_cap][32] uint32 stored blend
+                                    order (flag 64, HIER, blend_cap > 0), else 0: slot k of the
+                                    warp's lane l (pixel of its 8x4 strip) at (w*cap + k)*32 + l */
+    size_t blend_count;          /* [total pixels] uint32 blends per pixel (with blend_ids)  */
     size_t total;                /* total bytes                                              */
     int64_t capacity;            /* sort-entry capacity                                      */
     int64_t total_tiles, total_pixels;
@@ -194,9 +208,10 @@ stp_status stp_render(const stp_gaussians* g /* host struct of device pointers *
                       const stp_params* prm /* host */, void* workspace, size_t ws_bytes,
                       float* rgb, float* depth, float* tfinal, void* stream);
 
-/* Backward pass (Sec. 3.5): replays the forward's blend order front to back using the
+/* Backward pass (Sec. 3.5): walks the forward's blend order front to back using the
  * workspace of the preceding stp_render with the same arguments (which must not have been
- * modified), and ACCUMULATES (+=) the gradients of <d_rgb, rgb> + <d_depth, depth> into
+ * modified): the per-pixel order stored by the forward (blend_cap > 0), else, and for warps
+ * whose pixels blended more than blend_cap Gaussians, a replay of the queues. ACCUMULATES (+=) the gradients of <d_rgb, rgb> + <d_depth, depth> into
  * `grad` (device arrays in the input layout; zero them first for a fresh gradient).
  * d_depth may be NULL. Asynchronous.                                                       */
 stp_status stp_render_backward(const stp_gaussians* g, const stp_camera* cams, int32_t nviews,
@@ -286,7 +301,7 @@ uint64_t stp_kernel_launches(void);
 /* Thread-local message of the last error on this host thread (empty if none).            */
 const char* stp_last_error(void);
 
-/* Library version, e.g. 0x000200 for 0.2.0.                                              */
+/* Library version, e.g. 0x000300 for 0.3.0.                                              */
 int32_t stp_version(void);
 
 #ifdef __cplusplus

@@ -60,7 +60,7 @@ class Params(C.Structure):
                 ("alpha_max", C.c_float), ("inv_scale_max", C.c_float), ("dilation", C.c_float),
                 ("frustum_clamp", C.c_float), ("znear", C.c_float), ("bg", C.c_float * 3),
                 ("mode", C.c_int32), ("window_k", C.c_int32), ("flags", C.c_int32),
-                ("reserved", C.c_int32), ("max_entries", C.c_int64)]
+                ("blend_cap", C.c_int32), ("max_entries", C.c_int64)]
 
 
 class RunStatus(C.Structure):
@@ -73,7 +73,7 @@ _LAYOUT_SIZE_FIELDS = ["status", "views", "scenes", "geom", "color", "rect", "co
                        "scan_partials", "keys", "vals", "keys_alt", "vals_alt", "sorted_keys",
                        "sorted_vals", "ranges", "tfinal", "pix_state", "scratch", "dbg_nblend",
                        "dbg_hash", "dbg_delta", "grad_geom", "dbg_trace", "tile_counts", "tile_offsets",
-                       "tile_cursor", "tile_partials", "total"]
+                       "tile_cursor", "tile_partials", "blend_ids", "blend_count", "total"]
 
 
 class Layout(C.Structure):
@@ -183,6 +183,7 @@ def params_struct(prm: RenderParams, extra_flags: int = 0, max_entries: int = 0)
                                                              prm.frustum_clamp, prm.znear)
     p.bg[:] = [float(b) for b in prm.bg]
     p.mode, p.window_k, p.flags = prm.mode, prm.window_k, prm.flags | extra_flags
+    p.blend_cap = int(prm.blend_cap)
     p.max_entries = int(max_entries)
     return p
 

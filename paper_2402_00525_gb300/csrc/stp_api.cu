@@ -121,6 +121,8 @@ stp_status check(const int64_t* ns, const int32_t* vps, int32_t nscenes, const s
         return fail(STP_ERR_ARG, "mode %d: must be one of STP_MODE_HIER, FULL, GLOBAL, WINDOW", p->mode);
     if (p->mode == STP_MODE_WINDOW && !stp::render_head_supported(p->window_k))
         return fail(STP_ERR_NOT_SUPPORTED, "window_k = %d: compiled sizes are 1, 2, 4, 8, 16", p->window_k);
+    if (p->blend_cap < 0 || p->blend_cap > 4096)
+        return fail(STP_ERR_ARG, "blend_cap = %d: must be in [0, 4096]", p->blend_cap);
     if (p->max_entries < 0 || p->max_entries >= 0xFFFFFFFFLL)
         return fail(STP_ERR_ARG, "max_entries must be in [0, 2^32 - 1)");
     return STP_OK;
@@ -221,6 +223,11 @@ void make_plan(const int64_t* ns, const int32_t* vps, int32_t nscenes, const stp
     L.tile_partials = take(stp::scan_partials_count(tiles) * 8);
     L.grad_geom = 0;
     if (p->flags & kFlagBackward) L.grad_geom = take((size_t)P.m * stp::kGradStride * 4);
+    L.blend_ids = L.blend_count = 0;
+    if ((p->flags & kFlagBackward) && p->mode == STP_MODE_HIER && p->blend_cap > 0) {
+        L.blend_ids = take((size_t)tiles * 256 * (size_t)p->blend_cap * 4);
+        L.blend_count = take((size_t)pixels * 4);
+    }
     L.dbg_trace = 0;
     if (p->flags & kFlagTrace) L.dbg_trace = take((size_t)pixels * stp::kTraceLen * 4);
     L.total = o;
@@ -273,6 +280,9 @@ stp::PipeArgs make_args(const stp_params* p, const Plan& P, void* ws)
     a.sort_temp_bytes = stp::sort_hist_bytes();
     a.key_bits = L.key_bits;
     a.grad_geom = L.grad_geom ? (float*)(b + L.grad_geom) : nullptr;
+    a.blist = L.blend_ids ? (uint32_t*)(b + L.blend_ids) : nullptr;
+    a.blist_count = L.blend_count ? (uint32_t*)(b + L.blend_count) : nullptr;
+    a.blend_cap = L.blend_ids ? p->blend_cap : 0;
     a.dbg_trace = L.dbg_trace ? (int*)(b + L.dbg_trace) : nullptr;
     a.partitioned = (p->flags & kFlagGlobalSort) ? 0 : 1;
     a.tile_counts = (uint32_t*)(b + L.tile_counts);
@@ -431,7 +441,7 @@ uint64_t stp_kernel_launches(void) { return g_launches.load(std::memory_order_re
 
 const char* stp_last_error(void) { return g_err.c_str(); }
 
-int32_t stp_version(void) { return 0x000200; }
+int32_t stp_version(void) { return 0x000300; }
 
 stp_status stp_workspace_layout_batched(const int64_t* n, const int32_t* views_per_scene, int32_t nscenes,
                                         const stp_camera* cams, int32_t nviews, const stp_params* prm,

@@ -63,6 +63,11 @@ struct PipeArgs {
     const float* d_rgb;
     const float* d_depth;
     float* grad_geom;        // [m*kGradStride] per-(view, Gaussian) 2D gradients
+    // stored blend order (HIER forward with a backward to follow): per tile warp (8 per tile)
+    // blend_cap x 32 ids, slot k of lane l at (warp * blend_cap + k) * 32 + l; null = replay
+    uint32_t* blist;
+    uint32_t* blist_count;   // [total_pixels] blends of the pixel (may exceed blend_cap)
+    int blend_cap;
 };
 
 // Scene of the thread block whose first thread is t0 (largest s with thread_off <= t0).

@@ -105,7 +105,78 @@ struct PixCtx {
     long long pix;               // packed pixel index, -1 outside the image
     float g0, g1, g2, gz, gbg;   // backward: dL/drgb, dL/ddepth, <dL/drgb, bg>
     float Cf0, Cf1, Cf2, Zf, Tf; // backward: final colour (no background), depth, T
+    long long bl;                // stored blend order: slot 0 of this pixel (slot k at bl + 32 k)
 };
+
+// Gradient terms of one blended Gaussian (Sec. 3.5), given the pixel's state just after the
+// blend: T = T_i (transmittance in front of it), C / Z = colour and depth accumulated up to
+// and including it. dL/dalpha_i uses the suffix C_final - C_i and T_N / (1 - alpha_i).
+// Per-(view, Gaussian) scratch, 24 floats: [0..7] (sum dGG d.xy, dA00, dA01, dA11, sum dGG,
+// dcolour.rg), [8] dcolour.b, [12..23] depth factors (dm_k 9, dc_k 3). The first nine are
+// returned in (q0, q1, qc) for the caller to accumulate; the depth factors (only with a
+// depth gradient) are accumulated here with vector reductions (red.global.add.v4.f32).
+__device__ __forceinline__ void grad_terms(const PipeArgs& a, const PixCtx& c, long long ri, const float4 col,
+                                           const float4 r0, float alpha, float val, float t, float T,
+                                           float C0, float C1, float C2, float Z,
+                                           float4& q0, float4& q1, float& qc)
+{
+    const float wgt = alpha * T;
+    const float inv = __fdividef(1.f, 1.f - alpha);     // 1 - alpha >= 1 - alpha_max > 0
+    float da = c.g0 * (col.x * T - (c.Cf0 - C0) * inv) + c.g1 * (col.y * T - (c.Cf1 - C1) * inv) +
+               c.g2 * (col.z * T - (c.Cf2 - C2) * inv) - c.gbg * c.Tf * inv;
+    da += c.gz * (t * T - (c.Zf - Z) * inv);
+    Rec r;
+    r.r0 = r0;
+    q0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    q1 = make_float4(0.f, 0.f, c.g0 * wgt, c.g1 * wgt);
+    qc = c.g2 * wgt;
+    if (val < a.alpha_max) {
+        // val = opacity * G at this pixel, so with dGG = da * val: dL/dopacity gets dGG /
+        // opacity, dL/dA gets -dGG d d^T / 2 and dL/dmean2 gets A dGG d (d = x - mean2).
+        // The factors A and 1 / opacity are the same for every pixel of this (view,
+        // Gaussian), so the scratch sums dGG d and dGG, and the backward Preprocess
+        // applies them once.
+        const float dx = off_x(r, c.xc), dy = off_y(r, c.yc);
+        const float dGG = da * val;
+        q0 = make_float4(dGG * dx, dGG * dy, dGG * (-0.5f * dx * dx), dGG * (-dx * dy));
+        q1.x = dGG * (-0.5f * dy * dy);
+        q1.y = dGG;
+    }
+    if (c.gz != 0.f) {
+        // t = |d| N / D with a_k = m_k . d, N = sum a_k c_k, D = sum a_k^2 (record layout);
+        // the depth factors r2..r5 are loaded only here
+        float* gg = a.grad_geom + ri * kGradStride;
+        const float4* rp = a.geom + kRecFloat4 * ri;
+        r.r2 = __ldg(rp + 2);
+        r.r3 = __ldg(rp + 3);
+        r.r4 = __ldg(rp + 4);
+        r.r5 = __ldg(rp + 5);
+        const float u = c.u, w = c.w;
+        const float m[3][3] = {{r.r3.x, r.r3.y, r.r3.z}, {r.r3.w, r.r4.x, r.r4.y}, {r.r4.z, r.r4.w, r.r5.x}};
+        const float cc[3] = {r.r2.y, r.r2.z, r.r2.w};
+        float ak[3], dak[3];
+        for (int k = 0; k < 3; k++) ak[k] = m[k][0] * u + m[k][1] * w + m[k][2];
+        const float num = ak[0] * cc[0] + ak[1] * cc[1] + ak[2] * cc[2];
+        const float den = ak[0] * ak[0] + ak[1] * ak[1] + ak[2] * ak[2];
+        const float n = sqrtf(u * u + w * w + 1.f);
+        const float dt = c.gz * wgt;
+        const float tq = num / den;
+        for (int k = 0; k < 3; k++) dak[k] = dt * n * (cc[k] - 2.f * tq * ak[k]) / den;   // dt/da_k
+        const float fc = dt * n / den;                                                   // dt/dc_k = fc a_k
+        atomicAdd(reinterpret_cast<float4*>(gg + 12), make_float4(dak[0] * u, dak[0] * w, dak[0], dak[1] * u));
+        atomicAdd(reinterpret_cast<float4*>(gg + 16), make_float4(dak[1] * w, dak[1], dak[2] * u, dak[2] * w));
+        atomicAdd(reinterpret_cast<float4*>(gg + 20), make_float4(dak[2], fc * ak[0], fc * ak[1], fc * ak[2]));
+    }
+}
+
+// accumulate the nine terms of grad_terms into the (view, Gaussian) scratch
+__device__ __forceinline__ void grad_red(const PipeArgs& a, long long ri, const float4 q0, const float4 q1, float qc)
+{
+    float* gg = a.grad_geom + ri * kGradStride;
+    atomicAdd(reinterpret_cast<float4*>(gg), q0);
+    atomicAdd(reinterpret_cast<float4*>(gg + 4), q1);
+    atomicAdd(gg + 8, qc);
+}
 
 template <int HEAD, bool BWD>
 __device__ __forceinline__ void blend(const PipeArgs& a, const ViewDesc& V, Px<HEAD>& s,
@@ -127,58 +198,13 @@ __device__ __forceinline__ void blend(const PipeArgs& a, const ViewDesc& V, Px<H
     s.C2 += col.z * wgt;
     s.Z += t * wgt;
     if (BWD) {
-        // per-(view, Gaussian) scratch, 24 floats: [0..7] (sum dGG d.xy, dA00, dA01, dA11,
-        // sum dGG, dcolour.rg), [8] dcolour.b, [12..23] depth factors (dm_k 9, dc_k 3);
-        // accumulated with vector reductions (red.global.add.v4.f32)
-        float* gg = a.grad_geom + ri * kGradStride;
-        const float inv = __fdividef(1.f, 1.f - alpha);     // 1 - alpha >= 1 - alpha_max > 0
-        float da = c.g0 * (col.x * s.T - (c.Cf0 - s.C0) * inv) + c.g1 * (col.y * s.T - (c.Cf1 - s.C1) * inv) +
-                   c.g2 * (col.z * s.T - (c.Cf2 - s.C2) * inv) - c.gbg * c.Tf * inv;
-        da += c.gz * (t * s.T - (c.Zf - s.Z) * inv);
-        // the projected mean (the depth factors r2..r5 only for a depth gradient below)
-        Rec r;
-        const float4* rp = a.geom + kRecFloat4 * ri;
-        r.r0 = __ldg(rp);
-        float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 q1 = make_float4(0.f, 0.f, c.g0 * wgt, c.g1 * wgt);
-        if (val < a.alpha_max) {
-            // val = opacity * G at this pixel, so with dGG = da * val: dL/dopacity gets dGG /
-            // opacity, dL/dA gets -dGG d d^T / 2 and dL/dmean2 gets A dGG d (d = x - mean2).
-            // The factors A and 1 / opacity are the same for every pixel of this (view,
-            // Gaussian), so the scratch sums dGG d and dGG, and the backward Preprocess
-            // applies them once.
-            const float dx = off_x(r, c.xc), dy = off_y(r, c.yc);
-            const float dGG = da * val;
-            q0 = make_float4(dGG * dx, dGG * dy, dGG * (-0.5f * dx * dx), dGG * (-dx * dy));
-            q1.x = dGG * (-0.5f * dy * dy);
-            q1.y = dGG;
-        }
-        atomicAdd(reinterpret_cast<float4*>(gg), q0);
-        atomicAdd(reinterpret_cast<float4*>(gg + 4), q1);
-        atomicAdd(gg + 8, c.g2 * wgt);
-        if (c.gz != 0.f) {
-            // t = |d| N / D with a_k = m_k . d, N = sum a_k c_k, D = sum a_k^2 (record layout)
-            r.r2 = __ldg(rp + 2);
-            r.r3 = __ldg(rp + 3);
-            r.r4 = __ldg(rp + 4);
-            r.r5 = __ldg(rp + 5);
-            const float u = c.u, w = c.w;
-            const float m[3][3] = {{r.r3.x, r.r3.y, r.r3.z}, {r.r3.w, r.r4.x, r.r4.y}, {r.r4.z, r.r4.w, r.r5.x}};
-            const float cc[3] = {r.r2.y, r.r2.z, r.r2.w};
-            float ak[3], dak[3];
-            for (int k = 0; k < 3; k++) ak[k] = m[k][0] * u + m[k][1] * w + m[k][2];
-            const float num = ak[0] * cc[0] + ak[1] * cc[1] + ak[2] * cc[2];
-            const float den = ak[0] * ak[0] + ak[1] * ak[1] + ak[2] * ak[2];
-            const float n = sqrtf(u * u + w * w + 1.f);
-            const float dt = c.gz * wgt;
-            const float tq = num / den;
-            for (int k = 0; k < 3; k++) dak[k] = dt * n * (cc[k] - 2.f * tq * ak[k]) / den;   // dt/da_k
-            const float fc = dt * n / den;                                                   // dt/dc_k = fc a_k
-            atomicAdd(reinterpret_cast<float4*>(gg + 12), make_float4(dak[0] * u, dak[0] * w, dak[0], dak[1] * u));
-            atomicAdd(reinterpret_cast<float4*>(gg + 16), make_float4(dak[1] * w, dak[1], dak[2] * u, dak[2] * w));
-            atomicAdd(reinterpret_cast<float4*>(gg + 20), make_float4(dak[2], fc * ak[0], fc * ak[1], fc * ak[2]));
-        }
+        float4 q0, q1;
+        float qc;
+        grad_terms(a, c, ri, col, __ldg(a.geom + kRecFloat4 * ri), alpha, val, t, s.T, s.C0, s.C1, s.C2, s.Z, q0, q1, qc);
+        grad_red(a, ri, q0, q1, qc);
     }
+    // the stored blend order (backward without replay): the first blend_cap ids of the pixel
+    if (!BWD && a.blist && s.nbl < (uint32_t)a.blend_cap) a.blist[c.bl + 32ll * s.nbl] = id;
     if (!BWD && a.dbg_trace && s.nbl < (uint32_t)kTraceLen) a.dbg_trace[c.pix * kTraceLen + s.nbl] = (int)id;
     if (!BWD && a.dbg_hash) {          // debug statistics: order hash and sort error
         s.hash = s.hash * kHashMul + (unsigned long long)(id + 1u);
@@ -409,7 +435,8 @@ __global__ void __launch_bounds__(32 * kRenderWarps, (render_min_blocks<HEAD, BW
         const int m = (lo + hi + 1) >> 1;
         if (a.views[m].tile_off <= gtile) lo = m; else hi = m - 1;
     }
-    const ViewDesc& V = a.views[lo];
+    // a local copy: read through a reference, its fields would be reloaded after every store
+    const ViewDesc V = a.views[lo];
     const int W = V.W, H = V.H;
     const int tile = gtile - V.tile_off;
     const int tx = tile % V.tiles_x, ty = tile / V.tiles_x;
@@ -438,6 +465,12 @@ __global__ void __launch_bounds__(32 * kRenderWarps, (render_min_blocks<HEAD, BW
     c.w = to_w(V, c.yc);
     c.n = ray_norm(c.u, c.w);
     c.pix = inside ? V.pix_off + (long long)pyi * W + pxi : -1;
+    c.bl = ((long long)(gtile * 8 + warp) * a.blend_cap) * 32 + lane;
+    if (BWD && a.blist) {
+        // with a stored blend order only the warps with a pixel past its capacity replay
+        const uint32_t nb = inside ? a.blist_count[c.pix] : 0u;
+        if (!__any_sync(kFull, nb > (uint32_t)a.blend_cap)) return;
+    }
     c.g0 = c.g1 = c.g2 = c.gz = c.gbg = 0.f;
     c.Cf0 = c.Cf1 = c.Cf2 = c.Zf = c.Tf = 0.f;
     if (BWD && inside) {
@@ -576,6 +609,7 @@ __global__ void __launch_bounds__(32 * kRenderWarps, (render_min_blocks<HEAD, BW
         a.depth[p] = s.Z;
         a.tfinal_ws[p] = s.T;
         if (a.grad_geom) reinterpret_cast<float4*>(a.pix_state)[p] = make_float4(s.C0, s.C1, s.C2, s.Z);
+        if (a.blist) a.blist_count[p] = s.nbl;
         if (a.tfinal_out) a.tfinal_out[p] = s.T;
         if (a.dbg_nblend) a.dbg_nblend[p] = s.nbl;
         if (a.dbg_hash) a.dbg_hash[p] = s.hash;
@@ -585,6 +619,128 @@ __global__ void __launch_bounds__(32 * kRenderWarps, (render_min_blocks<HEAD, BW
     }
 }
 
+// Backward over the stored blend order (Sec. 3.5). The forward Render recorded, per pixel, the
+// ids it blended in blend order, so the gradients need no replay of the queues: each thread
+// walks its pixel's ids front to back, recomputes alpha (and, for a depth gradient, t_opt) from
+// the record with the forward's own rounding, and forms the same terms as the replay. Warps with
+// a pixel past the capacity are left to the replay kernel, which returns at once for all others.
+// Same block shape and pixel mapping as the forward. The product of the recomputed (1 - alpha)
+// must reproduce the forward's final T bit for bit; a pixel where it does not sets error bit 8.
+//
+// Neighbouring pixels often blend the same Gaussian at the same step (on 16 Full-HD views of 3M
+// Gaussians a step of a warp holds about 11 distinct ids over 27 live lanes), so the lanes of a
+// step that share an id sum their nine terms in shared memory and one of them issues the
+// reductions: 40% of the per-lane reductions, which dominate this kernel's L2 traffic.
+#ifndef STP_BWD_LIST_MIN_BLOCKS
+#define STP_BWD_LIST_MIN_BLOCKS 8
+#endif
+__global__ void __launch_bounds__(32 * kRenderWarps, STP_BWD_LIST_MIN_BLOCKS * 4 / kRenderWarps) k_render_bwd_list(PipeArgs a)
+{
+    __shared__ float sagg[kRenderWarps][9][33];   // [warp][term][lane], padded: conflict-free
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int warp = (int)(blockIdx.x % kBlocksPerTile) * kRenderWarps + wib;   // warp of the tile
+    if (a.status->error_bits & 1u) return;
+    const int gtile = (int)(blockIdx.x / kBlocksPerTile);
+    int lo = 0, hi = a.nviews - 1;
+    while (lo < hi) {
+        const int m = (lo + hi + 1) >> 1;
+        if (a.views[m].tile_off <= gtile) lo = m; else hi = m - 1;
+    }
+    const ViewDesc V = a.views[lo];
+    const int tile = gtile - V.tile_off;
+    const int tx = tile % V.tiles_x, ty = tile / V.tiles_x;
+    const int h = lane >> 4, q = (lane & 15) >> 2, pq = lane & 3;
+    const int sme = warp * 2 + h;
+    const int pxi = tx * kTile + (sme & 3) * 4 + (q & 1) * 2 + (pq & 1);
+    const int pyi = ty * kTile + (sme >> 2) * 4 + (q >> 1) * 2 + (pq >> 1);
+    const bool inside = pxi < V.W && pyi < V.H;
+    PixCtx c;
+    c.xc = pxi + 0.5f;
+    c.yc = pyi + 0.5f;
+    c.u = to_u(V, c.xc);
+    c.w = to_w(V, c.yc);
+    c.n = ray_norm(c.u, c.w);
+    c.pix = inside ? V.pix_off + (long long)pyi * V.W + pxi : -1;
+    c.bl = ((long long)(gtile * 8 + warp) * a.blend_cap) * 32 + lane;
+    const uint32_t nb = inside ? a.blist_count[c.pix] : 0u;
+    if (__any_sync(kFull, nb > (uint32_t)a.blend_cap)) return;     // replayed
+    c.g0 = c.g1 = c.g2 = c.gz = c.gbg = 0.f;
+    c.Cf0 = c.Cf1 = c.Cf2 = c.Zf = c.Tf = 0.f;
+    if (inside) {
+        c.g0 = a.d_rgb[3 * c.pix];
+        c.g1 = a.d_rgb[3 * c.pix + 1];
+        c.g2 = a.d_rgb[3 * c.pix + 2];
+        c.gz = a.d_depth ? a.d_depth[c.pix] : 0.f;
+        c.gbg = c.g0 * a.bg[0] + c.g1 * a.bg[1] + c.g2 * a.bg[2];
+        const float4 cz = reinterpret_cast<const float4*>(a.pix_state)[c.pix];
+        c.Cf0 = cz.x; c.Cf1 = cz.y; c.Cf2 = cz.z; c.Zf = cz.w;
+        c.Tf = a.tfinal_ws[c.pix];
+    }
+    const bool with_depth = a.d_depth != nullptr;
+    const uint32_t* ids = a.blist + c.bl;
+    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, Z = 0.f;
+    const uint32_t nmax = __reduce_max_sync(kFull, nb);
+    uint32_t nxt = nb > 0 ? __ldg(ids) : 0u;
+    // every lane runs the warp's longest list so that the steps stay aligned for the sharing
+#pragma unroll 1
+    for (uint32_t k = 0; k < nmax; k++) {
+        const bool valid = k < nb;
+        const uint32_t id = valid ? nxt : 0xFFFFFFFFu;
+        if (k + 1 < nb) nxt = __ldg(ids + 32ll * (k + 1));
+        const long long ri = V.rec_off + (valid ? id : 0u);
+        float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0;
+        float qc = 0.f;
+        if (valid) {
+            const float4* rp = a.geom + kRecFloat4 * ri;
+            Rec r;
+            r.r0 = __ldg(rp);
+            r.r1 = __ldg(rp + 1);
+            r.r2 = __ldg(rp + 2);
+            const float val = splat_value(r, c.xc, c.yc);
+            float t = 0.f;
+            if (with_depth) {
+                r.r3 = __ldg(rp + 3);
+                r.r4 = __ldg(rp + 4);
+                r.r5 = __ldg(rp + 5);
+                t = depth_uvn(r, c.u, c.w, c.n);
+            }
+            const float alpha = fminf(a.alpha_max, val);
+            const float4 col = __ldg(a.color + ri);
+            const float wgt = alpha * T;
+            C0 += col.x * wgt;
+            C1 += col.y * wgt;
+            C2 += col.z * wgt;
+            Z += t * wgt;
+            grad_terms(a, c, ri, col, r.r0, alpha, val, t, T, C0, C1, C2, Z, q0, q1, qc);
+            T = __fmul_rn(T, __fsub_rn(1.f, alpha));
+        }
+        // lanes holding the same id (finished lanes share the id ~0 and issue nothing)
+        const unsigned peers = __match_any_sync(kFull, id);
+        const bool solo = peers == (1u << lane);
+        const int leader = __ffs(peers) - 1;
+        float* sa = &sagg[wib][0][0];
+        if (!solo) {
+            sa[0 * 33 + lane] = q0.x; sa[1 * 33 + lane] = q0.y; sa[2 * 33 + lane] = q0.z; sa[3 * 33 + lane] = q0.w;
+            sa[4 * 33 + lane] = q1.x; sa[5 * 33 + lane] = q1.y; sa[6 * 33 + lane] = q1.z; sa[7 * 33 + lane] = q1.w;
+            sa[8 * 33 + lane] = qc;
+        }
+        __syncwarp();
+        if (!solo && lane == leader) {
+            unsigned rest = peers & (peers - 1u);     // the other lanes of the group
+            while (rest) {
+                const int p = __ffs(rest) - 1;
+                rest &= rest - 1u;
+                q0.x += sa[0 * 33 + p]; q0.y += sa[1 * 33 + p]; q0.z += sa[2 * 33 + p]; q0.w += sa[3 * 33 + p];
+                q1.x += sa[4 * 33 + p]; q1.y += sa[5 * 33 + p]; q1.z += sa[6 * 33 + p]; q1.w += sa[7 * 33 + p];
+                qc += sa[8 * 33 + p];
+            }
+        }
+        __syncwarp();                                 // the next step rewrites the staging
+        if (valid && lane == leader) grad_red(a, ri, q0, q1, qc);
+    }
+    if (inside && __float_as_uint(T) != __float_as_uint(c.Tf)) atomicOr(&a.status->error_bits, 8u);
+}
+
 template <int HEAD>
 cudaError_t launch_head(const PipeArgs& a, bool bwd, size_t smem, cudaStream_t s)
 {
@@ -592,6 +748,10 @@ cudaError_t launch_head(const PipeArgs& a, bool bwd, size_t smem, cudaStream_t s
     cudaError_t e;
     if (bwd) {
         if ((e = ensure_smem_limit(k_render<HEAD, true>, smem, set_bwd, 64)) != cudaSuccess) return e;
+        if (a.blist) {
+            k_render_bwd_list<<<a.total_tiles * kBlocksPerTile, 32 * kRenderWarps, 0, s>>>(a);
+            note_launches(1);
+        }
         k_render<HEAD, true><<<a.total_tiles * kBlocksPerTile, 32 * kRenderWarps, smem, s>>>(a);
         note_launches(1);
     } else {
@@ -623,6 +783,7 @@ __device__ __forceinline__ void flat_init(const PipeArgs& a, const ViewDesc& V, 
     c.w = to_w(V, c.yc);
     c.n = ray_norm(c.u, c.w);
     c.pix = (pxi < V.W && pyi < V.H) ? V.pix_off + (long long)pyi * V.W + pxi : -1;
+    c.bl = 0;                    // the flat orders store no blend order
     c.g0 = c.g1 = c.g2 = c.gz = c.gbg = 0.f;
     c.Cf0 = c.Cf1 = c.Cf2 = c.Zf = c.Tf = 0.f;
 }
@@ -658,7 +819,8 @@ __global__ void __launch_bounds__(256) k_render_flat(PipeArgs a)
         const int m = (lo + hi + 1) >> 1;
         if (a.views[m].tile_off <= gtile) lo = m; else hi = m - 1;
     }
-    const ViewDesc& V = a.views[lo];
+    // a local copy: read through a reference, its fields would be reloaded after every store
+    const ViewDesc V = a.views[lo];
     const int tile = gtile - V.tile_off;
     const int tx = tile % V.tiles_x, ty = tile / V.tiles_x;
     const int pxi = tx * kTile + (threadIdx.x & 15), pyi = ty * kTile + (threadIdx.x >> 4);

@@ -63,6 +63,9 @@ class RenderParams:
     mode: int = MODE_HIER
     window_k: int = 16
     flags: int = 0
+    # ids stored per pixel by a forward that a backward follows (the backward walks them instead
+    # of replaying the queues; pixels that blend more are replayed): 4 * blend_cap bytes a pixel
+    blend_cap: int = 192
 
     def validate(self) -> None:
         if self.tail < 64 or self.tail % 32 != 0:

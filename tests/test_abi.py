@@ -32,7 +32,7 @@ def test_every_declared_symbol_is_exported(lib):
     for name in declared:
         assert hasattr(lib, name), name
     assert sorted(N.EXPORTS) == declared
-    assert lib.stp_version() == 0x000200
+    assert lib.stp_version() == 0x000300
 
 
 def test_workspace_layout_is_consistent(lib):
@@ -47,8 +47,18 @@ def test_workspace_layout_is_consistent(lib):
     assert all(v % 256 == 0 for v, _ in offs)
     assert d["total"] > d["grad_geom"] >= d["dbg_hash"] > d["dbg_nblend"]
     assert d["sorted_keys"] in (d["keys"], d["keys_alt"])
+    # stored blend order: blend_cap ids for each of the 256 lanes of every tile, one count a pixel
+    assert d["blend_count"] >= d["blend_ids"] + 256 * 256 * prm.blend_cap * 4
+    assert d["total"] >= d["blend_count"] + 256 * 256 * 4
     size = lib.stp_workspace_size(sc.n, C.cast(N.cameras_array(cams), C.c_void_p), 1, C.byref(p))
     assert size == d["total"]
+    # no stored order without the backward flag, with blend_cap 0 or outside the HIER order
+    for flags, cap, mode in ((0, 192, I.MODE_HIER), (N.FLAG_BACKWARD, 0, I.MODE_HIER),
+                             (N.FLAG_BACKWARD, 192, I.MODE_GLOBAL)):
+        q = N.params_struct(prm, flags)
+        q.blend_cap, q.mode = cap, mode
+        Lq = N.layout(sc.n, cams, q)
+        assert Lq.blend_ids == 0 and Lq.blend_count == 0
     # several views of mixed sizes: tiles and pixels add up, key bits grow with the tile count
     cams4 = I.orbit_cameras(5, 15.0, 2.0, I.C4_SIZES, 50.0)
     L4 = N.layout(1000, cams4, N.params_struct(I.RenderParams()))
@@ -60,6 +70,7 @@ def test_workspace_layout_is_consistent(lib):
     ("tail", 48, N.STP_ERR_ARG), ("tail", 80, N.STP_ERR_ARG), ("mid", 6, N.STP_ERR_ARG),
     ("mid", 10, N.STP_ERR_ARG), ("head", 5, N.STP_ERR_NOT_SUPPORTED), ("lb_threshold", 0, N.STP_ERR_ARG),
     ("eps_o", 0.0, N.STP_ERR_ARG), ("mode", 7, N.STP_ERR_ARG), ("mode", -1, N.STP_ERR_ARG), ("max_entries", -1, N.STP_ERR_ARG),
+    ("blend_cap", -1, N.STP_ERR_ARG), ("blend_cap", 4097, N.STP_ERR_ARG),
 ])
 def test_bad_parameters_rejected_on_host(lib, field, value, code):
     sc, cams, prm = I.plain_forward_workload()

@@ -261,10 +261,22 @@ def test_full_hd_3m_sampled_tiles_match_oracle(oracle):
     assert st.error_bits == 0
 
 
-def test_backward_matches_oracle_adjoint(oracle):
+def strip_max(nbl: np.ndarray) -> np.ndarray:
+    """Largest per-pixel value of every 8x4 pixel strip (the pixels of one Render warp)."""
+    H, W = nbl.shape
+    pad = np.zeros(((H + 3) // 4 * 4, (W + 7) // 8 * 8), nbl.dtype)
+    pad[:H, :W] = nbl
+    return pad.reshape(pad.shape[0] // 4, 4, pad.shape[1] // 8, 8).max(axis=(1, 3))
+
+
+@pytest.mark.parametrize("cap", [0, 8, 192])
+def test_backward_matches_oracle_adjoint(oracle, cap):
     """Sec. 3.5 backward against the FP64 adjoint on the 512-Gaussian 64x64 case. The loss
-    weights are zero on undecided pixels, so both sides differentiate the same blend order."""
+    weights are zero on undecided pixels, so both sides differentiate the same blend order.
+    blend_cap 0 replays the queues everywhere, 192 walks the stored order everywhere, and 8
+    mixes the two (warps with a pixel past 8 blends replay)."""
     sc, _, cam, prm = I.fd_subcase()
+    prm = dataclasses.replace(prm, blend_cap=cap)
     rng = np.random.default_rng(4)
     with oracle.OracleRun(sc, cam, prm, record=True) as r:
         ora = r.render()
@@ -281,6 +293,9 @@ def test_backward_matches_oracle_adjoint(oracle):
                 torch.from_numpy(wz.reshape(-1).astype(np.float32)).cuda(), grads)
     torch.cuda.synchronize()
     assert rr.status().error_bits == 0
+    if cap == 8:
+        over = strip_max(rr.debug_stats()[0].cpu().numpy().reshape(cam.height, cam.width)) > cap
+        assert over.any() and not over.all()
     for k in R.FIELDS:
         a = grads[k].cpu().numpy().astype(np.float64).ravel()
         b = adj[k].ravel()
@@ -288,6 +303,38 @@ def test_backward_matches_oracle_adjoint(oracle):
         cos = a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30)
         print(k, "rel-L2 %.3g cos %.8f" % (rel, cos))
         assert rel <= 1e-3 and cos >= 0.9999, k
+
+
+def test_stored_blend_order_backward_equals_replay():
+    """The backward over the stored blend order and the queue replay differentiate the same
+    sequence: on 60k clustered Gaussians in three views (colour and depth losses) the gradients
+    at blend_cap 192 (stored order everywhere) and 4 (mixed) equal those at 0 (replay only) up
+    to the order of float atomics, and the recomputed final T matches the forward's bit for
+    bit (no error bit 8)."""
+    sc = I.cluster_scene(60000, 81, nclusters=8, centre_range=1.5, scale_range=(0.003, 0.3))
+    cams = I.orbit_cameras(3, 6.0, 1.0, [(320, 240), (256, 256), (200, 120)], 50.0)
+    g = R.scene_to_device(sc)
+    P = sum(c.num_pixels for c in cams)
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    d_rgb = torch.randn((P, 3), device="cuda", generator=gen) / P
+    d_dep = torch.randn((P,), device="cuda", generator=gen) / P
+    res, frac = {}, {}
+    for cap in (0, 4, 192):
+        r = R.Renderer(sc.n, cams, I.RenderParams(blend_cap=cap), backward=True, debug=True)
+        r.forward(g)
+        grads = {k: torch.zeros_like(g[k]) for k in R.FIELDS}
+        r.backward(g, d_rgb, d_dep, grads)
+        torch.cuda.synchronize()
+        assert r.status().error_bits == 0, cap
+        res[cap] = {k: v.cpu().numpy().astype(np.float64).ravel() for k, v in grads.items()}
+        frac[cap] = np.mean(np.concatenate([(strip_max(x.cpu().numpy()) > cap).ravel()
+                                            for x in r.split(r.debug_stats()[0])]))
+    assert 0.0 < frac[4] < 1.0 and frac[192] == 0.0     # mixed at 4, no replay at 192
+    for cap in (4, 192):
+        for k in R.FIELDS:
+            a, b = res[cap][k], res[0][k]
+            rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+            assert rel <= 1e-4, (cap, k, rel)
 
 
 def test_partitioned_sort_equals_global_radix_sort():
