@@ -43,6 +43,9 @@ FP32_LANES_PER_SM = 128
 # t_opt at a 4x4 or 2x2 box; alpha + t_opt at a pixel)
 FLOP_PER_SUBTILE_EVAL, FLOP_PER_QUAD_EVAL, FLOP_PER_PIXEL_EVAL = 80, 80, 45
 FLOP_PER_BLEND_GRAD = 40
+# backward over the stored blend order, per blend: alpha recomputed at the pixel (G2, exp,
+# opacity) with the colour and transmittance updates; then the gradient terms above
+FLOP_PER_BLEND_EVAL = 28
 
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "render_traffic_fullhd_3m_16views.md")
@@ -506,8 +509,9 @@ def main():
     peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved = flops / (render_ms * 1e-3) / 1e12
     bwd_render_ms = float(bwd_stage[6])
-    # backward Render: the forward's decisions again plus, per blend, the gradient terms
-    bflops = flops + FLOP_PER_BLEND_GRAD * cnt[3]
+    # backward Render: per blend of the stored order, alpha again plus the gradient terms (the
+    # few warps with a pixel past blend_cap replay the queues inside the same stage time)
+    bflops = (FLOP_PER_BLEND_EVAL + FLOP_PER_BLEND_GRAD) * cnt[3]
     bachieved = bflops / (bwd_render_ms * 1e-3) / 1e12
 
     line = {
@@ -534,11 +538,13 @@ def main():
                      "work_units": {"subtile_evals": cnt[0], "subtile_survivors": cnt[1], "quad_evals": cnt[2],
                                     "blends": cnt[3], "pixel_evals": cnt[4]},
                      "peak_basis": "FP32 FMA issue: %d SMs x 128 lanes x 2 x %.0f MHz" % (props.multi_processor_count, sm_max)},
-        "roofline_backward": {"bound": "alu", "kernel": "k_render (backward replay)", "achieved": bachieved,
+        "roofline_backward": {"bound": "alu", "kernel": "k_render_bwd_list (stored blend order)", "achieved": bachieved,
                               "peak": peak, "unit": "TFLOP/s", "frac": bachieved / peak,
-                              "traffic": measured_traffic("k_render<4,1>", scene.n, V),
-                              "note": "the replay's decision FLOPs plus %d FLOP per blend for the gradient "
-                                      "terms" % FLOP_PER_BLEND_GRAD},
+                              "traffic": measured_traffic("k_render_bwd_list", scene.n, V),
+                              "note": "%d FLOP per blend (alpha again, %d; gradient terms, %d); the kernel is "
+                                      "limited by its L2 float reductions, not by FP32 issue"
+                                      % (FLOP_PER_BLEND_EVAL + FLOP_PER_BLEND_GRAD, FLOP_PER_BLEND_EVAL,
+                                         FLOP_PER_BLEND_GRAD)},
     }
     # the paper's own figure, for context only (other GPU, other scenes: not a baseline)
     line["paper_context"] = {

@@ -176,6 +176,8 @@ typedef struct {                 /* byte offsets of workspace regions (for inspe
                                     order (flag 64, HIER, blend_cap > 0), else 0: slot k of the
                                     warp's lane l (pixel of its 8x4 strip) at (w*cap + k)*32 + l */
     size_t blend_count;          /* [total pixels] uint32 blends per pixel (with blend_ids)  */
+    size_t replay_warps;         /* [total tiles * 8] uint32 backward work list: tile warps with
+                                    a pixel past blend_cap, replayed (with blend_ids)        */
     size_t total;                /* total bytes                                              */
     int64_t capacity;            /* sort-entry capacity                                      */
     int64_t total_tiles, total_pixels;

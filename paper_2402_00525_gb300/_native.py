@@ -73,7 +73,7 @@ _LAYOUT_SIZE_FIELDS = ["status", "views", "scenes", "geom", "color", "rect", "co
                        "scan_partials", "keys", "vals", "keys_alt", "vals_alt", "sorted_keys",
                        "sorted_vals", "ranges", "tfinal", "pix_state", "scratch", "dbg_nblend",
                        "dbg_hash", "dbg_delta", "grad_geom", "dbg_trace", "tile_counts", "tile_offsets",
-                       "tile_cursor", "tile_partials", "blend_ids", "blend_count", "total"]
+                       "tile_cursor", "tile_partials", "blend_ids", "blend_count", "replay_warps", "total"]
 
 
 class Layout(C.Structure):

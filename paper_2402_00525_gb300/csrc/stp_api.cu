@@ -223,10 +223,11 @@ void make_plan(const int64_t* ns, const int32_t* vps, int32_t nscenes, const stp
     L.tile_partials = take(stp::scan_partials_count(tiles) * 8);
     L.grad_geom = 0;
     if (p->flags & kFlagBackward) L.grad_geom = take((size_t)P.m * stp::kGradStride * 4);
-    L.blend_ids = L.blend_count = 0;
+    L.blend_ids = L.blend_count = L.replay_warps = 0;
     if ((p->flags & kFlagBackward) && p->mode == STP_MODE_HIER && p->blend_cap > 0) {
         L.blend_ids = take((size_t)tiles * 256 * (size_t)p->blend_cap * 4);
         L.blend_count = take((size_t)pixels * 4);
+        L.replay_warps = take((size_t)tiles * 8 * 4);
     }
     L.dbg_trace = 0;
     if (p->flags & kFlagTrace) L.dbg_trace = take((size_t)pixels * stp::kTraceLen * 4);
@@ -282,6 +283,7 @@ stp::PipeArgs make_args(const stp_params* p, const Plan& P, void* ws)
     a.grad_geom = L.grad_geom ? (float*)(b + L.grad_geom) : nullptr;
     a.blist = L.blend_ids ? (uint32_t*)(b + L.blend_ids) : nullptr;
     a.blist_count = L.blend_count ? (uint32_t*)(b + L.blend_count) : nullptr;
+    a.replay_warps = L.replay_warps ? (uint32_t*)(b + L.replay_warps) : nullptr;
     a.blend_cap = L.blend_ids ? p->blend_cap : 0;
     a.dbg_trace = L.dbg_trace ? (int*)(b + L.dbg_trace) : nullptr;
     a.partitioned = (p->flags & kFlagGlobalSort) ? 0 : 1;
@@ -420,6 +422,9 @@ stp_status backward_impl(const stp_gaussians* scenes, int32_t nscenes, const int
     prof_mark(5, s);
     if ((e = cudaMemsetAsync(a.grad_geom, 0, (size_t)P.m * stp::kGradStride * 4, s)) != cudaSuccess)
         return cuda_fail(e, "clear gradient scratch");
+    // empty replay queue (the stored-order kernel fills it)
+    if (a.blist && (e = cudaMemsetAsync(&a.status->replay_n, 0, 2 * sizeof(unsigned int), s)) != cudaSuccess)
+        return cuda_fail(e, "clear replay queue");
     prof_mark(6, s);
     if ((e = stp::launch_render(a, true, s)) != cudaSuccess) return cuda_fail(e, "backward render");
     prof_mark(7, s);

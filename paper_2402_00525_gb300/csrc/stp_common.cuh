@@ -34,6 +34,8 @@ struct Status {
     unsigned long long num_entries;
     unsigned long long capacity;
     unsigned long long counters[5];   // debug counters (see stp_api.cu)
+    unsigned int replay_n;        // backward: warps queued for the replay (pixels past blend_cap)
+    unsigned int replay_next;     // backward: next queued warp to take
 };
 
 // ---------------------------------------------------------------- per-view constants

@@ -67,6 +67,7 @@ struct PipeArgs {
     // blend_cap x 32 ids, slot k of lane l at (warp * blend_cap + k) * 32 + l; null = replay
     uint32_t* blist;
     uint32_t* blist_count;   // [total_pixels] blends of the pixel (may exceed blend_cap)
+    uint32_t* replay_warps;  // [total_tiles * 8] tile warps (gtile * 8 + warp) the backward replays
     int blend_cap;
 };
 

@@ -31,6 +31,8 @@
 // t_min is not blended and the ray stops). The backward kernel is the same code with BWD =
 // true: it recomputes the identical decisions (shared rounding of the decision arithmetic)
 // and, at each blend, forms the gradients with the suffix colour C - C_i and T_N / T_i.
+#include <algorithm>
+
 #include <cuda_runtime.h>
 
 #include "stp_common.cuh"
@@ -417,19 +419,15 @@ __device__ __forceinline__ void merge_tail(const uint2* src, int ne, const uint2
     }
 }
 
+// One warp's share of a tile (two 4x4 subtiles) through the whole hierarchical Render: the
+// forward, or its replay for the backward. tailb is the warp's shared-memory queue area.
 template <int HEAD, bool BWD>
-__global__ void __launch_bounds__(32 * kRenderWarps, (render_min_blocks<HEAD, BWD>())) k_render(PipeArgs a)
+__device__ __forceinline__ void render_warp(const PipeArgs& a, const int gtile, const int warp, const int lane,
+                                            uint2* tailb)
 {
-    extern __shared__ uint2 sm[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int warp = (int)(blockIdx.x % kBlocksPerTile) * kRenderWarps + wib;   // warp of the tile
     const int TAIL = a.tail, MID = a.mid;
-    uint2* tailb = sm + wib * (4 * TAIL + 64 + 8 * MID);
     uint2* stage = tailb + 4 * TAIL;
     uint2* midb = stage + 64;
-    if (a.status->error_bits & 1u) return;
-
-    const int gtile = (int)(blockIdx.x / kBlocksPerTile);
     int lo = 0, hi = a.nviews - 1;
     while (lo < hi) {
         const int m = (lo + hi + 1) >> 1;
@@ -466,11 +464,6 @@ __global__ void __launch_bounds__(32 * kRenderWarps, (render_min_blocks<HEAD, BW
     c.n = ray_norm(c.u, c.w);
     c.pix = inside ? V.pix_off + (long long)pyi * W + pxi : -1;
     c.bl = ((long long)(gtile * 8 + warp) * a.blend_cap) * 32 + lane;
-    if (BWD && a.blist) {
-        // with a stored blend order only the warps with a pixel past its capacity replay
-        const uint32_t nb = inside ? a.blist_count[c.pix] : 0u;
-        if (!__any_sync(kFull, nb > (uint32_t)a.blend_cap)) return;
-    }
     c.g0 = c.g1 = c.g2 = c.gz = c.gbg = 0.f;
     c.Cf0 = c.Cf1 = c.Cf2 = c.Zf = c.Tf = 0.f;
     if (BWD && inside) {
@@ -619,11 +612,43 @@ __global__ void __launch_bounds__(32 * kRenderWarps, (render_min_blocks<HEAD, BW
     }
 }
 
+template <int HEAD, bool BWD>
+__global__ void __launch_bounds__(32 * kRenderWarps, (render_min_blocks<HEAD, BWD>())) k_render(PipeArgs a)
+{
+    extern __shared__ uint2 sm[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (a.status->error_bits & 1u) return;
+    render_warp<HEAD, BWD>(a, (int)(blockIdx.x / kBlocksPerTile), (int)(blockIdx.x % kBlocksPerTile) * kRenderWarps + wib,
+                           lane, sm + wib * (4 * a.tail + 64 + 8 * a.mid));
+}
+
+// Backward replay of the tile warps the stored-order kernel queued (a pixel past blend_cap):
+// a grid of resident blocks whose warps take queued tile warps one at a time, so that the
+// few replays cost no launch of a block per tile.
+template <int HEAD>
+__global__ void __launch_bounds__(32 * kRenderWarps, (render_min_blocks<HEAD, true>())) k_render_replay(PipeArgs a)
+{
+    extern __shared__ uint2 sm[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (a.status->error_bits & 1u) return;
+    const unsigned n = a.status->replay_n;
+    uint2* tailb = sm + wib * (4 * a.tail + 64 + 8 * a.mid);
+    for (;;) {
+        unsigned item = 0;
+        if (lane == 0) item = atomicAdd(&a.status->replay_next, 1u);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= n) break;
+        const uint32_t w = a.replay_warps[item];
+        render_warp<HEAD, true>(a, (int)(w >> 3), (int)(w & 7), lane, tailb);
+        __syncwarp();
+    }
+}
+
 // Backward over the stored blend order (Sec. 3.5). The forward Render recorded, per pixel, the
 // ids it blended in blend order, so the gradients need no replay of the queues: each thread
 // walks its pixel's ids front to back, recomputes alpha (and, for a depth gradient, t_opt) from
 // the record with the forward's own rounding, and forms the same terms as the replay. Warps with
-// a pixel past the capacity are left to the replay kernel, which returns at once for all others.
+// a pixel past the capacity are queued for the replay kernel.
 // Same block shape and pixel mapping as the forward. The product of the recomputed (1 - alpha)
 // must reproduce the forward's final T bit for bit; a pixel where it does not sets error bit 8.
 //
@@ -663,7 +688,10 @@ __global__ void __launch_bounds__(32 * kRenderWarps, STP_BWD_LIST_MIN_BLOCKS * 4
     c.pix = inside ? V.pix_off + (long long)pyi * V.W + pxi : -1;
     c.bl = ((long long)(gtile * 8 + warp) * a.blend_cap) * 32 + lane;
     const uint32_t nb = inside ? a.blist_count[c.pix] : 0u;
-    if (__any_sync(kFull, nb > (uint32_t)a.blend_cap)) return;     // replayed
+    if (__any_sync(kFull, nb > (uint32_t)a.blend_cap)) {           // queued for the replay
+        if (lane == 0) a.replay_warps[atomicAdd(&a.status->replay_n, 1u)] = (uint32_t)(gtile * 8 + warp);
+        return;
+    }
     c.g0 = c.g1 = c.g2 = c.gz = c.gbg = 0.f;
     c.Cf0 = c.Cf1 = c.Cf2 = c.Zf = c.Tf = 0.f;
     if (inside) {
@@ -749,11 +777,20 @@ cudaError_t launch_head(const PipeArgs& a, bool bwd, size_t smem, cudaStream_t s
     if (bwd) {
         if ((e = ensure_smem_limit(k_render<HEAD, true>, smem, set_bwd, 64)) != cudaSuccess) return e;
         if (a.blist) {
+            static int set_rep[64];
+            if ((e = ensure_smem_limit(k_render_replay<HEAD>, smem, set_rep, 64)) != cudaSuccess) return e;
+            int dev = 0, nsm = 0;
+            if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+            if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+            const long long resident = (long long)nsm * render_min_blocks<HEAD, true>();
+            const unsigned grid = (unsigned)std::min<long long>(resident, (long long)a.total_tiles * kBlocksPerTile);
             k_render_bwd_list<<<a.total_tiles * kBlocksPerTile, 32 * kRenderWarps, 0, s>>>(a);
+            k_render_replay<HEAD><<<grid, 32 * kRenderWarps, smem, s>>>(a);
+            note_launches(2);
+        } else {
+            k_render<HEAD, true><<<a.total_tiles * kBlocksPerTile, 32 * kRenderWarps, smem, s>>>(a);
             note_launches(1);
         }
-        k_render<HEAD, true><<<a.total_tiles * kBlocksPerTile, 32 * kRenderWarps, smem, s>>>(a);
-        note_launches(1);
     } else {
         if ((e = ensure_smem_limit(k_render<HEAD, false>, smem, set_fwd, 64)) != cudaSuccess) return e;
         k_render<HEAD, false><<<a.total_tiles * kBlocksPerTile, 32 * kRenderWarps, smem, s>>>(a);

@@ -49,7 +49,8 @@ def test_workspace_layout_is_consistent(lib):
     assert d["sorted_keys"] in (d["keys"], d["keys_alt"])
     # stored blend order: blend_cap ids for each of the 256 lanes of every tile, one count a pixel
     assert d["blend_count"] >= d["blend_ids"] + 256 * 256 * prm.blend_cap * 4
-    assert d["total"] >= d["blend_count"] + 256 * 256 * 4
+    assert d["replay_warps"] >= d["blend_count"] + 256 * 256 * 4
+    assert d["total"] >= d["replay_warps"] + 256 * 8 * 4
     size = lib.stp_workspace_size(sc.n, C.cast(N.cameras_array(cams), C.c_void_p), 1, C.byref(p))
     assert size == d["total"]
     # no stored order without the backward flag, with blend_cap 0 or outside the HIER order
@@ -58,7 +59,7 @@ def test_workspace_layout_is_consistent(lib):
         q = N.params_struct(prm, flags)
         q.blend_cap, q.mode = cap, mode
         Lq = N.layout(sc.n, cams, q)
-        assert Lq.blend_ids == 0 and Lq.blend_count == 0
+        assert Lq.blend_ids == 0 and Lq.blend_count == 0 and Lq.replay_warps == 0
     # several views of mixed sizes: tiles and pixels add up, key bits grow with the tile count
     cams4 = I.orbit_cameras(5, 15.0, 2.0, I.C4_SIZES, 50.0)
     L4 = N.layout(1000, cams4, N.params_struct(I.RenderParams()))
