@@ -655,13 +655,17 @@ __global__ void __launch_bounds__(32 * kRenderWarps, (render_min_blocks<HEAD, tr
 // Neighbouring pixels often blend the same Gaussian at the same step (on 16 Full-HD views of 3M
 // Gaussians a step of a warp holds about 11 distinct ids over 27 live lanes), so the lanes of a
 // step that share an id sum their nine terms in shared memory and one of them issues the
-// reductions: 40% of the per-lane reductions, which dominate this kernel's L2 traffic.
+// reductions: 40% of the per-lane reductions, which dominate this kernel's L2 traffic. The
+// staging is vectorised (three 16-byte stores per lane, three loads per peer): with nine scalar
+// accesses each the shared-memory pipe, not L2, was the limit (ncu: L1 at 97% of peak).
 #ifndef STP_BWD_LIST_MIN_BLOCKS
 #define STP_BWD_LIST_MIN_BLOCKS 8
 #endif
 __global__ void __launch_bounds__(32 * kRenderWarps, STP_BWD_LIST_MIN_BLOCKS * 4 / kRenderWarps) k_render_bwd_list(PipeArgs a)
 {
-    __shared__ float sagg[kRenderWarps][9][33];   // [warp][term][lane], padded: conflict-free
+    // per lane (q0, q1, qc) as three float4: 16-byte stores at a 48-byte lane stride are
+    // conflict-free, and a group leader reads a peer's terms with three loads
+    __shared__ __align__(16) float sagg[kRenderWarps][32 * 12];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int warp = (int)(blockIdx.x % kBlocksPerTile) * kRenderWarps + wib;   // warp of the tile
     if (a.status->error_bits & 1u) return;
@@ -746,11 +750,12 @@ __global__ void __launch_bounds__(32 * kRenderWarps, STP_BWD_LIST_MIN_BLOCKS * 4
         const unsigned peers = __match_any_sync(kFull, id);
         const bool solo = peers == (1u << lane);
         const int leader = __ffs(peers) - 1;
-        float* sa = &sagg[wib][0][0];
+        float* sa = &sagg[wib][0];
         if (!solo) {
-            sa[0 * 33 + lane] = q0.x; sa[1 * 33 + lane] = q0.y; sa[2 * 33 + lane] = q0.z; sa[3 * 33 + lane] = q0.w;
-            sa[4 * 33 + lane] = q1.x; sa[5 * 33 + lane] = q1.y; sa[6 * 33 + lane] = q1.z; sa[7 * 33 + lane] = q1.w;
-            sa[8 * 33 + lane] = qc;
+            float4* me = reinterpret_cast<float4*>(sa + lane * 12);
+            me[0] = q0;
+            me[1] = q1;
+            me[2] = make_float4(qc, 0.f, 0.f, 0.f);
         }
         __syncwarp();
         if (!solo && lane == leader) {
@@ -758,9 +763,11 @@ __global__ void __launch_bounds__(32 * kRenderWarps, STP_BWD_LIST_MIN_BLOCKS * 4
             while (rest) {
                 const int p = __ffs(rest) - 1;
                 rest &= rest - 1u;
-                q0.x += sa[0 * 33 + p]; q0.y += sa[1 * 33 + p]; q0.z += sa[2 * 33 + p]; q0.w += sa[3 * 33 + p];
-                q1.x += sa[4 * 33 + p]; q1.y += sa[5 * 33 + p]; q1.z += sa[6 * 33 + p]; q1.w += sa[7 * 33 + p];
-                qc += sa[8 * 33 + p];
+                const float4* o = reinterpret_cast<const float4*>(sa + p * 12);
+                const float4 a0 = o[0], a1 = o[1];
+                q0.x += a0.x; q0.y += a0.y; q0.z += a0.z; q0.w += a0.w;
+                q1.x += a1.x; q1.y += a1.y; q1.z += a1.z; q1.w += a1.w;
+                qc += o[2].x;
             }
         }
         __syncwarp();                                 // the next step rewrites the staging
