@@ -444,6 +444,26 @@ def main():
     del single, souts
     torch.cuda.empty_cache()
 
+    # ---------------------------------------------------------------- forward only (serving)
+    # The training forward above also stores each pixel's blend order for the backward; a
+    # renderer without the backward flag stores nothing beyond the images.
+    fo = R.Renderer(scene.n, cams, prm, capacity=rnd.capacity)
+    fout = (torch.empty_like(out[0]), torch.empty_like(out[1]), torch.empty_like(out[2]))
+    for _ in range(max(args.warmup, 1)):
+        fo.forward(g, out=fout, check=False)
+    torch.cuda.synchronize()
+    fo_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for e0, e1 in fo_ev:
+        e0.record()
+        fo.forward(g, out=fout, check=False)
+        e1.record()
+    torch.cuda.synchronize()
+    assert fo.status().error_bits == 0
+    fo_ms = max_over_ranks([float(np.mean([e0.elapsed_time(e1) for e0, e1 in fo_ev]))], dist, "cuda")[0]
+    fo_same = bool(torch.equal(fout[0], out[0]) and torch.equal(fout[1], out[1]))
+    del fo, fout
+    torch.cuda.empty_cache()
+
     # ---------------------------------------------------------------- end to end (host buffers)
     # A serving loop through the public API: every step copies its scene in from pinned host
     # memory and its rgb + depth out to pinned host memory. Two buffer sets and two copy
@@ -526,6 +546,9 @@ def main():
                      "backward": {n: round(float(x), 4) for n, x in zip(N.STAGE_NAMES, bwd_stage)}},
         "per_view": {"fwd_mpix_s": total_px / world / (pv_ms * 1e-3) / 1e6, "fwd_ms_16_views": pv_ms,
                      "batched_speedup": pv_ms / fwd_ms, "identical_to_batched": bool(same)},
+        "forward_only": {"mpix_s": job_mpix_per_s(P, world, fo_ms), "fwd_ms": fo_ms,
+                         "batched_speedup_vs_per_view": pv_ms / fo_ms, "identical_to_training_forward": fo_same,
+                         "note": "batched forward without the backward flag (no stored blend order)"},
         "entries_per_step": entries,
         "e2e": {"value": e2e_val, "unit": "Mpix/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_ms, "steps": n_e2e, "images_match_device": bool(same_e2e),

@@ -205,8 +205,9 @@ __device__ __forceinline__ void blend(const PipeArgs& a, const ViewDesc& V, Px<H
         grad_terms(a, c, ri, col, __ldg(a.geom + kRecFloat4 * ri), alpha, val, t, s.T, s.C0, s.C1, s.C2, s.Z, q0, q1, qc);
         grad_red(a, ri, q0, q1, qc);
     }
-    // the stored blend order (backward without replay): the first blend_cap ids of the pixel
-    if (!BWD && a.blist && s.nbl < (uint32_t)a.blend_cap) a.blist[c.bl + 32ll * s.nbl] = id;
+    // the stored blend order (backward without replay): the first blend_cap ids of the pixel,
+    // stored and later loaded with the evict-first hint (each id is touched once either way)
+    if (!BWD && a.blist && s.nbl < (uint32_t)a.blend_cap) __stcs(a.blist + c.bl + 32ll * s.nbl, id);
     if (!BWD && a.dbg_trace && s.nbl < (uint32_t)kTraceLen) a.dbg_trace[c.pix * kTraceLen + s.nbl] = (int)id;
     if (!BWD && a.dbg_hash) {          // debug statistics: order hash and sort error
         s.hash = s.hash * kHashMul + (unsigned long long)(id + 1u);
@@ -712,13 +713,13 @@ __global__ void __launch_bounds__(32 * kRenderWarps, STP_BWD_LIST_MIN_BLOCKS * 4
     const uint32_t* ids = a.blist + c.bl;
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, Z = 0.f;
     const uint32_t nmax = __reduce_max_sync(kFull, nb);
-    uint32_t nxt = nb > 0 ? __ldg(ids) : 0u;
+    uint32_t nxt = nb > 0 ? __ldcs(ids) : 0u;
     // every lane runs the warp's longest list so that the steps stay aligned for the sharing
 #pragma unroll 1
     for (uint32_t k = 0; k < nmax; k++) {
         const bool valid = k < nb;
         const uint32_t id = valid ? nxt : 0xFFFFFFFFu;
-        if (k + 1 < nb) nxt = __ldg(ids + 32ll * (k + 1));
+        if (k + 1 < nb) nxt = __ldcs(ids + 32ll * (k + 1));
         const long long ri = V.rec_off + (valid ? id : 0u);
         float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0;
         float qc = 0.f;
