@@ -157,7 +157,8 @@ typedef struct {                 /* byte offsets of workspace regions (for inspe
     size_t keys, vals;           /* [capacity] uint64 / uint32 radix-sort buffer B           */
     size_t keys_alt, vals_alt;   /* [capacity] radix-sort buffer A (Duplicate output)        */
     size_t sorted_keys;          /* = keys or keys_alt: where the sorted (tile, depth) keys  */
-    size_t sorted_vals;          /*   and Gaussian ids end up                                */
+    size_t sorted_vals;          /*   and Gaussian ids end up (the per-tile sort writes the
+                                      keys only with STP_FLAG_DEBUG_STATS: Render reads ids) */
     size_t ranges;               /* [total tiles] uint2 [start, end) into the sorted pairs   */
     size_t tfinal;               /* [total pixels] float final transmittance                 */
     size_t pix_state;            /* [total pixels] float4 (colour without background, depth) */

@@ -20,6 +20,7 @@ constexpr int STP_MODE_HIER_ID = 0;              // stp_params.mode values (incl
 constexpr int STP_MODE_FULL_ID = 1;
 constexpr int STP_MODE_GLOBAL_ID = 2;
 constexpr int STP_MODE_WINDOW_ID = 3;
+constexpr int kFlagDebugStats = 32;              // debug outputs (also the per-tile sort's sorted keys)
 constexpr int kFlagNoTileCull = 512;             // ablation D: Duplicate keeps every rectangle tile
 constexpr int kFlagNoHierCull = 1024;            // ablation E: no culling at the 4x4 / 2x2 levels                   // scenes per launch sequence
 constexpr int kSceneAlign = 256;                 // first thread of each scene: multiple of this

@@ -386,8 +386,9 @@ __device__ bool bucket_plan(const unsigned long long* src, uint32_t n, uint32_t*
     return fullest <= (uint32_t)kBucketMax;
 }
 
-// Scatter src into its buckets in `scat`, then rank each word inside its bucket. With `keys`
-// set, the ranked words go straight to the output pair arrays; otherwise to ranked[].
+// Scatter src into its buckets in `scat`, then rank each word inside its bucket. With `vals`
+// set, the ranked words go straight to the output ids (and, with `keys` set too, to the
+// output keys); otherwise to ranked[].
 template <int NB>
 __device__ void bucket_rank(const unsigned long long* src, unsigned long long* scat, uint32_t n,
                             const uint32_t* bcnt, uint32_t* bcur, uint32_t kmin, unsigned long long span,
@@ -405,8 +406,8 @@ __device__ void bucket_rank(const unsigned long long* src, unsigned long long* s
         const uint32_t end = bcur[b], beg = end - bcnt[b];
         uint32_t r = beg;
         for (uint32_t j = beg; j < end; j++) r += scat[j] < x;
-        if (keys) {
-            keys[r] = hi | (x >> 32);
+        if (vals) {
+            if (keys) keys[r] = hi | (x >> 32);
             vals[r] = (uint32_t)x;
         } else {
             ranked[r] = x;
@@ -431,13 +432,15 @@ __global__ void __launch_bounds__(kSegThreads) k_tile_sort(PipeArgs a)
     unsigned long long* g0 = (unsigned long long*)a.dup_keys + off;   // placed words (buffer A)
     unsigned long long* g1 = (unsigned long long*)a.keys + off;   // partner (buffer B)
     const unsigned long long hi = (unsigned long long)t << 32;
+    // the Render reads only the ids; the (tile, depth) keys are written for inspection only
+    uint64_t* okeys = (a.flags & kFlagDebugStats) ? a.keys + off : nullptr;
     uint32_t kmin;
     unsigned long long span;
     if (n <= (uint32_t)kSegCap) {
         uint32_t* bcnt = reinterpret_cast<uint32_t*>(seg_smem + kSegCap);
         uint32_t* bcur = bcnt + kBucketsSmall;
         if (bucket_plan<kBucketsSmall>(g0, n, bcnt, bcur, red, kmin, span)) {
-            bucket_rank<kBucketsSmall>(g0, seg_smem, n, bcnt, bcur, kmin, span, hi, a.keys + off, a.vals + off, nullptr);
+            bucket_rank<kBucketsSmall>(g0, seg_smem, n, bcnt, bcur, kmin, span, hi, okeys, a.vals + off, nullptr);
             return;
         }
     } else {
@@ -449,7 +452,7 @@ __global__ void __launch_bounds__(kSegThreads) k_tile_sort(PipeArgs a)
             __syncthreads();
             for (uint32_t i = threadIdx.x; i < n; i += kSegThreads) {
                 const unsigned long long v = g0[i];
-                a.keys[off + i] = hi | (v >> 32);
+                if (okeys) okeys[i] = hi | (v >> 32);
                 a.vals[off + i] = (uint32_t)v;
             }
             return;
@@ -463,7 +466,7 @@ __global__ void __launch_bounds__(kSegThreads) k_tile_sort(PipeArgs a)
     seg_fix_ties(g0, (int)n);
     for (uint32_t i = threadIdx.x; i < n; i += kSegThreads) {
         const unsigned long long v = g0[i];
-        a.keys[off + i] = hi | (v >> 32);
+        if (okeys) okeys[i] = hi | (v >> 32);
         a.vals[off + i] = (uint32_t)v;
     }
 }

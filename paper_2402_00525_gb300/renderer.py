@@ -263,7 +263,8 @@ class Renderer:
         return self._region(self.layout.dbg_trace, P * N.TRACE_LEN, torch.int32).view(P, N.TRACE_LEN)
 
     def sorted_lists(self):
-        """(ranges [T,2] int32, sorted keys int64, sorted ids int32) of the last forward."""
+        """(ranges [T,2] int32, sorted keys int64, sorted ids int32) of the last forward. With
+        the per-tile sort (the default) the keys are written only by a debug renderer."""
         L = self.layout
         st = self.status()
         E = min(int(st.num_entries), self.capacity)

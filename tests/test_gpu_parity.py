@@ -117,7 +117,7 @@ def test_sorted_tile_lists_match_oracle(oracle):
     sc = I.cluster_scene(30000, 78, nclusters=8, centre_range=1.5, scale_range=(0.003, 0.2))
     cam = I.look_at((0.2, 0.4, -6), (0, 0, 0), (0, 1, 0), 320, 256, 50.0)
     prm = I.RenderParams()
-    gpu = gpu_render(sc, [cam], prm, debug=False)
+    gpu = gpu_render(sc, [cam], prm)
     ranges, keys, vals = [x.cpu().numpy() for x in gpu["renderer"].sorted_lists()]
     with oracle.OracleRun(sc, cam, prm) as r:
         start, ids, ts = r.tile_lists()
