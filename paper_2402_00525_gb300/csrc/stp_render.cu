@@ -1,4 +1,4 @@
-// stp_render.cu -- hierarchical sorted Render (forward) and its replay for the backward pass.
+// stp_render.cu -- hierarchical sorted Render (forward) and the backward over its blend order.
 //
 // StopThePop (arXiv 2402.00525) Sec. 3.4 "Hierarchically sorted rendering", Fig. "pipeline",
 // appendix B.4 "Render"; backward Sec. 3.5.
@@ -28,9 +28,15 @@
 //   * a pixel drops alpha < eps_O, computes t_opt on its own ray and inserts into its head;
 //     when the head holds more than HEAD entries the smallest is blended.
 // Blending is front to back with the 3DGS early-out (the Gaussian that would take T below
-// t_min is not blended and the ray stops). The backward kernel is the same code with BWD =
-// true: it recomputes the identical decisions (shared rounding of the decision arithmetic)
-// and, at each blend, forms the gradients with the suffix colour C - C_i and T_N / T_i.
+// t_min is not blended and the ray stops).
+//
+// Backward (Sec. 3.5): the gradients of a blend need the suffix colour C - C_i and T_N / T_i,
+// so the blends are visited front to back in the forward's order. A forward that a backward
+// follows stores each pixel's first blend_cap blended ids (4 bytes a blend), and
+// k_render_bwd_list walks them, recomputing alpha with the forward's rounding. A warp with a
+// pixel past blend_cap is queued and replayed: k_render_replay runs the forward code with
+// BWD = true, which recomputes the identical decisions and forms the same terms at each
+// blend. With blend_cap 0, k_render<HEAD, true> replays every warp (the paper's way).
 #include <algorithm>
 
 #include <cuda_runtime.h>
@@ -49,7 +55,8 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 // low occupancy, so each instantiation is given the resident-block count (register cap) that
 // measured fastest on 16 Full-HD views of 3M Gaussians with 4-warp blocks: HEAD <= 4 forward
 // 6 blocks (80 registers, 32.8 ms against 37.6 ms at 111 registers and 2 x 8-warp blocks),
-// backward 5 (96 registers, 54.8 ms against 59.8 ms); wider heads hold more registers.
+// backward replay 5 (96 registers, 54.8 ms against 59.8 ms when it replayed every warp); wider
+// heads hold more registers.
 // Build-time knobs: -DSTP_RENDER_WARPS=..., -DSTP_RENDER_MIN_BLOCKS_FWD / _BWD=... (HEAD <= 4),
 // -DSTP_RENDER_MIN_BLOCKS=... (all instantiations).
 #ifndef STP_RENDER_WARPS
