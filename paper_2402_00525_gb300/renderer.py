@@ -113,6 +113,7 @@ class Renderer:
         else:
             self.layout = N.layout(self.n, self.cams, self.p)
         self.capacity = int(self.layout.capacity)
+        self._fwd_ready = False          # the workspace holds no forward state yet
         self.ws = None
         torch.cuda.empty_cache() if self.device.type == "cuda" else None
         self.ws = torch.empty(int(self.layout.total), dtype=torch.uint8, device=self.device)
@@ -131,6 +132,7 @@ class Renderer:
         same = all(a.width == b.width and a.height == b.height for a, b in zip(cams, self.cams))
         self.cams = cams
         self._cams_arr = N.cameras_array(self.cams)
+        self._fwd_ready = False
         if not same:
             self.total_pixels = sum(c.width * c.height for c in self.cams)
             self.pixel_offsets = np.cumsum([0] + [c.width * c.height for c in self.cams])
@@ -174,6 +176,7 @@ class Renderer:
                                                 C.c_void_p(strm.cuda_stream)))
             self.last_status = st
             break
+        self._fwd_ready = True
         return rgb, depth, tfin
 
     def _scenes(self, g):
@@ -198,6 +201,9 @@ class Renderer:
         into grads (dict of tensors shaped like the inputs)."""
         if not (self.flags & N.FLAG_BACKWARD):
             raise RuntimeError("construct the Renderer with backward=True")
+        if not self._fwd_ready:
+            # the backward reads the forward's blend order, lists and records from the workspace
+            raise RuntimeError("backward needs a forward with the current workspace and cameras first")
         sc = self._scenes(g)
         gl = list(grads) if self.batched else [grads]
         if len(gl) != len(sc):

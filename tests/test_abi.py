@@ -177,3 +177,18 @@ def test_batched_render_checks_scene_pointers_before_launch(lib):
                                 C.cast(N.cameras_array(cams), C.c_void_p), 2, C.byref(p), C.c_void_p(256),
                                 1 << 40, C.c_void_p(256), C.c_void_p(256), None, None)
     assert rc == N.STP_ERR_ARG and "sh_degree" in N.last_error()
+
+
+def test_backward_before_forward_is_refused_on_the_host(lib):
+    """The backward reads the forward's state from the workspace; the front end refuses it on
+    a workspace no forward has filled (fresh, regrown, or after new image sizes) before any
+    library call. A CPU workspace suffices: nothing is launched."""
+    torch = pytest.importorskip("torch")
+    from paper_2402_00525_gb300 import renderer as R
+    sc, cams, prm = I.plain_forward_workload()
+    r = R.Renderer(sc.n, cams, prm, device="cpu", backward=True)
+    with pytest.raises(RuntimeError, match="forward"):
+        r.backward({}, torch.zeros(1), None, {})
+    r2 = R.Renderer(sc.n, cams, prm, device="cpu")
+    with pytest.raises(RuntimeError, match="backward=True"):
+        r2.backward({}, torch.zeros(1), None, {})
