@@ -74,6 +74,7 @@ def lib():
         L.orc_get_preprocess.argtypes = [vp] + [vp] * 11
         L.orc_get_tile_lists.argtypes = [vp, vp, vp, vp]
         L.orc_render.argtypes = [vp] + [vp] * 9 + [C.c_int32, vp]
+        L.orc_render_ex.argtypes = [vp] + [vp] * 9 + [C.c_int32, vp, vp, C.c_double]
         L.orc_backward.argtypes = [vp, C.POINTER(_Scene)] + [vp] * 11
         L.orc_schedule_synthetic.restype = C.c_int32
         L.orc_schedule_synthetic.argtypes = [C.c_int32, vp, vp, C.c_double, C.c_int32, C.c_int32,
@@ -232,17 +233,20 @@ class OracleRun:
         lib().orc_get_tile_lists(self.h, _ptr(start), _ptr(ids), _ptr(ts))
         return start, ids[:E], ts[:E]
 
-    def render(self, max_seq: int = 0) -> dict:
+    def render(self, max_seq: int = 0, key_cut: float = np.inf) -> dict:
+        """Render the selected tiles. sat_batch[y, x] is the HIER batch during which the
+        pixel's ray terminated (-1: in the final drain or a flat order, -2: never); with a
+        finite key_cut every tile list is truncated to its entries with key t < key_cut."""
         H, W = self.cam.height, self.cam.width
         out = dict(rgb=np.zeros((H, W, 3)), depth=np.zeros((H, W)), tfinal=np.ones((H, W)),
                    nblend=np.zeros((H, W), np.int32), hash=np.zeros((H, W), np.uint64),
                    dmargin=np.full((H, W), np.inf), cmargin=np.full((H, W), np.inf),
-                   delta=np.zeros((H, W)))
+                   delta=np.zeros((H, W)), sat_batch=np.full((H, W), -2, np.int32))
         seq = np.full((H, W, max(max_seq, 1)), -1, np.int32)
         cnt = np.zeros(16, np.int64)
-        lib().orc_render(self.h, *[_ptr(out[k]) for k in ("rgb", "depth", "tfinal", "nblend", "hash",
-                                                          "dmargin", "cmargin", "delta")],
-                         _ptr(seq), max_seq, _ptr(cnt))
+        lib().orc_render_ex(self.h, *[_ptr(out[k]) for k in ("rgb", "depth", "tfinal", "nblend", "hash",
+                                                             "dmargin", "cmargin", "delta")],
+                            _ptr(seq), max_seq, _ptr(cnt), _ptr(out["sat_batch"]), float(key_cut))
         if max_seq:
             out["seq"] = seq
         out["counters"] = {k: int(cnt[i]) for i, k in enumerate(COUNTERS)}

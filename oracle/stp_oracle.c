@@ -333,11 +333,14 @@ typedef struct {
     int nb; uint64_t h;
     int has_last; double last_t, delta;
     hent head[HEADMAX + 1]; int nh;
+    int batch, sat_batch;       /* HIER batch being processed (-1: drain or flat order) and
+                                   the one during which the ray terminated (-2: never)    */
 } pstate;
 
 typedef struct {                /* per-render output sinks                                */
     double *rgb, *depth, *tfinal, *dmargin, *cmargin, *delta;
     int32_t* nblend; uint64_t* hash; int32_t* seq; int max_seq;
+    int32_t* satb;              /* per pixel: pstate.sat_batch                             */
 } sinks;
 
 static void cam_ray(const ctx* c, double x, double y, double d[3])
@@ -568,6 +571,7 @@ static void blend(ctx* c, pstate* ps, const sinks* sk, double t, int id, double 
     ps->cmin = fmin(ps->cmin, fabs(Tn / c->P.t_min - 1.0));
     if (Tn < c->P.t_min) {
         ps->done = 1;
+        ps->sat_batch = ps->batch;
         cnt[CNT_DONE_PIX]++;
         return;
     }
@@ -598,6 +602,8 @@ static void pixel_init(const ctx* c, pstate* ps, int X, int Y)
     ps->dmin = INFINITY;
     ps->cmin = INFINITY;
     ps->h = HASH_INIT;
+    ps->batch = -1;
+    ps->sat_batch = -2;
 }
 
 static void pixel_out(const ctx* c, const pstate* ps, const sinks* sk)
@@ -612,6 +618,7 @@ static void pixel_out(const ctx* c, const pstate* ps, const sinks* sk)
     if (sk->dmargin) sk->dmargin[p] = ps->dmin;
     if (sk->cmargin) sk->cmargin[p] = ps->cmin;
     if (sk->delta) sk->delta[p] = ps->delta;
+    if (sk->satb) sk->satb[p] = ps->sat_batch;
     if (c->C) {
         for (int k = 0; k < 3; k++) c->C[3 * p + k] = ps->C[k];
         c->Z[p] = ps->Z;
@@ -853,6 +860,7 @@ static void hier_subtile(ctx* c, const sinks* sk, int tile, int S, int64_t* cnt)
     margin_S(s, INFINITY, L->pre_margin);
     int nb = (L->n + 31) / 32;
     for (int b = 0; b < nb; b++) {
+        for (int k = 0; k < 16; k++) s->px[k].batch = b;
         margin_S(s, L->bm_d[b], L->bm_c[b]);
         entry nw[32];
         int nn = 0;
@@ -877,6 +885,7 @@ static void hier_subtile(ctx* c, const sinks* sk, int tile, int S, int64_t* cnt)
             midstage(s, ch, k);
         }
     }
+    for (int k = 0; k < 16; k++) s->px[k].batch = -1;        /* the drain */
     margin_S(s, INFINITY, L->bm_c[nb]);
     while (s->nt > 0) {
         entry ch[16];
@@ -1095,12 +1104,9 @@ void orc_get_tile_lists(void* h, int64_t* start, int32_t* ids, double* ts)
     if (start) start[c->ntiles] = o;
 }
 
-void orc_render(void* h, double* rgb, double* depth, double* tfinal, int32_t* nblend,
-                uint64_t* hash, double* dmargin, double* cmargin, double* delta,
-                int32_t* seq, int32_t max_seq, int64_t* counters)
+static void render_impl(ctx* c, const sinks* skp, int64_t* counters, double key_cut)
 {
-    ctx* c = (ctx*)h;
-    sinks sk = {rgb, depth, tfinal, dmargin, cmargin, delta, nblend, hash, seq, max_seq};
+    sinks sk = *skp;
     free_records(c);
     int64_t np = (int64_t)c->cam.width * c->cam.height;
     if (c->P.record_blends) {
@@ -1117,7 +1123,20 @@ void orc_render(void* h, double* rgb, double* depth, double* tfinal, int32_t* nb
             int w = c->g[i].rect[2] - c->g[i].rect[0] + 1, hh = c->g[i].rect[3] - c->g[i].rect[1] + 1;
             if (w > 0 && hh > 0) tot[CNT_CANDIDATES] += (int64_t)w * hh;
         }
-    tot[CNT_ENTRIES] = orc_num_entries(h);
+    tot[CNT_ENTRIES] = orc_num_entries(c);
+    /* a key cut renders each tile's list truncated to its entries with t < key_cut (a
+     * prefix: the lists are sorted by (t, id)); the full lengths are restored after      */
+    int* full_n = NULL;
+    if (key_cut < INFINITY) {
+        full_n = (int*)malloc((size_t)c->nsel * sizeof(int));
+        for (int k = 0; k < c->nsel; k++) {
+            tlist* L = &c->tl[c->sel[k]];
+            full_n[k] = L->n;
+            int m = 0;
+            while (m < L->n && L->e[m].t < key_cut) m++;
+            L->n = m;
+        }
+    }
 #pragma omp parallel
     {
         int64_t cnt[CNT_N];
@@ -1134,7 +1153,27 @@ void orc_render(void* h, double* rgb, double* depth, double* tfinal, int32_t* nb
         for (int k = 0; k < CNT_N; k++)
             if (k != CNT_VISIBLE && k != CNT_ENTRIES && k != CNT_CANDIDATES) tot[k] += cnt[k];
     }
+    if (full_n) {
+        for (int k = 0; k < c->nsel; k++) c->tl[c->sel[k]].n = full_n[k];
+        free(full_n);
+    }
     if (counters) memcpy(counters, tot, sizeof tot);
+}
+
+void orc_render(void* h, double* rgb, double* depth, double* tfinal, int32_t* nblend,
+                uint64_t* hash, double* dmargin, double* cmargin, double* delta,
+                int32_t* seq, int32_t max_seq, int64_t* counters)
+{
+    sinks sk = {rgb, depth, tfinal, dmargin, cmargin, delta, nblend, hash, seq, max_seq, NULL};
+    render_impl((ctx*)h, &sk, counters, INFINITY);
+}
+
+void orc_render_ex(void* h, double* rgb, double* depth, double* tfinal, int32_t* nblend,
+                   uint64_t* hash, double* dmargin, double* cmargin, double* delta,
+                   int32_t* seq, int32_t max_seq, int64_t* counters, int32_t* sat_batch, double key_cut)
+{
+    sinks sk = {rgb, depth, tfinal, dmargin, cmargin, delta, nblend, hash, seq, max_seq, sat_batch};
+    render_impl((ctx*)h, &sk, counters, key_cut);
 }
 
 int32_t orc_schedule_synthetic(int32_t n, const double* t, const int32_t* keep, double alpha,

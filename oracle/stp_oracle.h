@@ -71,6 +71,14 @@ void    orc_get_tile_lists(void* h, int64_t* start, int32_t* ids, double* ts);
 void    orc_render(void* h, double* rgb, double* depth, double* tfinal, int32_t* nblend,
                    uint64_t* hash, double* dmargin, double* cmargin, double* delta,
                    int32_t* seq, int32_t max_seq, int64_t* counters);
+/* orc_render with two additions: sat_batch[pixel] (may be NULL) receives the HIER batch
+ * during whose processing the pixel's ray terminated (-1: during the final drain or in a
+ * flat order, -2: never), and key_cut < INFINITY renders every tile list truncated to its
+ * entries with key t < key_cut (a prefix of the sorted list).                            */
+void    orc_render_ex(void* h, double* rgb, double* depth, double* tfinal, int32_t* nblend,
+                      uint64_t* hash, double* dmargin, double* cmargin, double* delta,
+                      int32_t* seq, int32_t max_seq, int64_t* counters, int32_t* sat_batch,
+                      double key_cut);
 /* adjoint of the last orc_render (record_blends must have been set); sc is the scene the
  * handle was created from.                                                               */
 void    orc_backward(void* h, const orc_scene* sc, const double* dl_drgb, const double* dl_ddepth,

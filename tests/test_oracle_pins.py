@@ -539,3 +539,31 @@ def test_global_order_decided_pixels_have_a_clear_termination_order(oracle):
             checked += 1
             tied += gap <= oracle.GAP_THR
     assert checked > 200 and tied > 20
+
+
+def test_key_prefix_keeps_pixels_finished_inside_its_complete_batches(oracle):
+    """A render of each tile's list truncated to the entries below a depth cut (a prefix of
+    the sorted list, Sec. 3.4 consumes lists in batches of 32) blends, at every pixel whose
+    ray terminated while a batch the prefix holds completely was being processed, exactly
+    the sequence the full list gives: up to that batch both runs take identical batches,
+    pops and blends. This is the exactness condition of building the lists in depth slices
+    (render a prefix, redo only the tiles it cannot finish). The condition is sharp: pixels
+    that terminated inside the prefix's last, incomplete batch can differ."""
+    sc = I.cluster_scene(20000, 91, nclusters=4, centre_range=0.8, scale_range=(0.01, 0.15))
+    cam = I.orbit_cameras(1, 4.0, 0.5, [(128, 96)], 50.0)[0]
+    with oracle.OracleRun(sc, cam, I.RenderParams()) as r:
+        full = r.render()
+        start, ids, ts = r.tile_lists()
+        cut = float(np.quantile(ts, 0.4))
+        pre = r.render(key_cut=cut)
+    m = np.array([np.count_nonzero(ts[start[t]:start[t + 1]] < cut) for t in range(cam.num_tiles)])
+    yy, xx = np.mgrid[0:cam.height, 0:cam.width]
+    tile = (yy // 16) * cam.tiles_x + xx // 16
+    b = full["sat_batch"]
+    inside = (b >= 0) & (32 * (b + 1) <= m[tile])           # finished within complete batches
+    partial = (b >= 0) & (32 * b < m[tile]) & ~inside       # finished in the last, partial batch
+    same = (full["hash"] == pre["hash"]) & (full["nblend"] == pre["nblend"])
+    assert inside.mean() > 0.1
+    assert same[inside].all()
+    assert (~same[partial]).any()                           # the complete-batch condition matters
+    assert (~same).sum() > 1000                              # the cut removed entries others need
