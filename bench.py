@@ -22,6 +22,7 @@ timing uses a collective (barrier + max).
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import subprocess
@@ -182,6 +183,51 @@ def oracle_threads() -> int:
     return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu on Arm hosts, /proc/cpuinfo otherwise)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def oracle_legs() -> dict:
+    """The FP64 oracle on the other workloads of the measurement plan, all host cores: the
+    4096-Gaussian 256x256 forward in full, the 512-Gaussian 64x64 forward + adjoint (the
+    finite-difference case), and one full 1280x720 forward of the 500k-Gaussian scene."""
+    from oracle import oracle as O
+    legs = {}
+    sc, cams, prm = I.plain_forward_workload()
+    t0 = time.perf_counter()
+    O.render(sc, cams[0], prm)
+    dt = time.perf_counter() - t0
+    legs["plain_4096_256x256_fwd"] = {"value": cams[0].num_pixels / dt / 1e6, "unit": "Mpix/s", "seconds": dt}
+    sc, _, cam, prm = I.fd_subcase()
+    t0 = time.perf_counter()
+    with O.OracleRun(sc, cam, prm, record=True) as r:
+        r.render()
+        r.backward(np.full((cam.height, cam.width, 3), 1.0 / (3 * cam.num_pixels)))
+    dt = time.perf_counter() - t0
+    legs["fd_512_64x64_fwd_bwd"] = {"value": 1e3 * dt, "unit": "ms per forward + adjoint", "seconds": dt}
+    sc, _, cam, prm = I.differentiation_workload()
+    t0 = time.perf_counter()
+    O.render(sc, cam, prm)
+    dt = time.perf_counter() - t0
+    legs["diff_500k_1280x720_fwd"] = {"value": cam.num_pixels / dt / 1e6, "unit": "Mpix/s", "seconds": dt}
+    return legs
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -201,7 +247,8 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "%d random tiles of one view per step" % ntiles},
-            "cpu_baseline": {"value": val, "unit": "Mpix/s", "cores": oracle_threads(), "kind": "oracle",
+            "cpu_baseline": {"value": val, "unit": "Mpix/s", "cores": oracle_threads(), "cpu_model": cpu_model(),
+                             "kind": "oracle",
                              "sample": "%d random 16x16 tiles of view (step mod 16) per step, full preprocess of the 3M Gaussians" % ntiles},
             "e2e": {"value": val, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -447,6 +494,7 @@ def main():
     # ---------------------------------------------------------------- forward only (serving)
     # The training forward above also stores each pixel's blend order for the backward; a
     # renderer without the backward flag stores nothing beyond the images.
+    rnd_ws_gb = rnd.workspace_bytes / 1e9
     fo = R.Renderer(scene.n, cams, prm, capacity=rnd.capacity)
     fout = (torch.empty_like(out[0]), torch.empty_like(out[1]), torch.empty_like(out[2]))
     for _ in range(max(args.warmup, 1)):
@@ -462,6 +510,49 @@ def main():
     fo_ms = max_over_ranks([float(np.mean([e0.elapsed_time(e1) for e0, e1 in fo_ev]))], dist, "cuda")[0]
     fo_same = bool(torch.equal(fout[0], out[0]) and torch.equal(fout[1], out[1]))
     del fo, fout
+    torch.cuda.empty_cache()
+
+    # ---------------------------------------------------------------- backward by replay
+    # The backward of Sec. 3.5 as the paper runs it: no per-pixel lists are stored, every warp
+    # recomputes the forward's queues (blend_cap 0). Same step, same gradients up to the order
+    # of float atomics; the headline step above walks the stored blend order instead.
+    rp = R.Renderer(scene.n, cams, dataclasses.replace(prm, blend_cap=0), backward=True, capacity=rnd.capacity)
+    rgrads = {k: torch.zeros_like(g[k]) for k in R.FIELDS}
+    rout = (torch.empty_like(out[0]), torch.empty_like(out[1]), torch.empty_like(out[2]))
+    for _ in range(max(args.warmup, 1)):
+        rp.forward(g, out=rout, check=False)
+        rp.backward(g, d_rgb, None, rgrads)
+    torch.cuda.synchronize()
+    rp_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    N.profile_enable(2 * K)
+    for e in rp_ev:
+        e[0].record()
+        rp.forward(g, out=rout, check=False)
+        e[1].record()
+        rp.backward(g, d_rgb, None, rgrads)
+        e[2].record()
+    torch.cuda.synchronize()
+    rp_stages = N.profile_read(2 * K)
+    N.profile_enable(0)
+    assert rp.status().error_bits == 0
+    rp_fwd, rp_step = max_over_ranks([float(np.mean([e[0].elapsed_time(e[1]) for e in rp_ev])),
+                                      float(np.mean([e[0].elapsed_time(e[2]) for e in rp_ev]))], dist, "cuda")
+    # gradients of one step of each backward agree (same blend order, other reduction order)
+    one = {k: torch.zeros_like(g[k]) for k in R.FIELDS}
+    two = {k: torch.zeros_like(g[k]) for k in R.FIELDS}
+    rp.forward(g, out=rout, check=False)
+    rp.backward(g, d_rgb, None, one)
+    rnd.forward(g, out=out, check=False)
+    rnd.backward(g, d_rgb, None, two)
+    torch.cuda.synchronize()
+    rp_rel = max(float((one[k] - two[k]).double().norm() / max(two[k].double().norm().item(), 1e-30)) for k in R.FIELDS)
+    replay = {"fwd_bwd_ms_per_view": rp_step / V, "ms_per_step": rp_step, "fwd_ms": rp_fwd,
+              "stage_ms": {"forward": {n: round(float(x), 4) for n, x in zip(N.STAGE_NAMES, rp_stages[0::2].mean(0))},
+                           "backward": {n: round(float(x), 4) for n, x in zip(N.STAGE_NAMES, rp_stages[1::2].mean(0))}},
+              "grad_rel_l2_vs_stored_order": rp_rel,
+              "note": "blend_cap 0: the backward replays the hierarchical queues (recomputed k-buffers, no "
+                      "per-pixel lists stored), as Sec. 3.5 specifies"}
+    del rp, rgrads, rout, one, two
     torch.cuda.empty_cache()
 
     # ---------------------------------------------------------------- end to end (host buffers)
@@ -502,7 +593,7 @@ def main():
     for k in range(2):
         e2e_step(k)
     torch.cuda.synchronize()
-    n_e2e = 6
+    n_e2e = K
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record(up)
     for k in range(n_e2e):
@@ -542,6 +633,11 @@ def main():
                    "queues": "%d/%d/%d" % (prm.tail, prm.mid, prm.head), "l2": "inputs larger than L2 (708 MB scene, 3.8 GB records)",
                    "parallelism": "views sharded over ranks" if world > 1 else "single GPU"},
         "fwd_ms_per_step": fwd_ms, "fwd_bwd_ms_per_view": step_ms / V,
+        "backward_modes": {"headline": "stored blend order (blend_cap %d): ms_per_step and fwd_bwd_ms_per_view"
+                                       % prm.blend_cap,
+                           "stored_order": {"fwd_bwd_ms_per_view": step_ms / V, "ms_per_step": step_ms,
+                                            "workspace_gb": rnd_ws_gb},
+                           "replay": replay},
         "stage_ms": {"forward": {n: round(float(x), 4) for n, x in zip(N.STAGE_NAMES, fwd_stage)},
                      "backward": {n: round(float(x), 4) for n, x in zip(N.STAGE_NAMES, bwd_stage)}},
         "per_view": {"fwd_mpix_s": total_px / world / (pv_ms * 1e-3) / 1e6, "fwd_ms_16_views": pv_ms,
@@ -590,9 +686,10 @@ def main():
         ntiles = 6000         # about 10-20 s of FP64 work on 16 host cores
         px, secs = oracle_sample(scene, cams[0], prm, ntiles, 7)
         line["cpu_baseline"] = {"value": px / secs / 1e6, "unit": "Mpix/s", "cores": oracle_threads(),
-                                "kind": "oracle",
+                                "cpu_model": cpu_model(), "kind": "oracle",
                                 "sample": "%d random 16x16 tiles of view 0 (%d px), FP64, incl. the preprocess of all 3M Gaussians, %.1f s" % (ntiles, px, secs),
-                                "single_thread": single_thread_oracle(args.n)}
+                                "single_thread": single_thread_oracle(args.n),
+                                "legs": oracle_legs()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

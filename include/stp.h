@@ -43,7 +43,10 @@ typedef enum {
     STP_ERR_CAPACITY = 2,       /* more (Gaussian, tile) entries than the workspace holds    */
     STP_ERR_TIMEOUT = 3,        /* a bounded device wait gave up                             */
     STP_ERR_CUDA = 4,           /* a CUDA runtime call failed (message in stp_last_error)    */
-    STP_ERR_NOT_SUPPORTED = 5   /* parameter combination not compiled in                      */
+    STP_ERR_NOT_SUPPORTED = 5,  /* parameter combination not compiled in                      */
+    STP_ERR_INCONSISTENT = 6    /* a backward's recomputed blend sequence disagreed with the
+                                   forward's (status error bit 8): the workspace or the inputs
+                                   changed between the two calls                            */
 } stp_status;
 
 /* Blend orders (Sec. 3.3, 3.4). HIER: the hierarchical resort (tail / mid / head queues).
@@ -126,6 +129,12 @@ typedef struct {
                                     replay the schedule. Same gradients either way (up to the
                                     order of float atomics). 0 = every warp replays.        */
     int64_t max_entries;         /* capacity of (Gaussian, tile) sort entries for one call  */
+    int32_t full_max_passes;     /* STP_MODE_FULL: bound on the peeling passes over a tile's list
+                                    (each pass blends the next 16 entries of every pixel in
+                                    depth order). 0 = list length / 16 + 2, which always
+                                    suffices; a smaller bound that runs out stops the tile and
+                                    sets status error bit 4 (STP_ERR_TIMEOUT). >= 0        */
+    int32_t reserved;
 } stp_params;
 
 typedef struct {                 /* device status block, read back by stp_read_status        */
@@ -139,6 +148,11 @@ typedef struct {                 /* device status block, read back by stp_read_s
                                     Render: [0] (entry, 4x4 subtile) evaluations, [1] 4x4
                                     survivors, [2] (entry, 2x2 quad) evaluations, [3] blends,
                                     [4] (entry, pixel) evaluations                         */
+    uint64_t invalid_gaussians;  /* Gaussians the last forward dropped as invalid, summed over
+                                    scenes: a non-finite mean, log-scale, quaternion component,
+                                    opacity logit or SH coefficient, or a quaternion of squared
+                                    length below 1e-20. Such a Gaussian covers no pixel and
+                                    receives zero gradient; it is not an error.              */
 } stp_run_status;
 
 typedef struct {                 /* byte offsets of workspace regions (for inspection)       */
@@ -250,7 +264,8 @@ stp_status stp_render_backward_batched(const stp_gaussians* scenes, int32_t nsce
                                        void* stream);
 
 /* Synchronises `stream`, copies the workspace's status block to *out (host) and returns
- * STP_ERR_CAPACITY / STP_ERR_TIMEOUT if the device recorded that condition, else STP_OK.  */
+ * STP_ERR_CAPACITY / STP_ERR_TIMEOUT / STP_ERR_INCONSISTENT if the device recorded that
+ * condition (error bits 1 / 4 / 8, in that order of precedence), else STP_OK.              */
 stp_status stp_read_status(const void* workspace, stp_run_status* out /* host */, void* stream);
 
 /* Stable LSD radix sort of (uint64 key, uint32 value) pairs on the low `key_bits` bits
@@ -271,8 +286,12 @@ stp_status stp_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint
  * process exits). The paper has no counterpart; this is a deployment variant of
  * stp_sort_pairs with the same arguments minus temp and the same results.
  *   - n > STP_SORT_STATIC_MAX_N is rejected with STP_ERR_ARG before any work.
- *   - The first call on a device looks up the array's device address (once per device,
- *     with that device current); make that first call before any stream capture.
+ *   - A call on a stream that is not capturing looks up the array's device address on the
+ *     current device (which allocates nothing); a call under stream capture reuses the
+ *     address found by the device's last call outside capture. So make one call on each
+ *     device before any stream capture, and again after a cudaDeviceReset, which reloads
+ *     the library's device code; a capture with no such earlier call fails with
+ *     STP_ERR_CUDA.
  *   - All calls share the array: calls whose work overlaps on the GPU (other streams, other
  *     host threads) race and must be serialised by the caller. Nothing in the array needs
  *     to start at zero.                                                                    */

@@ -71,6 +71,8 @@ def lib():
         L.orc_destroy.argtypes = [vp]
         L.orc_num_entries.restype = C.c_int64
         L.orc_num_entries.argtypes = [vp]
+        L.orc_num_invalid.restype = C.c_int64
+        L.orc_num_invalid.argtypes = [vp]
         L.orc_get_preprocess.argtypes = [vp] + [vp] * 11
         L.orc_get_tile_lists.argtypes = [vp, vp, vp, vp]
         L.orc_render.argtypes = [vp] + [vp] * 9 + [C.c_int32, vp]
@@ -212,6 +214,11 @@ class OracleRun:
     @property
     def num_entries(self) -> int:
         return int(lib().orc_num_entries(self.h))
+
+    @property
+    def num_invalid(self) -> int:
+        """Gaussians dropped as invalid (non-finite inputs or a zero-length quaternion)."""
+        return int(lib().orc_num_invalid(self.h))
 
     def preprocess(self) -> dict:
         n = self.scene.n

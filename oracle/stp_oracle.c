@@ -242,6 +242,7 @@ typedef struct {
     int rect[4];                 /* tiles [x0, x1] x [y0, y1] inclusive; x1 < x0 if empty  */
     int ntiles;
     double margin;               /* min relative margin of this Gaussian's own decisions  */
+    int invalid;                 /* inputs outside the method's domain: dropped, counted  */
 } grec;
 
 static void project_core(const orc_camera* cam, const orc_params* prm, const double p[3],
@@ -371,12 +372,39 @@ static int make_box(const ctx* c, int ox, int oy, int s, double box[4])
 }
 
 /* ------------------------------------------------------------------ preprocess */
+/* The method is defined for finite parameters and a rotation quaternion of non-zero length.
+ * A Gaussian with a non-finite mean, log-scale, quaternion component, opacity logit or SH
+ * coefficient, or with a quaternion whose squared length is below 1e-20, is invalid: it is
+ * dropped before any other step (it covers no pixel) and counted (reading: the paper does
+ * not discuss such inputs).                                                               */
+static int gaussian_valid(const orc_scene* sc, int64_t i, int sh_degree)
+{
+    double q2 = 0.0;
+    for (int k = 0; k < 3; k++)
+        if (!isfinite(sc->means[3 * i + k]) || !isfinite(sc->log_scales[3 * i + k])) return 0;
+    for (int k = 0; k < 4; k++) {
+        double q = sc->quats[4 * i + k];
+        if (!isfinite(q)) return 0;
+        q2 += q * q;
+    }
+    if (!(q2 >= 1e-20) || !isfinite(sc->logits[i])) return 0;
+    int K = (sh_degree + 1) * (sh_degree + 1);
+    for (int j = 0; j < 3 * K; j++)
+        if (!isfinite(sc->sh[i * 3 * K + j])) return 0;
+    return 1;
+}
+
 static void preprocess_one(ctx* c, const orc_scene* sc, int64_t i)
 {
     grec* g = &c->g[i];
     const orc_params* P = &c->P;
     memset(g, 0, sizeof *g);
     g->margin = INFINITY;
+    if (!gaussian_valid(sc, i, P->sh_degree)) {
+        g->invalid = 1;
+        g->rect[2] = -1; g->rect[3] = -1;
+        return;
+    }
     for (int k = 0; k < 3; k++) g->mu[k] = sc->means[3 * i + k];
     matvec3(c->cam.R, g->mu, g->p);
     for (int k = 0; k < 3; k++) g->p[k] += c->cam.t[k];
@@ -471,6 +499,34 @@ static double depth_at(const ctx* c, const grec* g, double x, double y)
     return orc_t_opt(d, c->o, g->mu, g->sinv);
 }
 
+/* Per-batch decision margins of a sorted list of L->n entries (allocated here): bm_d[b] is
+ * the depth gap at the boundary after batch b (which 32 entries load together, Sec. 3.4),
+ * bm_c[b] the smallest cull margin of a near-threshold entry whose key falls into batch b
+ * (b = nb: after the list). Only near entries with key t < key_cut belong to the list.     */
+static void batch_margins(tlist* L, double key_cut)
+{
+    int nb = (L->n + 31) / 32;
+    L->bm_d = (double*)malloc((size_t)(nb + 1) * sizeof(double));
+    L->bm_c = (double*)malloc((size_t)(nb + 1) * sizeof(double));
+    for (int b = 0; b <= nb; b++) {
+        L->bm_d[b] = INFINITY;
+        L->bm_c[b] = INFINITY;
+    }
+    for (int b = 0; b + 1 < nb; b++) L->bm_d[b] = relgap(L->e[32 * b + 31].t, L->e[32 * b + 32].t);
+    for (int k = 0; k < L->nn; k++) {
+        if (!(L->nr[k].t < key_cut)) continue;
+        int lo = 0, hi = L->n;
+        entry key = {L->nr[k].t, L->nr[k].id};
+        while (lo < hi) {
+            int md = (lo + hi) / 2;
+            if (cmp_entry(&L->e[md], &key) < 0) lo = md + 1; else hi = md;
+        }
+        int b = lo / 32;
+        if (b > nb) b = nb;
+        L->bm_c[b] = fmin(L->bm_c[b], L->nr[k].m);
+    }
+}
+
 /* Duplicate (Sec. 3.4 "Tile-based culling", "Tile-depth adjustment"): for every visible
  * Gaussian (ascending id) and every tile of its rectangle (row major), x_hat by Algorithm 1
  * on the tile's pixel-centre box; keep iff opacity * G2(x_hat) >= eps_O; key depth is
@@ -524,27 +580,7 @@ static void build_lists(ctx* c)
         tlist* L = &c->tl[tile];
         if (!L->selected) continue;
         if (L->n > 1) qsort(L->e, (size_t)L->n, sizeof(entry), cmp_entry);
-        int nb = (L->n + 31) / 32;
-        L->bm_d = (double*)malloc((size_t)(nb + 1) * sizeof(double));
-        L->bm_c = (double*)malloc((size_t)(nb + 1) * sizeof(double));
-        for (int b = 0; b <= nb; b++) {
-            L->bm_d[b] = INFINITY;
-            L->bm_c[b] = INFINITY;
-        }
-        /* batch-boundary depth gaps: which 32 entries load together (Sec. 3.4)           */
-        for (int b = 0; b + 1 < nb; b++) L->bm_d[b] = relgap(L->e[32 * b + 31].t, L->e[32 * b + 32].t);
-        /* near-threshold entry-set decisions act from the batch they fall into           */
-        for (int k = 0; k < L->nn; k++) {
-            int lo = 0, hi = L->n;
-            entry key = {L->nr[k].t, L->nr[k].id};
-            while (lo < hi) {
-                int md = (lo + hi) / 2;
-                if (cmp_entry(&L->e[md], &key) < 0) lo = md + 1; else hi = md;
-            }
-            int b = lo / 32;
-            if (b > nb) b = nb;
-            L->bm_c[b] = fmin(L->bm_c[b], L->nr[k].m);
-        }
+        batch_margins(L, INFINITY);
     }
 }
 
@@ -1057,6 +1093,14 @@ void orc_destroy(void* h)
     free(c);
 }
 
+int64_t orc_num_invalid(void* h)
+{
+    ctx* c = (ctx*)h;
+    int64_t k = 0;
+    for (int64_t i = 0; i < c->n; i++) k += c->g[i].invalid;
+    return k;
+}
+
 int64_t orc_num_entries(void* h)
 {
     ctx* c = (ctx*)h;
@@ -1125,16 +1169,23 @@ static void render_impl(ctx* c, const sinks* skp, int64_t* counters, double key_
         }
     tot[CNT_ENTRIES] = orc_num_entries(c);
     /* a key cut renders each tile's list truncated to its entries with t < key_cut (a
-     * prefix: the lists are sorted by (t, id)); the full lengths are restored after      */
+     * prefix: the lists are sorted by (t, id)) with the decision margins of that prefix;
+     * the full lengths and margins are restored after                                    */
     int* full_n = NULL;
+    double **full_bd = NULL, **full_bc = NULL;
     if (key_cut < INFINITY) {
         full_n = (int*)malloc((size_t)c->nsel * sizeof(int));
+        full_bd = (double**)malloc((size_t)c->nsel * sizeof(double*));
+        full_bc = (double**)malloc((size_t)c->nsel * sizeof(double*));
         for (int k = 0; k < c->nsel; k++) {
             tlist* L = &c->tl[c->sel[k]];
             full_n[k] = L->n;
+            full_bd[k] = L->bm_d;
+            full_bc[k] = L->bm_c;
             int m = 0;
             while (m < L->n && L->e[m].t < key_cut) m++;
             L->n = m;
+            batch_margins(L, key_cut);
         }
     }
 #pragma omp parallel
@@ -1154,8 +1205,17 @@ static void render_impl(ctx* c, const sinks* skp, int64_t* counters, double key_
             if (k != CNT_VISIBLE && k != CNT_ENTRIES && k != CNT_CANDIDATES) tot[k] += cnt[k];
     }
     if (full_n) {
-        for (int k = 0; k < c->nsel; k++) c->tl[c->sel[k]].n = full_n[k];
+        for (int k = 0; k < c->nsel; k++) {
+            tlist* L = &c->tl[c->sel[k]];
+            free(L->bm_d);
+            free(L->bm_c);
+            L->n = full_n[k];
+            L->bm_d = full_bd[k];
+            L->bm_c = full_bc[k];
+        }
         free(full_n);
+        free(full_bd);
+        free(full_bc);
     }
     if (counters) memcpy(counters, tot, sizeof tot);
 }

@@ -61,6 +61,9 @@ void*   orc_create(const orc_scene* sc, const orc_camera* cam, const orc_params*
                    const int32_t* tile_sel, int32_t nsel);
 void    orc_destroy(void* h);
 int64_t orc_num_entries(void* h);
+/* Gaussians dropped as invalid: a non-finite mean, log-scale, quaternion, logit or SH
+ * coefficient, or a quaternion of squared length below 1e-20.                            */
+int64_t orc_num_invalid(void* h);
 /* per-Gaussian preprocess results (any pointer may be NULL)                              */
 void    orc_get_preprocess(void* h, int32_t* visible, double* mean2, double* conic,
                            double* opacity, double* color, double* sinv6, double* v3,

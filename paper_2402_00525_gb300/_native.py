@@ -15,7 +15,8 @@ from .inputs import Camera, RenderParams
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libstp.so")
 
-STP_OK, STP_ERR_ARG, STP_ERR_CAPACITY, STP_ERR_TIMEOUT, STP_ERR_CUDA, STP_ERR_NOT_SUPPORTED = range(6)
+(STP_OK, STP_ERR_ARG, STP_ERR_CAPACITY, STP_ERR_TIMEOUT, STP_ERR_CUDA, STP_ERR_NOT_SUPPORTED,
+ STP_ERR_INCONSISTENT) = range(7)
 FLAG_DEBUG_STATS = 32
 FLAG_BACKWARD = 64
 FLAG_DEBUG_TRACE = 128
@@ -60,13 +61,14 @@ class Params(C.Structure):
                 ("alpha_max", C.c_float), ("inv_scale_max", C.c_float), ("dilation", C.c_float),
                 ("frustum_clamp", C.c_float), ("znear", C.c_float), ("bg", C.c_float * 3),
                 ("mode", C.c_int32), ("window_k", C.c_int32), ("flags", C.c_int32),
-                ("blend_cap", C.c_int32), ("max_entries", C.c_int64)]
+                ("blend_cap", C.c_int32), ("max_entries", C.c_int64), ("full_max_passes", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class RunStatus(C.Structure):
     _fields_ = [("error_bits", C.c_uint32), ("mismatched", C.c_uint32),
                 ("num_entries", C.c_uint64), ("capacity", C.c_uint64),
-                ("counters", C.c_uint64 * 5)]
+                ("counters", C.c_uint64 * 5), ("invalid_gaussians", C.c_uint64)]
 
 
 _LAYOUT_SIZE_FIELDS = ["status", "views", "scenes", "geom", "color", "rect", "counts", "offsets", "keep_mask",
@@ -185,6 +187,7 @@ def params_struct(prm: RenderParams, extra_flags: int = 0, max_entries: int = 0)
     p.mode, p.window_k, p.flags = prm.mode, prm.window_k, prm.flags | extra_flags
     p.blend_cap = int(prm.blend_cap)
     p.max_entries = int(max_entries)
+    p.full_max_passes = int(prm.full_max_passes)
     return p
 
 

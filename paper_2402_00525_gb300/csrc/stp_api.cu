@@ -125,6 +125,7 @@ stp_status check(const int64_t* ns, const int32_t* vps, int32_t nscenes, const s
         return fail(STP_ERR_ARG, "blend_cap = %d: must be in [0, 4096]", p->blend_cap);
     if (p->max_entries < 0 || p->max_entries >= 0xFFFFFFFFLL)
         return fail(STP_ERR_ARG, "max_entries must be in [0, 2^32 - 1)");
+    if (p->full_max_passes < 0) return fail(STP_ERR_ARG, "full_max_passes must be >= 0");
     return STP_OK;
 }
 
@@ -285,6 +286,7 @@ stp::PipeArgs make_args(const stp_params* p, const Plan& P, void* ws)
     a.blist_count = L.blend_count ? (uint32_t*)(b + L.blend_count) : nullptr;
     a.replay_warps = L.replay_warps ? (uint32_t*)(b + L.replay_warps) : nullptr;
     a.blend_cap = L.blend_ids ? p->blend_cap : 0;
+    a.full_max_passes = p->full_max_passes;
     a.dbg_trace = L.dbg_trace ? (int*)(b + L.dbg_trace) : nullptr;
     a.partitioned = (p->flags & kFlagGlobalSort) ? 0 : 1;
     a.tile_counts = (uint32_t*)(b + L.tile_counts);
@@ -301,6 +303,7 @@ __global__ void k_status_init(stp::Status* st, unsigned long long cap)
     st->num_entries = 0;
     st->capacity = cap;
     for (int k = 0; k < 5; k++) st->counters[k] = 0;
+    st->invalid = 0;
 }
 
 stp_status check_scene(const stp_gaussians& g, int s)
@@ -524,9 +527,12 @@ stp_status stp_read_status(const void* workspace, stp_run_status* out, void* str
     out->num_entries = h.num_entries;
     out->capacity = h.capacity;
     for (int k = 0; k < 5; k++) out->counters[k] = h.counters[k];
+    out->invalid_gaussians = h.invalid;
     if (h.error_bits & 1u)
         return fail(STP_ERR_CAPACITY, "%llu entries needed, capacity %llu", h.num_entries, h.capacity);
     if (h.error_bits & 4u) return fail(STP_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (h.error_bits & 8u)
+        return fail(STP_ERR_INCONSISTENT, "the backward's blend sequence disagreed with the forward's");
     return STP_OK;
 }
 

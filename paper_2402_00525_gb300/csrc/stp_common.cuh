@@ -37,6 +37,7 @@ struct Status {
     unsigned long long counters[5];   // debug counters (see stp_api.cu)
     unsigned int replay_n;        // backward: warps queued for the replay (pixels past blend_cap)
     unsigned int replay_next;     // backward: next queued warp to take
+    unsigned long long invalid;   // forward: Gaussians dropped as invalid (counted once per scene)
 };
 
 // ---------------------------------------------------------------- per-view constants

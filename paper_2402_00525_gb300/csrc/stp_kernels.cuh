@@ -69,6 +69,7 @@ struct PipeArgs {
     uint32_t* blist_count;   // [total_pixels] blends of the pixel (may exceed blend_cap)
     uint32_t* replay_warps;  // [total_tiles * 8] tile warps (gtile * 8 + warp) the backward replays
     int blend_cap;
+    int full_max_passes;     // FULL order: host bound on peeling passes (0 = always enough)
 };
 
 // Scene of the thread block whose first thread is t0 (largest s with thread_off <= t0).

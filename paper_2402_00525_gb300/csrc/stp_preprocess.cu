@@ -26,7 +26,9 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 
 // Real spherical harmonics to degree 3, Condon-Shortley phase, as polynomials of the unit
 // view direction; constants sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) (times sqrt 2 for m != 0).
-__device__ __forceinline__ void sh_colour(const float* __restrict__ c, int K, float x, float y,
+// Returns false if a channel's sum is not finite (a non-finite coefficient: NaN and +-inf
+// propagate through the sum whatever the basis values, 0 included).
+__device__ __forceinline__ bool sh_colour(const float* __restrict__ c, int K, float x, float y,
                                           float z, float out[3])
 {
     const float k0 = 0.28209479177387814f, k1 = 0.4886025119029199f;
@@ -64,7 +66,18 @@ __device__ __forceinline__ void sh_colour(const float* __restrict__ c, int K, fl
     out[0] = fmaxf(s0, 0.f);
     out[1] = fmaxf(s1, 0.f);
     out[2] = fmaxf(s2, 0.f);
+    return isfinite(s0) && isfinite(s1) && isfinite(s2);
 }
+
+// every SH coefficient of a Gaussian is finite (checked where the colour was not evaluated)
+__device__ __noinline__ bool sh_finite(const float* __restrict__ c, int K)
+{
+    bool ok = true;
+    for (int j = 0; j < 3 * K; j++) ok &= isfinite(__ldg(c + j));
+    return ok;
+}
+
+enum RecKind { kRecInvisible = 0, kRecVisible = 1, kRecInvalid = 2 };
 
 struct GaussIn {             // view-independent quantities of one Gaussian
     float mu[3];
@@ -74,6 +87,7 @@ struct GaussIn {             // view-independent quantities of one Gaussian
     float opacity;
     const float* sh;         // this Gaussian's SH coefficients [sh_k][3]
     int sh_k;
+    bool valid;              // finite parameters and a quaternion of non-zero length
 };
 
 __device__ __forceinline__ void load_gauss(const PipeArgs& a, const SceneDesc& S, int i, GaussIn& g)
@@ -83,7 +97,9 @@ __device__ __forceinline__ void load_gauss(const PipeArgs& a, const SceneDesc& S
     g.mu[2] = __ldg(S.means + 3 * i + 2);
     float qw = __ldg(S.quats + 4 * i), qx = __ldg(S.quats + 4 * i + 1);
     float qy = __ldg(S.quats + 4 * i + 2), qz = __ldg(S.quats + 4 * i + 3);
-    const float ql = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+    const float q[4] = {qw, qx, qy, qz};
+    const float q2 = qw * qw + qx * qx + qy * qy + qz * qz;
+    const float ql = rsqrtf(q2);
     qw *= ql; qx *= ql; qy *= ql; qz *= ql;
     const float R[9] = {1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy),
                         2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx),
@@ -94,29 +110,58 @@ __device__ __forceinline__ void load_gauss(const PipeArgs& a, const SceneDesc& S
         g.si[k] = fminf(expf(-ls), a.inv_scale_max);
     }
     for (int k = 0; k < 9; k++) g.Rq[k] = R[k];
-    g.opacity = 1.f / (1.f + expf(-__ldg(S.logits + i)));
+    const float logit = __ldg(S.logits + i);
+    g.opacity = 1.f / (1.f + expf(-logit));
     g.sh = S.sh + (long long)i * S.sh_k * 3;
     g.sh_k = S.sh_k;
+    // Inputs outside the method's domain make the Gaussian invalid: it is dropped before any
+    // other step and counted (the SH coefficients are checked through the colour sum). x * 0
+    // is NaN exactly when x is NaN or infinite, so one sum tests all eleven scalars.
+    float chk = logit * 0.f;
+    for (int k = 0; k < 3; k++) chk += g.mu[k] * 0.f + __ldg(S.log_scales + 3 * i + k) * 0.f;
+    chk += (q[0] * 0.f + q[1] * 0.f) + (q[2] * 0.f + q[3] * 0.f);
+    g.valid = chk == 0.f && q2 >= 1e-20f;
 }
 
-// Per-(view, Gaussian) record (layout in stp_common.cuh). Returns false if invisible.
+
+// An invalid Gaussian is counted once per scene, by the thread of the scene's first view
+// (count = true). Where that view culls the Gaussian before its colour is evaluated, the SH
+// coefficients are checked directly.
+__device__ __forceinline__ int invisible(const PipeArgs& a, const GaussIn& g, bool count)
+{
+    if (count && !sh_finite(g.sh, g.sh_k)) {
+        atomicAdd(&a.status->invalid, 1ull);
+        return kRecInvalid;
+    }
+    return kRecInvisible;
+}
+__device__ __forceinline__ int invalid(const PipeArgs& a, bool count)
+{
+    if (count) atomicAdd(&a.status->invalid, 1ull);
+    return kRecInvalid;
+}
+
+// Per-(view, Gaussian) record (layout in stp_common.cuh). Returns kRecVisible, kRecInvisible
+// (near plane, opacity below eps_O, degenerate splat: the colour is not evaluated) or
+// kRecInvalid (non-finite inputs); the record stays zero unless visible.
 // The camera-space mean and its projection are evaluated in FP64 (a handful of operations per
 // Gaussian and view): mean2 is ~1e3 px, where an FP32 rounding of 6e-5 px would move the alpha
 // of a sub-pixel-wide splat by ~1e-3 relative. Sigma2 = B B^T + dilation I with B = T M
 // (M = R_q diag(s), Sigma = M M^T), so det Sigma2 = |b0 x b1|^2 + dil (|b0|^2 + |b1|^2) + dil^2
 // is a sum of non-negative terms instead of the cancelling a c - b^2.
-__device__ bool make_record(const PipeArgs& a, const ViewDesc& V, const GaussIn& g, int i,
-                            Rec& rec, float4& col, ushort4& rect)
+__device__ int make_record(const PipeArgs& a, const ViewDesc& V, const GaussIn& g, int i,
+                           Rec& rec, float4& col, ushort4& rect, bool count)
 {
     rect = make_ushort4(0, 0, 0, 0);
     rec.r0 = rec.r1 = rec.r2 = rec.r3 = rec.r4 = rec.r5 = make_float4(0.f, 0.f, 0.f, 0.f);
     col = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!g.valid) return invalid(a, count);
     double pd[3];
     for (int k = 0; k < 3; k++)
         pd[k] = (double)V.R[3 * k] * g.mu[0] + (double)V.R[3 * k + 1] * g.mu[1] + (double)V.R[3 * k + 2] * g.mu[2] +
                 (double)V.t[k];
-    if (!(pd[2] > (double)a.znear)) return false;
-    if (!(g.opacity >= a.eps_o)) return false;
+    if (!(pd[2] > (double)a.znear)) return invisible(a, g, count);
+    if (!(g.opacity >= a.eps_o)) return invisible(a, g, count);
     const double uxd = pd[0] / pd[2], uyd = pd[1] / pd[2];
     const double mxd = (double)V.fx * uxd + (double)V.cx, myd = (double)V.fy * uyd + (double)V.cy;
     const float p[3] = {(float)pd[0], (float)pd[1], (float)pd[2]};
@@ -143,7 +188,7 @@ __device__ bool make_record(const PipeArgs& a, const ViewDesc& V, const GaussIn&
     const float dil = a.dilation;
     const float ca = n0 + dil, cc = n1 + dil;
     const float det = (x0 * x0 + x1 * x1 + x2 * x2) + dil * (n0 + n1) + dil * dil;
-    if (!(det > 0.f)) return false;
+    if (!(det > 0.f)) return invisible(a, g, count);
     // eigen form of Sigma2: lambda_max = mean + sqrt(half-difference^2 + b^2), lambda_min = det/lambda_max
     const float hd = 0.5f * (ca - cc);
     const float lmax = 0.5f * (ca + cc) + sqrtf(hd * hd + cb * cb);
@@ -179,7 +224,10 @@ __device__ bool make_record(const PipeArgs& a, const ViewDesc& V, const GaussIn&
     float d[3] = {g.mu[0] - V.o[0], g.mu[1] - V.o[1], g.mu[2] - V.o[2]};
     const float dl = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     float rgb[3];
-    sh_colour(g.sh, g.sh_k, d[0] * dl, d[1] * dl, d[2] * dl, rgb);
+    if (!sh_colour(g.sh, g.sh_k, d[0] * dl, d[1] * dl, d[2] * dl, rgb)) {
+        rec.r0 = rec.r1 = rec.r2 = rec.r3 = rec.r4 = rec.r5 = make_float4(0.f, 0.f, 0.f, 0.f);
+        return invalid(a, count);
+    }
     col = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
     // Candidate tiles. With the opacity-aware radius of appendix B.2, o G >= eps_O holds only on
     // the ellipse (x - mean2)^T A (x - mean2) <= t_O^2, whose axis-aligned half-widths are
@@ -202,7 +250,7 @@ __device__ bool make_record(const PipeArgs& a, const ViewDesc& V, const GaussIn&
     if (tx1 >= tx0 && ty1 >= ty0)
         rect = make_ushort4((unsigned short)tx0, (unsigned short)ty0, (unsigned short)(tx1 + 1),
                             (unsigned short)(ty1 + 1));
-    return true;
+    return kRecVisible;
 }
 
 __device__ __forceinline__ Rec shfl_rec(const Rec& r, int src)
@@ -473,9 +521,10 @@ __global__ void __launch_bounds__(128, STP_PRE_MIN_BLOCKS) k_preprocess(PipeArgs
     if (th.live) {
         GaussIn g;
         load_gauss(a, th.S, i, g);
-        vis = make_record(a, V, g, i, r, col, rc);
+        vis = make_record(a, V, g, i, r, col, rc, th.v == th.S.view_begin) == kRecVisible;
     } else {
         r.r0 = r.r1 = r.r2 = r.r3 = r.r4 = r.r5 = make_float4(0.f, 0.f, 0.f, 0.f);
+        col = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     uint32_t mask = 0;
     const uint32_t cnt = tiles_pass<false>(a, V, th.v, vis, r, rc, 0, 0, 0, &mask);

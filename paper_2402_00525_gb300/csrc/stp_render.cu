@@ -891,8 +891,8 @@ __global__ void __launch_bounds__(256) k_render_flat(PipeArgs a)
     unsigned long long last = 0ull;
     bool has_last = false, more = mode == STP_MODE_FULL_ID && !s.done;
     // every pass that continues blends HEAD entries of some pixel, so nL / HEAD + 1 passes
-    // exhaust any list; the bound makes that explicit
-    const int max_pass = nL / HEAD + 2;
+    // exhaust any list; the bound makes that explicit, and the caller may lower it
+    const int max_pass = a.full_max_passes > 0 ? min(a.full_max_passes, nL / HEAD + 2) : nL / HEAD + 2;
     int pass = 0;
     do {
         unsigned long long ck[HEAD];

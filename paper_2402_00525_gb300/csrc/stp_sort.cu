@@ -548,19 +548,26 @@ static std::mutex g_static_mu;
 
 long long sort_static_max_n() { return kStaticMaxN; }
 
-// Device address of the static scratch on the current device, looked up once per device.
-cudaError_t sort_static_scratch(void** out)
+// Device address of the static scratch on the current device. A call on a stream that is not
+// capturing looks the address up again (cudaGetSymbolAddress allocates nothing), so a module
+// reloaded after cudaDeviceReset is found at its new place; a call under stream capture uses
+// the address of the device's last call outside capture and fails if there was none.
+cudaError_t sort_static_scratch(void** out, cudaStream_t s)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if ((e = cudaStreamIsCapturing(s, &cap)) != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_sort_static_scratch);
         if (e != cudaSuccess) return e;
         g_static_addr[dev] = p;
+    } else if (!g_static_addr[dev]) {
+        return cudaErrorStreamCaptureUnsupported;
     }
     *out = g_static_addr[dev];
     return cudaSuccess;
@@ -571,7 +578,7 @@ cudaError_t sort_pairs_static(const uint64_t* kin, const uint32_t* vin, uint64_t
 {
     if (n < 0 || n > kStaticMaxN || sort_grid(n) > kStaticGrid) return cudaErrorInvalidValue;
     void* base = nullptr;
-    cudaError_t e = sort_static_scratch(&base);
+    cudaError_t e = sort_static_scratch(&base, s);
     if (e != cudaSuccess) return e;
     uint32_t* hist = (uint32_t*)base;
     uint64_t* kalt = (uint64_t*)((char*)base + kStaticHistBytes);

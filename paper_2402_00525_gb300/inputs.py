@@ -66,6 +66,8 @@ class RenderParams:
     # ids stored per pixel by a forward that a backward follows (the backward walks them instead
     # of replaying the queues; pixels that blend more are replayed): 4 * blend_cap bytes a pixel
     blend_cap: int = 192
+    # FULL order only: bound on the peeling passes over a tile's list (0 = enough for any list)
+    full_max_passes: int = 0
 
     def validate(self) -> None:
         if self.tail < 64 or self.tail % 32 != 0:

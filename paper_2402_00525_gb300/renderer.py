@@ -96,6 +96,7 @@ class Renderer:
         self.pixel_offsets = np.cumsum([0] + [c.width * c.height for c in self.cams])
         self.ws = None
         self._graphs = 0
+        self.generation = 0              # forwards run so far (the autograd path checks it)
         self._alloc(capacity or 0)
 
     # ------------------------------------------------------------------ workspace
@@ -169,6 +170,9 @@ class Renderer:
                 break
             st = N.read_status(_ptr(self.ws), strm.cuda_stream, raise_on_error=False)
             if st.error_bits & 1:
+                if attempt == 2:
+                    raise N.CapacityError(N.STP_ERR_CAPACITY, "%d sort entries needed, capacity %d after "
+                                          "three attempts" % (st.num_entries, self.capacity))
                 self._alloc(int(st.num_entries * self.headroom) + 1024)
                 continue
             if st.error_bits & ~2:
@@ -177,6 +181,7 @@ class Renderer:
             self.last_status = st
             break
         self._fwd_ready = True
+        self.generation += 1
         return rgb, depth, tfin
 
     def _scenes(self, g):
@@ -298,25 +303,54 @@ class Renderer:
         return geom, color, rect, counts
 
 
+class StaleForwardError(RuntimeError):
+    """The renderer ran another forward between an output's forward and its backward."""
+
+
 class _RenderFn(torch.autograd.Function):
+    """Forward and backward of one Renderer call (Sec. 3.5). The backward state (sorted lists,
+    records, the stored blend order) lives in the renderer's one workspace, so an output can
+    be differentiated only while that workspace still holds its forward: ctx keeps the
+    renderer's forward generation, and the backward raises if another forward ran since."""
+
     @staticmethod
-    def forward(ctx, renderer: Renderer, sh_degree: int, means, log_scales, quats, opacity_logits, sh):
+    def forward(ctx, renderer: Renderer, sh_degree: int, check_status: bool, means, log_scales, quats,
+                opacity_logits, sh):
         g = dict(means=means.contiguous(), log_scales=log_scales.contiguous(), quats=quats.contiguous(),
                  opacity_logits=opacity_logits.contiguous(), sh=sh.contiguous(), sh_degree=sh_degree)
         rgb, depth, _ = renderer.forward(g)
         ctx.renderer = renderer
+        ctx.generation = renderer.generation
+        ctx.check_status = check_status
         ctx.g = g
         return rgb, depth
 
     @staticmethod
     def backward(ctx, d_rgb, d_depth):
+        r = ctx.renderer
+        if r.generation != ctx.generation:
+            raise StaleForwardError("the renderer ran %d more forward pass(es) after this output was "
+                                    "rendered; its workspace no longer holds this output's blend order"
+                                    % (r.generation - ctx.generation))
         g = ctx.g
+        if d_rgb is None:            # only depth reaches the loss
+            d_rgb = torch.zeros((r.total_pixels, 3), dtype=torch.float32, device=r.device)
         grads = {k: torch.zeros_like(g[k]) for k in FIELDS}
-        ctx.renderer.backward(g, d_rgb, d_depth, grads)
-        return (None, None) + tuple(grads[k] for k in FIELDS)
+        r.backward(g, d_rgb.float(), None if d_depth is None else d_depth.float(), grads)
+        if ctx.check_status:
+            # synchronises; raises on error bit 8 (the backward did not reproduce the forward's
+            # blend sequence) and on any other recorded condition
+            N.read_status(_ptr(r.ws), torch.cuda.current_stream(r.device).cuda_stream)
+        return (None, None, None) + tuple(grads[k] for k in FIELDS)
 
 
-def render(renderer: Renderer, g: dict):
-    """Differentiable render: returns (rgb [P,3], depth [P]); backward via libstp."""
-    return _RenderFn.apply(renderer, int(g["sh_degree"]), g["means"], g["log_scales"], g["quats"],
-                           g["opacity_logits"], g["sh"])
+def render(renderer: Renderer, g: dict, check_status: bool = True):
+    """Differentiable render: returns (rgb [P,3], depth [P]); backward via libstp.
+
+    Each output must be differentiated before the same renderer renders again (the backward
+    raises StaleForwardError otherwise). With check_status the backward reads the device
+    status block (one host synchronisation) and raises if it recorded an error."""
+    if not (renderer.flags & N.FLAG_BACKWARD):
+        raise RuntimeError("construct the Renderer with backward=True")
+    return _RenderFn.apply(renderer, int(g["sh_degree"]), bool(check_status), g["means"], g["log_scales"],
+                           g["quats"], g["opacity_logits"], g["sh"])

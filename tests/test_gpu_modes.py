@@ -84,6 +84,9 @@ def test_backward_under_readings_and_ablations_matches_adjoint(oracle, flags):
         ora = r.render()
         w = rng.normal(size=(cam.height, cam.width, 3)) / cam.num_pixels
         wz = rng.normal(size=(cam.height, cam.width)) / cam.num_pixels * 0.1
+        # ablation E keeps every entry in the 4x4 / 2x2 queues, so more near-equal depth
+        # comparisons touch each pixel (98.1% decided against >= 99.85% otherwise)
+        assert ora["decided"].mean() >= (0.98 if flags == I.FLAG_NO_HIER_CULL else 0.99)
         w[~ora["decided"]] = 0
         wz[~ora["decided"]] = 0
         adj = r.backward(w, wz)
@@ -100,7 +103,7 @@ def test_backward_under_readings_and_ablations_matches_adjoint(oracle, flags):
         b = adj[k].ravel()
         rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
         cos = a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30)
-        assert rel <= 1e-3 and cos >= 0.9999, (k, rel, cos)
+        assert rel <= 1e-4 and cos >= 0.9999, (k, rel, cos)
 
 
 @pytest.mark.parametrize("mode,k", [(I.MODE_GLOBAL, 16), (I.MODE_WINDOW, 16)])

@@ -282,6 +282,8 @@ def test_backward_matches_oracle_adjoint(oracle, cap):
         ora = r.render()
         w = rng.normal(size=(cam.height, cam.width, 3)) / cam.num_pixels
         wz = rng.normal(size=(cam.height, cam.width)) / cam.num_pixels * 0.1
+        # fewer than 1% of the pixels may sit near a decision threshold (parity bar)
+        assert ora["decided"].mean() >= 0.99, ora["decided"].mean()
         w[~ora["decided"]] = 0
         wz[~ora["decided"]] = 0
         adj = r.backward(w, wz)
@@ -302,7 +304,7 @@ def test_backward_matches_oracle_adjoint(oracle, cap):
         rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
         cos = a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30)
         print(k, "rel-L2 %.3g cos %.8f" % (rel, cos))
-        assert rel <= 1e-3 and cos >= 0.9999, k
+        assert rel <= 1e-4 and cos >= 0.9999, (k, rel, cos)
 
 
 def test_stored_blend_order_backward_equals_replay():

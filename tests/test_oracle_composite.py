@@ -229,3 +229,52 @@ def test_conic_is_the_inverse_of_the_projected_covariance(oracle):
         p = Rc @ _f32(sc.means[i]) + np.array(camf.t[:])
         mean2 = np.array([camf.fx * p[0] / p[2] + camf.cx, camf.fy * p[1] / p[2] + camf.cy])
         np.testing.assert_allclose(pp["mean2"][i], mean2, rtol=1e-12, atol=1e-9)
+
+
+# ------------------------------------------------------------ inputs outside the domain
+def invalid_variant(sc):
+    """Copy of `sc` with twelve Gaussians made invalid in different ways, the indices, and a
+    reference copy where the same Gaussians are merely invisible (opacity logit -30, so
+    opacity < eps_O)."""
+    bad = np.array([3, 17, 29, 41, 55, 68, 80, 97, 110, 123, 140, 151])
+    s1 = I.Scene(sc.means.copy(), sc.log_scales.copy(), sc.quats.copy(), sc.opacity_logits.copy(),
+                 sc.sh.copy(), sc.sh_degree)
+    s1.means[bad[0], 0] = np.nan
+    s1.means[bad[1], 2] = np.inf
+    s1.log_scales[bad[2], 1] = -np.inf          # zero scale
+    s1.log_scales[bad[3], 0] = np.inf
+    s1.quats[bad[4]] = 0.0                       # no rotation defined
+    s1.quats[bad[5], 3] = np.nan
+    s1.opacity_logits[bad[6]] = np.nan
+    s1.opacity_logits[bad[7]] = np.inf
+    s1.sh[bad[8], 0, 1] = np.nan
+    s1.sh[bad[9], -1, 2] = np.inf               # highest band: its basis value may be 0
+    s1.sh[bad[10], 1, 0] = -np.inf
+    s1.means[bad[11], 1] = -np.inf
+    s2 = I.Scene(sc.means.copy(), sc.log_scales.copy(), sc.quats.copy(), sc.opacity_logits.copy(),
+                 sc.sh.copy(), sc.sh_degree)
+    s2.opacity_logits[bad] = -30.0
+    return s1, s2, bad
+
+
+def test_invalid_gaussians_are_dropped_and_counted(oracle):
+    """A Gaussian with a non-finite parameter or a zero-length quaternion covers no pixel: the
+    image equals that of the same scene with those Gaussians made invisible, bit for bit, the
+    oracle counts them, and their adjoint is zero while every other gradient is unchanged."""
+    sc = I.uniform_scene(160, 93, scale_range=(0.02, 0.12), sh_degree=2)
+    cam = I.look_at((0.2, 0.1, -3), (0, 0, 0), (0, 1, 0), 64, 48, 60.0)
+    prm = I.RenderParams()
+    s1, s2, bad = invalid_variant(sc)
+    rng = np.random.default_rng(5)
+    w = rng.normal(size=(cam.height, cam.width, 3))
+    with oracle.OracleRun(s1, cam, prm, record=True) as r1, oracle.OracleRun(s2, cam, prm, record=True) as r2:
+        assert r1.num_invalid == len(bad) and r2.num_invalid == 0
+        a, b = r1.render(), r2.render()
+        for k in ("rgb", "depth", "tfinal", "nblend", "hash"):
+            assert np.array_equal(a[k], b[k]), k
+        assert a["nblend"].sum() > 0
+        g1, g2 = r1.backward(w), r2.backward(w)
+    for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        assert np.all(g1[k][bad] == 0) and np.all(np.isfinite(g1[k])), k
+        keep = np.setdiff1d(np.arange(sc.n), bad)
+        assert np.array_equal(g1[k][keep], g2[k][keep]), k
