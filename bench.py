@@ -392,6 +392,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--per-view-rounds", type=int, default=2)
     ap.add_argument("--no-extra", action="store_true", help="skip the 64-view and 8-scene legs")
+    ap.add_argument("--profile-forward", action="store_true",
+                    help="only run warm-up + steps batched forwards (no backward flag: a small workspace), "
+                         "for profiler captures; prints the forward time")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -419,6 +422,16 @@ def main():
     V = len(cams)
     P = sum(c.num_pixels for c in cams)
     g = R.scene_to_device(scene)
+    if args.profile_forward:
+        fr = R.Renderer(scene.n, cams, prm)
+        fr.forward(g)                                        # sizes the capacity (may render twice)
+        for _ in range(args.warmup + args.steps):
+            fr.forward(g, check=False)
+        torch.cuda.synchronize()
+        assert fr.status().error_bits == 0
+        print(json.dumps({"profile_forward": True, "gaussians": scene.n, "views": V,
+                          "launches_per_forward": 9}), flush=True)
+        return
     rnd = R.Renderer(scene.n, cams, prm, backward=True)
     out = (torch.empty((P, 3), device="cuda"), torch.empty((P,), device="cuda"), torch.empty((P,), device="cuda"))
     rnd.forward(g, out=out)                                   # sizes the sort-entry capacity

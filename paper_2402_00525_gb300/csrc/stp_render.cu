@@ -82,6 +82,17 @@ constexpr int render_min_blocks()
 #endif
 }
 
+// Head-stage FIFO: a quad's mid-queue pops are appended to its FIFO (ids, in pop order) and
+// its pixels consume them at the end of each iteration of the list loop (a batch of 32 list
+// entries, or one drain step), all quads of the warp together. A pixel sees exactly the
+// sequence it would see if it consumed every pop at once, so the results are the same; the
+// warp's lanes are busy together instead of only the lanes of the quads that happened to pop.
+// One iteration appends at most 32 + MID - 4 entries to a FIFO: a batch makes a tail pop at
+// most twice (it adds <= 32 entries to a tail holding <= TAIL - 32), and the quad's mid queue
+// holds <= MID - 4 entries between sub-batches.
+constexpr int kFifo = 48;
+static_assert(kFifo >= 32 + kMaxMid - 4, "head FIFO must hold one iteration's pops");
+
 __device__ __forceinline__ uint32_t depth_key(float t)
 {
     const uint32_t k = fkey(t);
@@ -94,6 +105,10 @@ __device__ __forceinline__ float level_cull_eps(const PipeArgs& a)
 {
     return (a.flags & kFlagNoHierCull) ? -1.f : a.eps_o;
 }
+
+// per-warp shared memory in uint2 units: tails (2 subtiles x 2 buffers), the batch staging,
+// the eight mid queues and the eight head FIFOs (kFifo ids each)
+__host__ __device__ constexpr int render_warp_smem(int tail, int mid) { return 4 * tail + 64 + 8 * mid + 4 * kFifo; }
 
 template <int HEAD>
 struct Px {
@@ -299,23 +314,21 @@ __device__ __forceinline__ void head_flush(const PipeArgs& a, const ViewDesc& V,
 
 struct Warp {                    // warp-uniform tail state and per-quad mid state
     int nt[2], ts[2], tb[2];
-    int nm, ms;                  // this lane's quad
+    int nm, ms;                  // this lane's quad: mid-queue length and front
+    int fc;                      // this lane's quad: entries waiting in its head FIFO
 };
 
+// The pixels consume their quads' FIFOs (every lane of the warp calls this). Not unrolled:
+// one inlined copy of the head step (and of its blend).
 template <int HEAD, bool BWD>
-__device__ __forceinline__ void headstage(const PipeArgs& a, const ViewDesc& V, Px<HEAD>& s,
-                                          const PixCtx& c, Warp& wq, uint2* mq, bool pop, int cap)
+__device__ __forceinline__ void head_consume(const PipeArgs& a, const ViewDesc& V, Px<HEAD>& s,
+                                             const PixCtx& c, Warp& wq, const uint32_t* fq)
 {
-    const int pc = pop ? min(cap, wq.nm) : 0;
-    const int ms0 = wq.ms;
-    wq.ms += pc;
-    wq.nm -= pc;
     const bool evict_first = (a.flags & 1) != 0;
-    // not unrolled: one inlined copy of the head step (and of its blend); the entries are read
-    // from the quad's mid queue, which nothing writes until the warp's next merge
+    const int n = wq.fc;
 #pragma unroll 1
-    for (int k = 0; k < pc && !s.done; k++) {
-        const uint32_t gid = mq[ms0 + k].y;
+    for (int k = 0; k < n && !s.done; k++) {
+        const uint32_t gid = fq[k];
         const Rec r = load_rec(a.geom, V.rec_off + gid);
         const float val = splat_value(r, c.xc, c.yc);
         if (a.dbg_nblend != nullptr && !BWD) atomicAdd(&a.status->counters[4], 1ull);
@@ -324,11 +337,24 @@ __device__ __forceinline__ void headstage(const PipeArgs& a, const ViewDesc& V, 
             head_push<HEAD, BWD>(a, V, s, c, depth_key(t), gid, val, evict_first);
         }
     }
+    wq.fc = 0;
+    __syncwarp();                                 // the FIFOs are refilled after this
+}
+
+// Append the front `cnt` entries of this lane's quad's mid queue to the quad's FIFO (the four
+// lanes of the quad copy them). Every lane of the warp calls it.
+__device__ __forceinline__ void mid_pop(Warp& wq, const uint2* mq, uint32_t* fq, int cnt, int pq)
+{
+    for (int k = pq; k < cnt; k += 4) fq[wq.fc + k] = mq[wq.ms + k].y;
+    wq.ms += cnt;
+    wq.nm -= cnt;
+    wq.fc += cnt;
+    __syncwarp();
 }
 
 template <int HEAD, bool BWD>
 __device__ void midstage(const PipeArgs& a, const ViewDesc& V, Px<HEAD>& s, const PixCtx& c,
-                         Warp& wq, const uint2* tailb, uint2* mq, const Box& bQ, bool qval,
+                         Warp& wq, const uint2* tailb, uint2* mq, uint32_t* fq, const Box& bQ, bool qval,
                          int c0, int c1, int lane)
 {
     const int h = lane >> 4, pq = lane & 3, qbase = lane & ~3;
@@ -400,8 +426,7 @@ __device__ void midstage(const PipeArgs& a, const ViewDesc& V, Px<HEAD>& s, cons
         wq.nm += nn;
         wq.ms = 0;
         const bool pop = wq.nm > MID - 4;
-        if (__any_sync(kFull, pop)) headstage<HEAD, BWD>(a, V, s, c, wq, mq, pop, 4);
-        __syncwarp();
+        if (__any_sync(kFull, pop)) mid_pop(wq, mq, fq, pop ? 4 : 0, pq);
     }
 }
 
@@ -436,6 +461,7 @@ __device__ __forceinline__ void render_warp(const PipeArgs& a, const int gtile, 
     const int TAIL = a.tail, MID = a.mid;
     uint2* stage = tailb + 4 * TAIL;
     uint2* midb = stage + 64;
+    uint32_t* fifob = reinterpret_cast<uint32_t*>(midb + 8 * MID);
     int lo = 0, hi = a.nviews - 1;
     while (lo < hi) {
         const int m = (lo + hi + 1) >> 1;
@@ -502,8 +528,9 @@ __device__ __forceinline__ void render_warp(const PipeArgs& a, const int gtile, 
     }
     Warp wq;
     wq.nt[0] = wq.nt[1] = wq.ts[0] = wq.ts[1] = wq.tb[0] = wq.tb[1] = 0;
-    wq.nm = wq.ms = 0;
+    wq.nm = wq.ms = wq.fc = 0;
     uint2* mq = midb + (h * 4 + q) * MID;
+    uint32_t* fq = fifob + (h * 4 + q) * kFifo;
 
     const uint2 rg = a.ranges[gtile];
     const int lst = (int)rg.x, nL = (int)(rg.y - rg.x);
@@ -511,7 +538,6 @@ __device__ __forceinline__ void render_warp(const PipeArgs& a, const int gtile, 
     const float cull_eps = level_cull_eps(a);
     const bool count = a.dbg_nblend != nullptr && !BWD;
     unsigned long long n_eval_s = 0, n_surv_s = 0;
-    bool finished = false;
     // One loop for the batches and the drain, so that the mid stage (and the head stage and
     // blend inside it) is inlined once. While batches remain, a batch is loaded and merged and
     // the tails pop 16 while they hold more than TAIL-32; afterwards each iteration pops one
@@ -519,10 +545,8 @@ __device__ __forceinline__ void render_warp(const PipeArgs& a, const int gtile, 
     int b0 = 0;
     for (;;) {
         const bool batch = b0 < nL;
-        if (__all_sync(kFull, s.done)) {
-            finished = batch;
-            break;
-        }
+        if (__all_sync(kFull, s.done)) break;
+        bool last = false;
         if (batch) {
             const int idx = b0 + lane;
             const bool in = idx < nL;
@@ -565,13 +589,17 @@ __device__ __forceinline__ void render_warp(const PipeArgs& a, const int gtile, 
             wq.tb[0] ^= 1;
             wq.tb[1] ^= 1;
             b0 += 32;
+        } else if (wq.nt[0] == 0 && wq.nt[1] == 0) {
+            // tails drained: the mid queues flush into the FIFOs behind their pops, and the
+            // pixels take everything in this last iteration
+            mid_pop(wq, mq, fq, wq.nm, pq);
+            last = true;
         } else {
-            if (wq.nt[0] == 0 && wq.nt[1] == 0) break;
             const unsigned live = __ballot_sync(kFull, !s.done);
             if ((live & 0xFFFFu) == 0) wq.nt[0] = 0;
             if ((live >> 16) == 0) wq.nt[1] = 0;
         }
-        for (;;) {
+        for (; !last;) {
             int c0, c1;
             if (batch) {
                 c0 = wq.nt[0] > TAIL - 32 ? 16 : 0;
@@ -581,19 +609,16 @@ __device__ __forceinline__ void render_warp(const PipeArgs& a, const int gtile, 
                 c0 = min(16, wq.nt[0]);
                 c1 = min(16, wq.nt[1]);
             }
-            midstage<HEAD, BWD>(a, V, s, c, wq, tailb, mq, bQ, qval, c0, c1, lane);
+            midstage<HEAD, BWD>(a, V, s, c, wq, tailb, mq, fq, bQ, qval, c0, c1, lane);
             wq.ts[0] += c0; wq.nt[0] -= c0;
             wq.ts[1] += c1; wq.nt[1] -= c1;
             if (!batch) break;
         }
+        // the pixels take this iteration's pops now (so the saturation test above is current)
+        if (__any_sync(kFull, wq.fc > 0)) head_consume<HEAD, BWD>(a, V, s, c, wq, fq);
+        if (last) break;
     }
-    if (!finished) {
-        while (__any_sync(kFull, wq.nm > 0) && !__all_sync(kFull, s.done)) {
-            headstage<HEAD, BWD>(a, V, s, c, wq, mq, wq.nm > 0, 4);
-            __syncwarp();
-        }
-        head_flush<HEAD, BWD>(a, V, s, c);
-    }
+    head_flush<HEAD, BWD>(a, V, s, c);
     if (count) {
         if (lane == 0) {
             atomicAdd(&a.status->counters[0], n_eval_s);
@@ -627,7 +652,7 @@ __global__ void __launch_bounds__(32 * kRenderWarps, (render_min_blocks<HEAD, BW
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     if (a.status->error_bits & 1u) return;
     render_warp<HEAD, BWD>(a, (int)(blockIdx.x / kBlocksPerTile), (int)(blockIdx.x % kBlocksPerTile) * kRenderWarps + wib,
-                           lane, sm + wib * (4 * a.tail + 64 + 8 * a.mid));
+                           lane, sm + wib * render_warp_smem(a.tail, a.mid));
 }
 
 // Backward replay of the tile warps the stored-order kernel queued (a pixel past blend_cap):
@@ -640,7 +665,7 @@ __global__ void __launch_bounds__(32 * kRenderWarps, (render_min_blocks<HEAD, tr
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     if (a.status->error_bits & 1u) return;
     const unsigned n = a.status->replay_n;
-    uint2* tailb = sm + wib * (4 * a.tail + 64 + 8 * a.mid);
+    uint2* tailb = sm + wib * render_warp_smem(a.tail, a.mid);
     for (;;) {
         unsigned item = 0;
         if (lane == 0) item = atomicAdd(&a.status->replay_next, 1u);
@@ -1007,7 +1032,7 @@ cudaError_t launch_flat(const PipeArgs& a, cudaStream_t s)
 
 }  // namespace
 
-size_t render_smem_bytes(int tail, int mid) { return (size_t)kRenderWarps * (4 * tail + 64 + 8 * mid) * sizeof(uint2); }
+size_t render_smem_bytes(int tail, int mid) { return (size_t)kRenderWarps * render_warp_smem(tail, mid) * sizeof(uint2); }
 
 bool render_head_supported(int head) { return head == 1 || head == 2 || head == 4 || head == 8 || head == 16; }
 

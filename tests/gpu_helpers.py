@@ -22,9 +22,13 @@ def gpu_render(scene, cams, prm, debug=True, capacity=None):
 
 # Undecided pixels (a depth gap, cull or alpha test within the decision threshold) get no
 # exact check, since FP32 and FP64 may legitimately take the near-tie the other way. They
-# are held to a sanity bound instead: most keep the oracle's exact blend order, and the
-# pixels whose colour moves by more than the decided bar are a small share of those compared.
-UND_SAME_ORDER_MIN = 0.8      # undecided pixels with the oracle's blend count and order hash
+# are held to a sanity bound instead: in the hierarchical and FULL orders most keep the
+# oracle's exact blend order (measured >= 95%), and in every order the pixels whose colour
+# moves by more than the decided bar are a small share of those compared (measured <= 0.2%).
+# In the list orders (GLOBAL, WINDOW-k) the tile list's order is the blend order, so every
+# near-equal pair of FP32 keys that ties (then ordered by id) where the FP64 keys do not
+# changes the order: there only the colour and count bounds apply.
+UND_SAME_ORDER_MIN = 0.9      # undecided pixels with the oracle's blend count and order hash
 RGB_OUTLIER_MAX = 0.02        # compared pixels with max |d rgb| > 1e-4
 NBLEND_P99_MAX = 2            # p99 of |d blend count| over undecided pixels
 
@@ -41,7 +45,7 @@ def undecided_stats(gpu, k, ora, tiles_mask=None):
                 nblend_p99=float(np.percentile(dnb[und], 99)) if und.any() else 0.0)
 
 
-def compare_view(gpu, k, ora, tiles_mask=None, min_decided=0.99, label=""):
+def compare_view(gpu, k, ora, tiles_mask=None, min_decided=0.99, label="", list_order=False):
     dec = ora["decided"].copy()
     if tiles_mask is not None:
         dec &= tiles_mask
@@ -62,7 +66,7 @@ def compare_view(gpu, k, ora, tiles_mask=None, min_decided=0.99, label=""):
     assert dt.size == 0 or dt.max() <= 1e-5
     us = undecided_stats(gpu, k, ora, tiles_mask)
     print("%s undecided: %s" % (label, us))
-    assert us["same_order"] >= UND_SAME_ORDER_MIN, (label, us)
+    assert list_order or us["same_order"] >= UND_SAME_ORDER_MIN, (label, us)
     assert us["rgb_outliers"] <= RGB_OUTLIER_MAX, (label, us)
     assert us["nblend_p99"] <= NBLEND_P99_MAX, (label, us)
     return frac

@@ -68,7 +68,9 @@ def test_invalid_gaussians_receive_zero_gradient():
     for k in R.FIELDS:
         assert np.all(np.isfinite(out["invalid"][k])), k
         assert np.all(out["invalid"][k][bad] == 0), k
-        np.testing.assert_allclose(out["invalid"][k][keep], out["invisible"][k][keep], rtol=1e-5, atol=1e-9)
+        # the same blends; only the order of the float reductions differs between the runs
+        a, b = out["invalid"][k][keep].astype(np.float64), out["invisible"][k][keep].astype(np.float64)
+        assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b), k
 
 
 def test_invalid_gaussians_counted_per_scene_in_a_batch():

@@ -52,7 +52,8 @@ def test_mode_matches_oracle(oracle, case):
         prm = dataclasses.replace(base, **CASES[case])
         gpu = gpu_render(sc, [cam], prm)
         ora = oracle.render(sc, cam, prm)
-        frac = compare_view(gpu, 0, ora, min_decided=0.9, label="%s / %s" % (case, name))
+        frac = compare_view(gpu, 0, ora, min_decided=0.9, label="%s / %s" % (case, name),
+                            list_order=prm.mode in (I.MODE_GLOBAL, I.MODE_WINDOW))
         st = gpu["renderer"].status()
         assert st.error_bits == 0 and st.num_entries == ora["num_entries"]
         print(case, name, "decided %.4f" % frac, "delta avg %.4f" % ora["delta"].mean())
@@ -118,5 +119,5 @@ def test_list_orders_on_full_hd_3m_sampled_tiles(oracle, mode, k):
     with oracle.OracleRun(sc, cams[0], prm, tiles=tiles) as r:
         ora = r.render()
     frac = compare_view(gpu, 0, ora, tiles_mask=tile_mask(cams[0], tiles), min_decided=0.7,
-                        label="mode %d full hd" % mode)
+                        label="mode %d full hd" % mode, list_order=True)
     print("mode", mode, "decided", frac)
