@@ -110,17 +110,23 @@ __device__ __forceinline__ float level_cull_eps(const PipeArgs& a)
 // the eight mid queues and the eight head FIFOs (kFifo ids each)
 __host__ __device__ constexpr int render_warp_smem(int tail, int mid) { return 4 * tail + 64 + 8 * mid + 4 * kFifo; }
 
-template <int HEAD>
-struct Px {
+// Debug state of a pixel (blend-order hash, sort error): held only by the DBG instantiations,
+// so the timed path carries none of it in registers and takes no debug branch per blend.
+template <bool DBG> struct PxDbg {};
+template <> struct PxDbg<true> {
+    unsigned long long hash;
+    float last_t, delta;         // sort error: sum of the backward steps of the blended t_opt
+};
+
+template <int HEAD, bool DBG>
+struct Px : PxDbg<DBG> {
     float T, C0, C1, C2, Z;
     bool done;
-    int nh;
-    uint32_t hk[HEAD + 1];
-    uint32_t hid[HEAD + 1];
-    float hv[HEAD + 1];          // opacity * G2 at the pixel (before the alpha_max clamp)
+    int nh;                      // entries in the head, at the front of hk / hid / hv
+    uint32_t hk[HEAD];           // ascending keys, kInvalidKey beyond nh
+    uint32_t hid[HEAD];
+    float hv[HEAD];              // opacity * G2 at the pixel (before the alpha_max clamp)
     uint32_t nbl;
-    unsigned long long hash;
-    float last_t, delta;         // debug: sort error (sum of backward steps of the blended t_opt)
 };
 
 struct PixCtx {
@@ -202,8 +208,8 @@ __device__ __forceinline__ void grad_red(const PipeArgs& a, long long ri, const 
     atomicAdd(gg + 8, qc);
 }
 
-template <int HEAD, bool BWD>
-__device__ __forceinline__ void blend(const PipeArgs& a, const ViewDesc& V, Px<HEAD>& s,
+template <int HEAD, bool BWD, bool DBG>
+__device__ __forceinline__ void blend(const PipeArgs& a, const ViewDesc& V, Px<HEAD, DBG>& s,
                                       const PixCtx& c, uint32_t key, uint32_t id, float val)
 {
     if (s.done) return;
@@ -230,33 +236,39 @@ __device__ __forceinline__ void blend(const PipeArgs& a, const ViewDesc& V, Px<H
     // the stored blend order (backward without replay): the first blend_cap ids of the pixel,
     // stored and later loaded with the evict-first hint (each id is touched once either way)
     if (!BWD && a.blist && s.nbl < (uint32_t)a.blend_cap) __stcs(a.blist + c.bl + 32ll * s.nbl, id);
-    if (!BWD && a.dbg_trace && s.nbl < (uint32_t)kTraceLen) a.dbg_trace[c.pix * kTraceLen + s.nbl] = (int)id;
-    if (!BWD && a.dbg_hash) {          // debug statistics: order hash and sort error
-        s.hash = s.hash * kHashMul + (unsigned long long)(id + 1u);
-        if (s.nbl > 0 && s.last_t > t) s.delta += s.last_t - t;
-        s.last_t = t;
+    if constexpr (DBG && !BWD) {
+        if (a.dbg_trace && s.nbl < (uint32_t)kTraceLen) a.dbg_trace[c.pix * kTraceLen + s.nbl] = (int)id;
+        if (a.dbg_hash) {              // debug statistics: order hash and sort error
+            s.hash = s.hash * kHashMul + (unsigned long long)(id + 1u);
+            if (s.nbl > 0 && s.last_t > t) s.delta += s.last_t - t;
+            s.last_t = t;
+        }
     }
     s.T = Tn;
     s.nbl++;
 }
 
-// head (per-pixel k-buffer, Sec. 3.3) primitives on register arrays with static indices
-template <int HEAD>
-__device__ __forceinline__ void head_insert(Px<HEAD>& s, uint32_t key, uint32_t id, float val)
+// head (per-pixel k-buffer, Sec. 3.3) primitives on register arrays with static indices.
+// Insert into a head holding nh < HEAD entries, after equal keys (stable).
+template <int HEAD, bool DBG>
+__device__ __forceinline__ void head_insert(Px<HEAD, DBG>& s, uint32_t key, uint32_t id, float val)
 {
-    // insert after equal keys (stable)
-    uint32_t nk[HEAD + 1], ni[HEAD + 1];
-    float nv[HEAD + 1];
+    uint32_t nk[HEAD], ni[HEAD];
+    float nv[HEAD];
+    bool prev_le = true;
 #pragma unroll
-    for (int j = 0; j <= HEAD; j++) {
+    for (int j = 0; j < HEAD; j++) {
+        // slot j keeps its entry if it is <= key; else it takes key (if slot j-1 kept its
+        // entry) or slot j-1's entry (shifted back by one)
         const bool le = s.hk[j] <= key;
-        const bool prev_le = (j == 0) ? true : (s.hk[j - 1] <= key);
-        nk[j] = le ? s.hk[j] : (prev_le ? key : s.hk[j - 1]);
-        ni[j] = le ? s.hid[j] : (prev_le ? id : s.hid[j - 1]);
-        nv[j] = le ? s.hv[j] : (prev_le ? val : s.hv[j - 1]);
+        const int p = j > 0 ? j - 1 : 0;
+        nk[j] = le ? s.hk[j] : (prev_le ? key : s.hk[p]);
+        ni[j] = le ? s.hid[j] : (prev_le ? id : s.hid[p]);
+        nv[j] = le ? s.hv[j] : (prev_le ? val : s.hv[p]);
+        prev_le = le;
     }
 #pragma unroll
-    for (int j = 0; j <= HEAD; j++) {
+    for (int j = 0; j < HEAD; j++) {
         s.hk[j] = nk[j];
         s.hid[j] = ni[j];
         s.hv[j] = nv[j];
@@ -264,51 +276,111 @@ __device__ __forceinline__ void head_insert(Px<HEAD>& s, uint32_t key, uint32_t 
     s.nh++;
 }
 
-template <int HEAD>
-__device__ __forceinline__ void head_pop(Px<HEAD>& s, uint32_t& key, uint32_t& id, float& val)
+// The head is full: insert (key, id, val) after equal keys and take the smallest of the HEAD + 1
+// entries out, in one pass. If the new entry is smaller than every held one it leaves at once
+// and the head is unchanged; otherwise the front leaves and the new entry is merged into the
+// other HEAD - 1. (key, id, val) returns the entry taken out.
+template <int HEAD, bool DBG>
+__device__ __forceinline__ void head_exchange(Px<HEAD, DBG>& s, uint32_t& key, uint32_t& id, float& val)
+{
+    const bool pass = key < s.hk[0];
+    bool le[HEAD];
+#pragma unroll
+    for (int j = 0; j < HEAD; j++) le[j] = s.hk[j] <= key;
+    uint32_t nk[HEAD], ni[HEAD];
+    float nv[HEAD];
+#pragma unroll
+    for (int j = 0; j < HEAD; j++) {
+        // slot j takes the next held entry if it is <= key, else the new entry if the entry
+        // before it is <= key (slot 0: unless the new entry passes), else keeps its own
+        const int n = j + 1 < HEAD ? j + 1 : j;
+        const bool nxt = j + 1 < HEAD && le[n];
+        const bool nw = j == 0 ? !pass : le[j];
+        nk[j] = nxt ? s.hk[n] : (nw ? key : s.hk[j]);
+        ni[j] = nxt ? s.hid[n] : (nw ? id : s.hid[j]);
+        nv[j] = nxt ? s.hv[n] : (nw ? val : s.hv[j]);
+    }
+    const uint32_t ok = s.hk[0], oi = s.hid[0];
+    const float ov = s.hv[0];
+    key = pass ? key : ok;
+    id = pass ? id : oi;
+    val = pass ? val : ov;
+#pragma unroll
+    for (int j = 0; j < HEAD; j++) {
+        s.hk[j] = nk[j];
+        s.hid[j] = ni[j];
+        s.hv[j] = nv[j];
+    }
+}
+
+template <int HEAD, bool DBG>
+__device__ __forceinline__ void head_pop(Px<HEAD, DBG>& s, uint32_t& key, uint32_t& id, float& val)
 {
     key = s.hk[0];
     id = s.hid[0];
     val = s.hv[0];
 #pragma unroll
-    for (int j = 0; j < HEAD; j++) {
+    for (int j = 0; j + 1 < HEAD; j++) {
         s.hk[j] = s.hk[j + 1];
         s.hid[j] = s.hid[j + 1];
         s.hv[j] = s.hv[j + 1];
     }
-    s.hk[HEAD] = kInvalidKey;
+    s.hk[HEAD - 1] = kInvalidKey;
     s.nh--;
 }
 
 // Insert (key, id, val); when more than HEAD entries are held blend the smallest (Sec. 3.3
-// k-buffer; evict_first = the alternative "blend before insert" reading). The blend sits at one
-// call site so that its body (large in the backward replay) is inlined once.
-template <int HEAD, bool BWD>
-__device__ __forceinline__ void head_push(const PipeArgs& a, const ViewDesc& V, Px<HEAD>& s,
+// k-buffer; evict_first = the alternative "blend before insert" reading, where the front of a
+// full head is blended first and the new entry then inserted). The blend and the insertion
+// each sit at one call site, so that their bodies (the blend is large in the backward replay)
+// are inlined once.
+template <int HEAD, bool BWD, bool DBG>
+__device__ __forceinline__ void head_push(const PipeArgs& a, const ViewDesc& V, Px<HEAD, DBG>& s,
                                           const PixCtx& c, uint32_t key, uint32_t id, float val,
                                           bool evict_first)
 {
-    const bool pop_first = evict_first && s.nh == HEAD;
-    if (!pop_first) head_insert(s, key, id, val);
-    if (pop_first || s.nh > HEAD) {
-        uint32_t k, i;
-        float v;
-        head_pop(s, k, i, v);
-        blend<HEAD, BWD>(a, V, s, c, k, i, v);
-        if (pop_first && !s.done) head_insert(s, key, id, val);
+    const bool full = s.nh == HEAD;
+    if (full) {
+        uint32_t k = key, i = id;
+        float v = val;
+        if (evict_first) head_pop(s, k, i, v);
+        else head_exchange(s, k, i, v);
+        blend<HEAD, BWD, DBG>(a, V, s, c, k, i, v);
     }
+    if (!full || (evict_first && !s.done)) head_insert(s, key, id, val);
 }
 
 // blend what the head still holds, nearest first
-template <int HEAD, bool BWD>
-__device__ __forceinline__ void head_flush(const PipeArgs& a, const ViewDesc& V, Px<HEAD>& s, const PixCtx& c)
+template <int HEAD, bool BWD, bool DBG>
+__device__ __forceinline__ void head_flush(const PipeArgs& a, const ViewDesc& V, Px<HEAD, DBG>& s, const PixCtx& c)
 {
 #pragma unroll 1
     while (s.nh > 0 && !s.done) {
         uint32_t k, i;
         float v;
         head_pop(s, k, i, v);
-        blend<HEAD, BWD>(a, V, s, c, k, i, v);
+        blend<HEAD, BWD, DBG>(a, V, s, c, k, i, v);
+    }
+}
+
+template <int HEAD, bool DBG>
+__device__ __forceinline__ void px_init(Px<HEAD, DBG>& s, bool inside)
+{
+    s.T = 1.f;
+    s.C0 = s.C1 = s.C2 = s.Z = 0.f;
+    s.done = !inside;
+    s.nh = 0;
+    s.nbl = 0;
+    if constexpr (DBG) {
+        s.hash = kHashInit;
+        s.last_t = 0.f;
+        s.delta = 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < HEAD; j++) {
+        s.hk[j] = kInvalidKey;
+        s.hid[j] = 0;
+        s.hv[j] = 0.f;
     }
 }
 
@@ -320,8 +392,8 @@ struct Warp {                    // warp-uniform tail state and per-quad mid sta
 
 // The pixels consume their quads' FIFOs (every lane of the warp calls this). Not unrolled:
 // one inlined copy of the head step (and of its blend).
-template <int HEAD, bool BWD>
-__device__ __forceinline__ void head_consume(const PipeArgs& a, const ViewDesc& V, Px<HEAD>& s,
+template <int HEAD, bool BWD, bool DBG>
+__device__ __forceinline__ void head_consume(const PipeArgs& a, const ViewDesc& V, Px<HEAD, DBG>& s,
                                              const PixCtx& c, Warp& wq, const uint32_t* fq)
 {
     const bool evict_first = (a.flags & 1) != 0;
@@ -331,10 +403,10 @@ __device__ __forceinline__ void head_consume(const PipeArgs& a, const ViewDesc& 
         const uint32_t gid = fq[k];
         const Rec r = load_rec(a.geom, V.rec_off + gid);
         const float val = splat_value(r, c.xc, c.yc);
-        if (a.dbg_nblend != nullptr && !BWD) atomicAdd(&a.status->counters[4], 1ull);
+        if (DBG && !BWD && a.dbg_nblend != nullptr) atomicAdd(&a.status->counters[4], 1ull);
         if (fminf(a.alpha_max, val) >= a.eps_o) {
             const float t = depth_uvn(r, c.u, c.w, c.n);
-            head_push<HEAD, BWD>(a, V, s, c, depth_key(t), gid, val, evict_first);
+            head_push<HEAD, BWD, DBG>(a, V, s, c, depth_key(t), gid, val, evict_first);
         }
     }
     wq.fc = 0;
@@ -352,8 +424,8 @@ __device__ __forceinline__ void mid_pop(Warp& wq, const uint2* mq, uint32_t* fq,
     __syncwarp();
 }
 
-template <int HEAD, bool BWD>
-__device__ void midstage(const PipeArgs& a, const ViewDesc& V, Px<HEAD>& s, const PixCtx& c,
+template <int HEAD, bool BWD, bool DBG>
+__device__ void midstage(const PipeArgs& a, const ViewDesc& V, Px<HEAD, DBG>& s, const PixCtx& c,
                          Warp& wq, const uint2* tailb, uint2* mq, uint32_t* fq, const Box& bQ, bool qval,
                          int c0, int c1, int lane)
 {
@@ -389,7 +461,7 @@ __device__ void midstage(const PipeArgs& a, const ViewDesc& V, Px<HEAD>& s, cons
         }
         const unsigned bal = __ballot_sync(kFull, key != kInvalidKey);
         const int nn = __popc((bal >> qbase) & 0xFu);
-        if (a.dbg_nblend != nullptr && !BWD) {
+        if (DBG && !BWD && a.dbg_nblend != nullptr) {
             const unsigned ev = __ballot_sync(kFull, e < cnt && qval);
             if (lane == 0) atomicAdd(&a.status->counters[2], (unsigned long long)__popc(ev));
         }
@@ -454,7 +526,7 @@ __device__ __forceinline__ void merge_tail(const uint2* src, int ne, const uint2
 
 // One warp's share of a tile (two 4x4 subtiles) through the whole hierarchical Render: the
 // forward, or its replay for the backward. tailb is the warp's shared-memory queue area.
-template <int HEAD, bool BWD>
+template <int HEAD, bool BWD, bool DBG>
 __device__ __forceinline__ void render_warp(const PipeArgs& a, const int gtile, const int warp, const int lane,
                                             uint2* tailb)
 {
@@ -511,21 +583,8 @@ __device__ __forceinline__ void render_warp(const PipeArgs& a, const int gtile, 
         c.Tf = a.tfinal_ws[c.pix];
     }
 
-    Px<HEAD> s;
-    s.T = 1.f;
-    s.C0 = s.C1 = s.C2 = s.Z = 0.f;
-    s.done = !inside;
-    s.nh = 0;
-    s.nbl = 0;
-    s.hash = kHashInit;
-    s.last_t = 0.f;
-    s.delta = 0.f;
-#pragma unroll
-    for (int j = 0; j <= HEAD; j++) {
-        s.hk[j] = kInvalidKey;
-        s.hid[j] = 0;
-        s.hv[j] = 0.f;
-    }
+    Px<HEAD, DBG> s;
+    px_init(s, inside);
     Warp wq;
     wq.nt[0] = wq.nt[1] = wq.ts[0] = wq.ts[1] = wq.tb[0] = wq.tb[1] = 0;
     wq.nm = wq.ms = wq.fc = 0;
@@ -536,7 +595,7 @@ __device__ __forceinline__ void render_warp(const PipeArgs& a, const int gtile, 
     const int lst = (int)rg.x, nL = (int)(rg.y - rg.x);
     const bool centre = (a.flags & 2) != 0;
     const float cull_eps = level_cull_eps(a);
-    const bool count = a.dbg_nblend != nullptr && !BWD;
+    const bool count = DBG && !BWD && a.dbg_nblend != nullptr;
     unsigned long long n_eval_s = 0, n_surv_s = 0;
     // One loop for the batches and the drain, so that the mid stage (and the head stage and
     // blend inside it) is inlined once. While batches remain, a batch is loaded and merged and
@@ -609,16 +668,16 @@ __device__ __forceinline__ void render_warp(const PipeArgs& a, const int gtile, 
                 c0 = min(16, wq.nt[0]);
                 c1 = min(16, wq.nt[1]);
             }
-            midstage<HEAD, BWD>(a, V, s, c, wq, tailb, mq, fq, bQ, qval, c0, c1, lane);
+            midstage<HEAD, BWD, DBG>(a, V, s, c, wq, tailb, mq, fq, bQ, qval, c0, c1, lane);
             wq.ts[0] += c0; wq.nt[0] -= c0;
             wq.ts[1] += c1; wq.nt[1] -= c1;
             if (!batch) break;
         }
         // the pixels take this iteration's pops now (so the saturation test above is current)
-        if (__any_sync(kFull, wq.fc > 0)) head_consume<HEAD, BWD>(a, V, s, c, wq, fq);
+        if (__any_sync(kFull, wq.fc > 0)) head_consume<HEAD, BWD, DBG>(a, V, s, c, wq, fq);
         if (last) break;
     }
-    head_flush<HEAD, BWD>(a, V, s, c);
+    head_flush<HEAD, BWD, DBG>(a, V, s, c);
     if (count) {
         if (lane == 0) {
             atomicAdd(&a.status->counters[0], n_eval_s);
@@ -637,28 +696,30 @@ __device__ __forceinline__ void render_warp(const PipeArgs& a, const int gtile, 
         if (a.grad_geom) reinterpret_cast<float4*>(a.pix_state)[p] = make_float4(s.C0, s.C1, s.C2, s.Z);
         if (a.blist) a.blist_count[p] = s.nbl;
         if (a.tfinal_out) a.tfinal_out[p] = s.T;
-        if (a.dbg_nblend) a.dbg_nblend[p] = s.nbl;
-        if (a.dbg_hash) a.dbg_hash[p] = s.hash;
-        if (a.dbg_delta) a.dbg_delta[p] = s.delta;
-    } else {
+        if constexpr (DBG) {
+            if (a.dbg_nblend) a.dbg_nblend[p] = s.nbl;
+            if (a.dbg_hash) a.dbg_hash[p] = s.hash;
+            if (a.dbg_delta) a.dbg_delta[p] = s.delta;
+        }
+    } else if constexpr (DBG) {
         if (a.dbg_nblend && a.dbg_nblend[p] != s.nbl) atomicOr(&a.status->error_bits, 8u);
     }
 }
 
-template <int HEAD, bool BWD>
+template <int HEAD, bool BWD, bool DBG>
 __global__ void __launch_bounds__(32 * kRenderWarps, (render_min_blocks<HEAD, BWD>())) k_render(PipeArgs a)
 {
     extern __shared__ uint2 sm[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     if (a.status->error_bits & 1u) return;
-    render_warp<HEAD, BWD>(a, (int)(blockIdx.x / kBlocksPerTile), (int)(blockIdx.x % kBlocksPerTile) * kRenderWarps + wib,
+    render_warp<HEAD, BWD, DBG>(a, (int)(blockIdx.x / kBlocksPerTile), (int)(blockIdx.x % kBlocksPerTile) * kRenderWarps + wib,
                            lane, sm + wib * render_warp_smem(a.tail, a.mid));
 }
 
 // Backward replay of the tile warps the stored-order kernel queued (a pixel past blend_cap):
 // a grid of resident blocks whose warps take queued tile warps one at a time, so that the
 // few replays cost no launch of a block per tile.
-template <int HEAD>
+template <int HEAD, bool DBG>
 __global__ void __launch_bounds__(32 * kRenderWarps, (render_min_blocks<HEAD, true>())) k_render_replay(PipeArgs a)
 {
     extern __shared__ uint2 sm[];
@@ -672,7 +733,7 @@ __global__ void __launch_bounds__(32 * kRenderWarps, (render_min_blocks<HEAD, tr
         item = __shfl_sync(kFull, item, 0);
         if (item >= n) break;
         const uint32_t w = a.replay_warps[item];
-        render_warp<HEAD, true>(a, (int)(w >> 3), (int)(w & 7), lane, tailb);
+        render_warp<HEAD, true, DBG>(a, (int)(w >> 3), (int)(w & 7), lane, tailb);
         __syncwarp();
     }
 }
@@ -809,31 +870,31 @@ __global__ void __launch_bounds__(32 * kRenderWarps, STP_BWD_LIST_MIN_BLOCKS * 4
     if (inside && __float_as_uint(T) != __float_as_uint(c.Tf)) atomicOr(&a.status->error_bits, 8u);
 }
 
-template <int HEAD>
+template <int HEAD, bool DBG>
 cudaError_t launch_head(const PipeArgs& a, bool bwd, size_t smem, cudaStream_t s)
 {
     static int set_fwd[64], set_bwd[64];
     cudaError_t e;
     if (bwd) {
-        if ((e = ensure_smem_limit(k_render<HEAD, true>, smem, set_bwd, 64)) != cudaSuccess) return e;
+        if ((e = ensure_smem_limit(k_render<HEAD, true, DBG>, smem, set_bwd, 64)) != cudaSuccess) return e;
         if (a.blist) {
             static int set_rep[64];
-            if ((e = ensure_smem_limit(k_render_replay<HEAD>, smem, set_rep, 64)) != cudaSuccess) return e;
+            if ((e = ensure_smem_limit(k_render_replay<HEAD, DBG>, smem, set_rep, 64)) != cudaSuccess) return e;
             int dev = 0, nsm = 0;
             if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
             if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
             const long long resident = (long long)nsm * render_min_blocks<HEAD, true>();
             const unsigned grid = (unsigned)std::min<long long>(resident, (long long)a.total_tiles * kBlocksPerTile);
             k_render_bwd_list<<<a.total_tiles * kBlocksPerTile, 32 * kRenderWarps, 0, s>>>(a);
-            k_render_replay<HEAD><<<grid, 32 * kRenderWarps, smem, s>>>(a);
+            k_render_replay<HEAD, DBG><<<grid, 32 * kRenderWarps, smem, s>>>(a);
             note_launches(2);
         } else {
-            k_render<HEAD, true><<<a.total_tiles * kBlocksPerTile, 32 * kRenderWarps, smem, s>>>(a);
+            k_render<HEAD, true, DBG><<<a.total_tiles * kBlocksPerTile, 32 * kRenderWarps, smem, s>>>(a);
             note_launches(1);
         }
     } else {
-        if ((e = ensure_smem_limit(k_render<HEAD, false>, smem, set_fwd, 64)) != cudaSuccess) return e;
-        k_render<HEAD, false><<<a.total_tiles * kBlocksPerTile, 32 * kRenderWarps, smem, s>>>(a);
+        if ((e = ensure_smem_limit(k_render<HEAD, false, DBG>, smem, set_fwd, 64)) != cudaSuccess) return e;
+        k_render<HEAD, false, DBG><<<a.total_tiles * kBlocksPerTile, 32 * kRenderWarps, smem, s>>>(a);
         note_launches(1);
     }
     return cudaGetLastError();
@@ -865,24 +926,6 @@ __device__ __forceinline__ void flat_init(const PipeArgs& a, const ViewDesc& V, 
     c.Cf0 = c.Cf1 = c.Cf2 = c.Zf = c.Tf = 0.f;
 }
 
-template <int HEAD>
-__device__ __forceinline__ void px_init(Px<HEAD>& s, bool inside)
-{
-    s.T = 1.f;
-    s.C0 = s.C1 = s.C2 = s.Z = 0.f;
-    s.done = !inside;
-    s.nh = 0;
-    s.nbl = 0;
-    s.hash = kHashInit;
-    s.last_t = 0.f;
-    s.delta = 0.f;
-#pragma unroll
-    for (int j = 0; j <= HEAD; j++) {
-        s.hk[j] = kInvalidKey;
-        s.hid[j] = 0;
-        s.hv[j] = 0.f;
-    }
-}
 
 template <int HEAD>
 __global__ void __launch_bounds__(256) k_render_flat(PipeArgs a)
@@ -904,7 +947,7 @@ __global__ void __launch_bounds__(256) k_render_flat(PipeArgs a)
     PixCtx c;
     flat_init(a, V, pxi, pyi, c);
     const bool inside = c.pix >= 0;
-    Px<HEAD> s;
+    Px<HEAD, true> s;                // comparison orders: debug outputs checked at run time
     px_init(s, inside);
     const uint2 rg = a.ranges[gtile];
     const int lst = (int)rg.x, nL = (int)(rg.y - rg.x);
@@ -954,10 +997,10 @@ __global__ void __launch_bounds__(256) k_render_flat(PipeArgs a)
                     const uint32_t key = depth_key(depth_uvn(r, c.u, c.w, c.n));
                     const uint32_t gid = sid[j];
                     if (mode == STP_MODE_GLOBAL_ID) {
-                        blend<HEAD, false>(a, V, s, c, key, gid, val);
+                        blend<HEAD, false, true>(a, V, s, c, key, gid, val);
                         if (s.done) break;
                     } else if (mode == STP_MODE_WINDOW_ID) {
-                        head_push<HEAD, false>(a, V, s, c, key, gid, val, evict_first);
+                        head_push<HEAD, false, true>(a, V, s, c, key, gid, val, evict_first);
                         if (s.done) break;
                     } else {
                         const unsigned long long ek = ((unsigned long long)key << 32) | (uint32_t)(b0 + j);
@@ -987,7 +1030,7 @@ __global__ void __launch_bounds__(256) k_render_flat(PipeArgs a)
                 // blend the peeled entries nearest first (shifting keeps the indices static)
 #pragma unroll 1
                 for (int j = 0; j < nc && !s.done; j++) {
-                    blend<HEAD, false>(a, V, s, c, (uint32_t)(ck[0] >> 32), cid[0], cv[0]);
+                    blend<HEAD, false, true>(a, V, s, c, (uint32_t)(ck[0] >> 32), cid[0], cv[0]);
 #pragma unroll
                     for (int q = 0; q + 1 < HEAD; q++) {
                         ck[q] = ck[q + 1];
@@ -1004,7 +1047,7 @@ __global__ void __launch_bounds__(256) k_render_flat(PipeArgs a)
             if (!__syncthreads_or(more)) break;
         }
     } while (mode == STP_MODE_FULL_ID);
-    if (mode == STP_MODE_WINDOW_ID) head_flush<HEAD, false>(a, V, s, c);
+    if (mode == STP_MODE_WINDOW_ID) head_flush<HEAD, false, true>(a, V, s, c);
     if (count) {
         atomicAdd(&a.status->counters[4], n_eval);
         atomicAdd(&a.status->counters[3], (unsigned long long)s.nbl);
@@ -1053,12 +1096,15 @@ cudaError_t launch_render(const PipeArgs& a, bool backward, cudaStream_t s)
         }
     }
     const size_t smem = render_smem_bytes(a.tail, a.mid);
+    // debug outputs (blend counts, hashes, sort error, traces, work counters) select the
+    // instantiations that keep and write them
+    const bool dbg = a.dbg_nblend || a.dbg_hash || a.dbg_delta || a.dbg_trace;
     switch (a.head) {
-        case 1: return launch_head<1>(a, backward, smem, s);
-        case 2: return launch_head<2>(a, backward, smem, s);
-        case 4: return launch_head<4>(a, backward, smem, s);
-        case 8: return launch_head<8>(a, backward, smem, s);
-        case 16: return launch_head<16>(a, backward, smem, s);
+        case 1: return dbg ? launch_head<1, true>(a, backward, smem, s) : launch_head<1, false>(a, backward, smem, s);
+        case 2: return dbg ? launch_head<2, true>(a, backward, smem, s) : launch_head<2, false>(a, backward, smem, s);
+        case 4: return dbg ? launch_head<4, true>(a, backward, smem, s) : launch_head<4, false>(a, backward, smem, s);
+        case 8: return dbg ? launch_head<8, true>(a, backward, smem, s) : launch_head<8, false>(a, backward, smem, s);
+        case 16: return dbg ? launch_head<16, true>(a, backward, smem, s) : launch_head<16, false>(a, backward, smem, s);
         default: return cudaErrorInvalidValue;
     }
 }
