@@ -93,6 +93,11 @@ constexpr int render_min_blocks()
 constexpr int kFifo = 48;
 static_assert(kFifo >= 32 + kMaxMid - 4, "head FIFO must hold one iteration's pops");
 
+// The head queue compares depths as floats. A NaN or +inf depth (a degenerate splat) is held
+// as FLT_MAX, so +inf marks an empty slot below which every real entry sorts.
+constexpr float kEmptyT = __builtin_huge_valf();
+__device__ __forceinline__ float head_depth(float t) { return fminf(t, 3.402823466e38f); }
+
 __device__ __forceinline__ uint32_t depth_key(float t)
 {
     const uint32_t k = fkey(t);
@@ -123,7 +128,7 @@ struct Px : PxDbg<DBG> {
     float T, C0, C1, C2, Z;
     bool done;
     int nh;                      // entries in the head, at the front of hk / hid / hv
-    uint32_t hk[HEAD];           // ascending keys, kInvalidKey beyond nh
+    float hk[HEAD];              // ascending depths t_opt at the pixel, kEmptyT beyond nh
     uint32_t hid[HEAD];
     float hv[HEAD];              // opacity * G2 at the pixel (before the alpha_max clamp)
     uint32_t nbl;
@@ -210,7 +215,7 @@ __device__ __forceinline__ void grad_red(const PipeArgs& a, long long ri, const 
 
 template <int HEAD, bool BWD, bool DBG>
 __device__ __forceinline__ void blend(const PipeArgs& a, const ViewDesc& V, Px<HEAD, DBG>& s,
-                                      const PixCtx& c, uint32_t key, uint32_t id, float val)
+                                      const PixCtx& c, float t, uint32_t id, float val)
 {
     if (s.done) return;
     const float alpha = fminf(a.alpha_max, val);
@@ -221,7 +226,6 @@ __device__ __forceinline__ void blend(const PipeArgs& a, const ViewDesc& V, Px<H
     }
     const long long ri = V.rec_off + id;
     const float4 col = __ldg(a.color + ri);
-    const float t = fkey_inv(key);
     const float wgt = alpha * s.T;
     s.C0 += col.x * wgt;
     s.C1 += col.y * wgt;
@@ -251,9 +255,10 @@ __device__ __forceinline__ void blend(const PipeArgs& a, const ViewDesc& V, Px<H
 // head (per-pixel k-buffer, Sec. 3.3) primitives on register arrays with static indices.
 // Insert into a head holding nh < HEAD entries, after equal keys (stable).
 template <int HEAD, bool DBG>
-__device__ __forceinline__ void head_insert(Px<HEAD, DBG>& s, uint32_t key, uint32_t id, float val)
+__device__ __forceinline__ void head_insert(Px<HEAD, DBG>& s, float key, uint32_t id, float val)
 {
-    uint32_t nk[HEAD], ni[HEAD];
+    float nk[HEAD];
+    uint32_t ni[HEAD];
     float nv[HEAD];
     bool prev_le = true;
 #pragma unroll
@@ -281,13 +286,14 @@ __device__ __forceinline__ void head_insert(Px<HEAD, DBG>& s, uint32_t key, uint
 // and the head is unchanged; otherwise the front leaves and the new entry is merged into the
 // other HEAD - 1. (key, id, val) returns the entry taken out.
 template <int HEAD, bool DBG>
-__device__ __forceinline__ void head_exchange(Px<HEAD, DBG>& s, uint32_t& key, uint32_t& id, float& val)
+__device__ __forceinline__ void head_exchange(Px<HEAD, DBG>& s, float& key, uint32_t& id, float& val)
 {
     const bool pass = key < s.hk[0];
     bool le[HEAD];
 #pragma unroll
     for (int j = 0; j < HEAD; j++) le[j] = s.hk[j] <= key;
-    uint32_t nk[HEAD], ni[HEAD];
+    float nk[HEAD];
+    uint32_t ni[HEAD];
     float nv[HEAD];
 #pragma unroll
     for (int j = 0; j < HEAD; j++) {
@@ -300,8 +306,8 @@ __device__ __forceinline__ void head_exchange(Px<HEAD, DBG>& s, uint32_t& key, u
         ni[j] = nxt ? s.hid[n] : (nw ? id : s.hid[j]);
         nv[j] = nxt ? s.hv[n] : (nw ? val : s.hv[j]);
     }
-    const uint32_t ok = s.hk[0], oi = s.hid[0];
-    const float ov = s.hv[0];
+    const float ok = s.hk[0], ov = s.hv[0];
+    const uint32_t oi = s.hid[0];
     key = pass ? key : ok;
     id = pass ? id : oi;
     val = pass ? val : ov;
@@ -314,7 +320,7 @@ __device__ __forceinline__ void head_exchange(Px<HEAD, DBG>& s, uint32_t& key, u
 }
 
 template <int HEAD, bool DBG>
-__device__ __forceinline__ void head_pop(Px<HEAD, DBG>& s, uint32_t& key, uint32_t& id, float& val)
+__device__ __forceinline__ void head_pop(Px<HEAD, DBG>& s, float& key, uint32_t& id, float& val)
 {
     key = s.hk[0];
     id = s.hid[0];
@@ -325,7 +331,7 @@ __device__ __forceinline__ void head_pop(Px<HEAD, DBG>& s, uint32_t& key, uint32
         s.hid[j] = s.hid[j + 1];
         s.hv[j] = s.hv[j + 1];
     }
-    s.hk[HEAD - 1] = kInvalidKey;
+    s.hk[HEAD - 1] = kEmptyT;
     s.nh--;
 }
 
@@ -336,13 +342,13 @@ __device__ __forceinline__ void head_pop(Px<HEAD, DBG>& s, uint32_t& key, uint32
 // are inlined once.
 template <int HEAD, bool BWD, bool DBG>
 __device__ __forceinline__ void head_push(const PipeArgs& a, const ViewDesc& V, Px<HEAD, DBG>& s,
-                                          const PixCtx& c, uint32_t key, uint32_t id, float val,
+                                          const PixCtx& c, float key, uint32_t id, float val,
                                           bool evict_first)
 {
     const bool full = s.nh == HEAD;
     if (full) {
-        uint32_t k = key, i = id;
-        float v = val;
+        float k = key, v = val;
+        uint32_t i = id;
         if (evict_first) head_pop(s, k, i, v);
         else head_exchange(s, k, i, v);
         blend<HEAD, BWD, DBG>(a, V, s, c, k, i, v);
@@ -356,8 +362,8 @@ __device__ __forceinline__ void head_flush(const PipeArgs& a, const ViewDesc& V,
 {
 #pragma unroll 1
     while (s.nh > 0 && !s.done) {
-        uint32_t k, i;
-        float v;
+        float k, v;
+        uint32_t i;
         head_pop(s, k, i, v);
         blend<HEAD, BWD, DBG>(a, V, s, c, k, i, v);
     }
@@ -378,7 +384,7 @@ __device__ __forceinline__ void px_init(Px<HEAD, DBG>& s, bool inside)
     }
 #pragma unroll
     for (int j = 0; j < HEAD; j++) {
-        s.hk[j] = kInvalidKey;
+        s.hk[j] = kEmptyT;
         s.hid[j] = 0;
         s.hv[j] = 0.f;
     }
@@ -406,7 +412,7 @@ __device__ __forceinline__ void head_consume(const PipeArgs& a, const ViewDesc& 
         if (DBG && !BWD && a.dbg_nblend != nullptr) atomicAdd(&a.status->counters[4], 1ull);
         if (fminf(a.alpha_max, val) >= a.eps_o) {
             const float t = depth_uvn(r, c.u, c.w, c.n);
-            head_push<HEAD, BWD, DBG>(a, V, s, c, depth_key(t), gid, val, evict_first);
+            head_push<HEAD, BWD, DBG>(a, V, s, c, head_depth(t), gid, val, evict_first);
         }
     }
     wq.fc = 0;
@@ -620,12 +626,14 @@ __device__ __forceinline__ void render_warp(const PipeArgs& a, const int gtile, 
                 if (s0 && box_keep_depth(r, bS[0], V, cull_eps, centre, &t)) k0 = depth_key(t);
                 if (s1 && box_keep_depth(r, bS[1], V, cull_eps, centre, &t)) k1 = depth_key(t);
             }
-            uint32_t r0 = 0, r1 = 0;
+            // stable rank: lanes with a smaller key, plus lanes before this one with an equal key
+            uint32_t r0 = __popc(__match_any_sync(kFull, k0) & lanemask_lt());
+            uint32_t r1 = __popc(__match_any_sync(kFull, k1) & lanemask_lt());
 #pragma unroll 8
             for (int j = 0; j < 32; j++) {
                 const uint32_t o0 = __shfl_sync(kFull, k0, j), o1 = __shfl_sync(kFull, k1, j);
-                r0 += (o0 < k0) || (o0 == k0 && j < lane);
-                r1 += (o1 < k1) || (o1 == k1 && j < lane);
+                r0 += o0 < k0;
+                r1 += o1 < k1;
             }
             const int nn0 = __popc(__ballot_sync(kFull, k0 != kInvalidKey));
             const int nn1 = __popc(__ballot_sync(kFull, k1 != kInvalidKey));
@@ -840,8 +848,9 @@ __global__ void __launch_bounds__(32 * kRenderWarps, STP_BWD_LIST_MIN_BLOCKS * 4
             grad_terms(a, c, ri, col, r.r0, alpha, val, t, T, C0, C1, C2, Z, q0, q1, qc);
             T = __fmul_rn(T, __fsub_rn(1.f, alpha));
         }
-        // lanes holding the same id (finished lanes share the id ~0 and issue nothing)
-        const unsigned peers = __match_any_sync(kFull, id);
+        // lanes holding the same id; a lane past its list takes an id of its own (no Gaussian id
+        // has the top bit set), so it stages nothing and issues nothing
+        const unsigned peers = __match_any_sync(kFull, valid ? id : (0x80000000u | lane));
         const bool solo = peers == (1u << lane);
         const int leader = __ffs(peers) - 1;
         float* sa = &sagg[wib][0];
@@ -994,15 +1003,16 @@ __global__ void __launch_bounds__(256) k_render_flat(PipeArgs a)
                     const float val = splat_value(r, c.xc, c.yc);
                     n_eval++;
                     if (!(fminf(a.alpha_max, val) >= a.eps_o)) continue;
-                    const uint32_t key = depth_key(depth_uvn(r, c.u, c.w, c.n));
+                    const float t = depth_uvn(r, c.u, c.w, c.n);
                     const uint32_t gid = sid[j];
                     if (mode == STP_MODE_GLOBAL_ID) {
-                        blend<HEAD, false, true>(a, V, s, c, key, gid, val);
+                        blend<HEAD, false, true>(a, V, s, c, t, gid, val);
                         if (s.done) break;
                     } else if (mode == STP_MODE_WINDOW_ID) {
-                        head_push<HEAD, false, true>(a, V, s, c, key, gid, val, evict_first);
+                        head_push<HEAD, false, true>(a, V, s, c, head_depth(t), gid, val, evict_first);
                         if (s.done) break;
                     } else {
+                        const uint32_t key = depth_key(t);
                         const unsigned long long ek = ((unsigned long long)key << 32) | (uint32_t)(b0 + j);
                         if ((has_last && ek <= last) || ek >= ck[HEAD - 1]) continue;
                         // keep the HEAD smallest: insert ek into the ascending ck
@@ -1030,7 +1040,7 @@ __global__ void __launch_bounds__(256) k_render_flat(PipeArgs a)
                 // blend the peeled entries nearest first (shifting keeps the indices static)
 #pragma unroll 1
                 for (int j = 0; j < nc && !s.done; j++) {
-                    blend<HEAD, false, true>(a, V, s, c, (uint32_t)(ck[0] >> 32), cid[0], cv[0]);
+                    blend<HEAD, false, true>(a, V, s, c, fkey_inv((uint32_t)(ck[0] >> 32)), cid[0], cv[0]);
 #pragma unroll
                     for (int q = 0; q + 1 < HEAD; q++) {
                         ck[q] = ck[q + 1];
