@@ -162,7 +162,8 @@ __device__ int make_record(const PipeArgs& a, const ViewDesc& V, const GaussIn& 
                 (double)V.t[k];
     if (!(pd[2] > (double)a.znear)) return invisible(a, g, count);
     if (!(g.opacity >= a.eps_o)) return invisible(a, g, count);
-    const double uxd = pd[0] / pd[2], uyd = pd[1] / pd[2];
+    const double izd = 1.0 / pd[2];               // one FP64 division (the FP64 pipe is slow here)
+    const double uxd = pd[0] * izd, uyd = pd[1] * izd;
     const double mxd = (double)V.fx * uxd + (double)V.cx, myd = (double)V.fy * uyd + (double)V.cy;
     const float p[3] = {(float)pd[0], (float)pd[1], (float)pd[2]};
     const float iz = 1.f / p[2];
@@ -539,6 +540,64 @@ __global__ void __launch_bounds__(128, STP_PRE_MIN_BLOCKS) k_preprocess(PipeArgs
     }
 }
 
+// Position of the n-th (0-based) set bit of m (m has more than n set bits).
+__device__ __forceinline__ int nth_set_bit(uint32_t m, int n)
+{
+    int pos = 0;
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const int c = __popc(m & ((1u << s) - 1u));
+        if (c <= n) {
+            n -= c;
+            m >>= s;
+            pos += s;
+        }
+    }
+    return pos;
+}
+
+// Partitioned placement of the kept tiles recorded in the lanes' masks, spread over the warp:
+// the warp's (record, kept tile) pairs are numbered by an exclusive scan of the lanes' counts
+// and taken 32 at a time, one pair per lane, so every lane works whatever its own record's
+// tile count (a lane's own loop over its tiles leaves the lanes of small records idle). A lane
+// reads the owning record again (an L1 hit: the owner just loaded it) and computes the key and
+// placement exactly as the owner would; the order inside a tile's range is fixed later by the
+// per-tile sort on (depth, id).
+__device__ void place_spread(const PipeArgs& a, int vidx, ushort4 rc, uint32_t gid, uint32_t mask)
+{
+    const int lane = threadIdx.x & 31;
+    const int n = __popc(mask);
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(kFull, incl, 31);
+    const int w = (int)rc.z - (int)rc.x;
+    for (int base = 0; base < total; base += 32) {
+        const int p = base + lane;
+        int own = 0;                                   // first lane whose inclusive count exceeds p
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1)
+            if (__shfl_sync(kFull, incl, own + st - 1) <= p) own += st;
+        const int src = p < total ? own : 0;
+        const int first = __shfl_sync(kFull, incl - n, src);
+        const uint32_t ms = __shfl_sync(kFull, mask, src);
+        const int x0 = __shfl_sync(kFull, (int)rc.x, src), y0 = __shfl_sync(kFull, (int)rc.y, src);
+        const int ws = __shfl_sync(kFull, w, src);
+        const uint32_t gs = __shfl_sync(kFull, gid, src);
+        const int vs = __shfl_sync(kFull, vidx, src);
+        if (p < total) {
+            const int k = nth_set_bit(ms, p - first);
+            const int tx = x0 + k % ws, ty = y0 + k / ws;
+            const ViewDesc& Vs = a.views[vs];
+            const Rec rs = load_rec(a.geom, Vs.rec_off + gs);
+            place_entry(a, (uint32_t)(Vs.tile_off + ty * Vs.tiles_x + tx), kept_depth_key(a, Vs, rs, tx, ty), gs);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(128, STP_DUP_MIN_BLOCKS) k_duplicate(PipeArgs a)
 {
     const RecThread th = rec_thread(a);
@@ -557,7 +616,20 @@ __global__ void __launch_bounds__(128, STP_DUP_MIN_BLOCKS) k_duplicate(PipeArgs 
     } else {
         r.r0 = r.r1 = r.r2 = r.r3 = r.r4 = r.r5 = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    const uint32_t got = tiles_pass<true>(a, V, th.v, th.live && want > 0, r, rc, off, want, (uint32_t)i, &mask);
+    bool has = th.live && want > 0;
+    if (a.partitioned && !(a.flags & 16)) {
+        // the records whose kept tiles Preprocess recorded in a mask (at most 32 candidates,
+        // not above the load-balancing threshold) are placed by the whole warp together; the
+        // rest keep the two-phase path, which then sees neither their tiles nor their mask
+        const int nc = has ? ((int)rc.z - (int)rc.x) * ((int)rc.w - (int)rc.y) : 0;
+        const bool spread = has && nc <= 32 && nc <= a.lb_threshold;
+        place_spread(a, th.v, rc, (uint32_t)i, spread ? mask : 0u);
+        if (spread) {
+            has = false;
+            mask = 0u;
+        }
+    }
+    const uint32_t got = tiles_pass<true>(a, V, th.v, has, r, rc, off, want, (uint32_t)i, &mask);
     if (th.live && got != want && !a.partitioned) {
         // Preprocess and Duplicate disagree (cannot happen with the shared rounding of the
         // decision arithmetic; kept as the paper's safety net, appendix B.4): pad with

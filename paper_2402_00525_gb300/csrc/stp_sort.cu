@@ -313,17 +313,26 @@ __device__ void seg_fix_ties(unsigned long long* x, int n)
 // fullest bucket exceeds kBucketMax takes four stable 8-bit radix passes in global memory.
 constexpr int kBucketsSmall = 1024, kBucketsLarge = 4096, kBucketMax = 512;
 
-template <int NB>
-__device__ __forceinline__ uint32_t bucket_of(uint32_t d, uint32_t kmin, unsigned long long span)
+// Bucket of depth word d: the high word of (d - kmin) * mul with mul = min(2^32 - 1,
+// floor(NB 2^32 / span)) for a tile's key span, so every bucket is < NB and the map is monotone
+// (all a bucket sort needs; the ranks inside buckets make the order exact). One multiply per
+// word instead of a 64-bit division.
+__device__ __forceinline__ uint32_t bucket_of(uint32_t d, uint32_t kmin, uint32_t mul)
 {
-    return (uint32_t)(((unsigned long long)(d - kmin) * NB) / span);
+    return __umulhi(d - kmin, mul);
+}
+template <int NB>
+__device__ __forceinline__ uint32_t bucket_mul(unsigned long long span)
+{
+    const unsigned long long m = ((unsigned long long)NB << 32) / span;
+    return m > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)m;
 }
 
 // Histogram + scan of the bucket counts; returns false (nothing written) if a bucket is too
 // full. On success bcur[b] holds the start of bucket b.
 template <int NB>
 __device__ bool bucket_plan(const unsigned long long* src, uint32_t n, uint32_t* bcnt, uint32_t* bcur,
-                            uint32_t* red, uint32_t& kmin, unsigned long long& span)
+                            uint32_t* red, uint32_t& kmin, uint32_t& mul)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t lo = 0xFFFFFFFFu, hi = 0u;
@@ -349,9 +358,9 @@ __device__ bool bucket_plan(const unsigned long long* src, uint32_t n, uint32_t*
         hi = max(hi, red[kSegWarps + w]);
     }
     kmin = lo;
-    span = (unsigned long long)(hi - lo) + 1ull;
+    mul = bucket_mul<NB>((unsigned long long)(hi - lo) + 1ull);
     for (uint32_t i = threadIdx.x; i < n; i += kSegThreads)
-        atomicAdd(&bcnt[bucket_of<NB>((uint32_t)(src[i] >> 32), kmin, span)], 1u);
+        atomicAdd(&bcnt[bucket_of((uint32_t)(src[i] >> 32), kmin, mul)], 1u);
     __syncthreads();
     // exclusive scan of the counts: thread j owns buckets kPer*j .. kPer*j + kPer - 1
     constexpr int kPer = NB / kSegThreads;
@@ -391,18 +400,18 @@ __device__ bool bucket_plan(const unsigned long long* src, uint32_t n, uint32_t*
 // output keys); otherwise to ranked[].
 template <int NB>
 __device__ void bucket_rank(const unsigned long long* src, unsigned long long* scat, uint32_t n,
-                            const uint32_t* bcnt, uint32_t* bcur, uint32_t kmin, unsigned long long span,
+                            const uint32_t* bcnt, uint32_t* bcur, uint32_t kmin, uint32_t mul,
                             unsigned long long hi, uint64_t* keys, uint32_t* vals, unsigned long long* ranked)
 {
     for (uint32_t i = threadIdx.x; i < n; i += kSegThreads) {
         const unsigned long long x = src[i];
-        scat[atomicAdd(&bcur[bucket_of<NB>((uint32_t)(x >> 32), kmin, span)], 1u)] = x;
+        scat[atomicAdd(&bcur[bucket_of((uint32_t)(x >> 32), kmin, mul)], 1u)] = x;
     }
     __syncthreads();
     // bcur[b] is now the end of bucket b
     for (uint32_t i = threadIdx.x; i < n; i += kSegThreads) {
         const unsigned long long x = scat[i];
-        const uint32_t b = bucket_of<NB>((uint32_t)(x >> 32), kmin, span);
+        const uint32_t b = bucket_of((uint32_t)(x >> 32), kmin, mul);
         const uint32_t end = bcur[b], beg = end - bcnt[b];
         uint32_t r = beg;
         for (uint32_t j = beg; j < end; j++) r += scat[j] < x;
@@ -434,21 +443,20 @@ __global__ void __launch_bounds__(kSegThreads) k_tile_sort(PipeArgs a)
     const unsigned long long hi = (unsigned long long)t << 32;
     // the Render reads only the ids; the (tile, depth) keys are written for inspection only
     uint64_t* okeys = (a.flags & kFlagDebugStats) ? a.keys + off : nullptr;
-    uint32_t kmin;
-    unsigned long long span;
+    uint32_t kmin, mul;
     if (n <= (uint32_t)kSegCap) {
         uint32_t* bcnt = reinterpret_cast<uint32_t*>(seg_smem + kSegCap);
         uint32_t* bcur = bcnt + kBucketsSmall;
-        if (bucket_plan<kBucketsSmall>(g0, n, bcnt, bcur, red, kmin, span)) {
-            bucket_rank<kBucketsSmall>(g0, seg_smem, n, bcnt, bcur, kmin, span, hi, okeys, a.vals + off, nullptr);
+        if (bucket_plan<kBucketsSmall>(g0, n, bcnt, bcur, red, kmin, mul)) {
+            bucket_rank<kBucketsSmall>(g0, seg_smem, n, bcnt, bcur, kmin, mul, hi, okeys, a.vals + off, nullptr);
             return;
         }
     } else {
         uint32_t* bcnt = reinterpret_cast<uint32_t*>(seg_smem);      // 2 x 4096 counters
         uint32_t* bcur = bcnt + kBucketsLarge;
-        if (bucket_plan<kBucketsLarge>(g0, n, bcnt, bcur, red, kmin, span)) {
+        if (bucket_plan<kBucketsLarge>(g0, n, bcnt, bcur, red, kmin, mul)) {
             // scatter into the partner range, rank back into the placed range, then write out
-            bucket_rank<kBucketsLarge>(g0, g1, n, bcnt, bcur, kmin, span, hi, nullptr, nullptr, g0);
+            bucket_rank<kBucketsLarge>(g0, g1, n, bcnt, bcur, kmin, mul, hi, nullptr, nullptr, g0);
             __syncthreads();
             for (uint32_t i = threadIdx.x; i < n; i += kSegThreads) {
                 const unsigned long long v = g0[i];
