@@ -88,8 +88,9 @@ def dist_env():
 
 
 def shard_views(all_cams, rank: int, world: int):
-    """Views are independent: rank r renders views r, r + world, ... (no data-path collective)."""
-    return list(all_cams)[rank::world]
+    """Views are independent: rank r renders views r, r + world, ... (no forward collective)."""
+    from paper_2402_00525_gb300 import distributed as D
+    return D.shard_views(all_cams, rank, world)
 
 
 def max_over_ranks(values, dist=None, device="cpu"):
@@ -437,11 +438,16 @@ def main():
     rnd.forward(g, out=out)                                   # sizes the sort-entry capacity
     gen = torch.Generator(device="cuda").manual_seed(1234)
     d_rgb = (torch.randint(0, 2, (P, 3), device="cuda", generator=gen).float() * 2 - 1) / (3 * P)
-    grads = {k: torch.zeros_like(g[k]) for k in R.FIELDS}
+    # the gradient lives in one flat buffer: with several ranks on one scene the step ends with
+    # its sum over the ranks (the one exchange of the path), reduced in place
+    from paper_2402_00525_gb300 import distributed as D
+    gflat, grads = D.gradient_buffers(g)
 
     def step():
         rnd.forward(g, out=out, check=False)
         rnd.backward(g, d_rgb, None, grads)
+        if dist:
+            D.allreduce_buffer(gflat)
 
     for _ in range(args.warmup):
         step()
@@ -464,6 +470,8 @@ def main():
         rnd.forward(g, out=out, check=False)
         ev[k][1].record()
         rnd.backward(g, d_rgb, None, grads)
+        if dist:
+            D.allreduce_buffer(gflat)            # NCCL: the per-scene gradient summed over ranks
         ev[k][2].record()
     torch.cuda.synchronize()
     launches = N.kernel_launches() - launches0
@@ -644,7 +652,8 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_gaussians": scene.n, "views_per_gpu": V, "resolution": "1920x1080",
                    "queues": "%d/%d/%d" % (prm.tail, prm.mid, prm.head), "l2": "inputs larger than L2 (708 MB scene, 3.8 GB records)",
-                   "parallelism": "views sharded over ranks" if world > 1 else "single GPU"},
+                   "parallelism": ("views sharded over ranks, gradients all-reduced (sum) each step"
+                                   if world > 1 else "single GPU")},
         "fwd_ms_per_step": fwd_ms, "fwd_bwd_ms_per_view": step_ms / V,
         "backward_modes": {"headline": "stored blend order (blend_cap %d): ms_per_step and fwd_bwd_ms_per_view"
                                        % prm.blend_cap,
@@ -687,7 +696,7 @@ def main():
         "entries_per_view_here": entries / V,
     }
     if world == 1 and not args.no_extra:
-        del rnd, out, grads
+        del rnd, out, grads, gflat
         torch.cuda.empty_cache()
         line["batching"] = batching_leg(torch, R, N, g, scene.n)
         del g
