@@ -162,7 +162,8 @@ typedef struct {                 /* byte offsets of workspace regions (for inspe
     size_t geom;                 /* [M] 96-byte render records (layout in stp_common.cuh);
                                     M = sum over views of the N of the view's scene, view
                                     after view, Gaussian id ascending within a view          */
-    size_t color;                /* [M] float4 colours                                       */
+    size_t view_z;               /* [M] float camera-space depth of the projected mean (the tile
+                                      key of STP_FLAG_VIEW_DEPTH_KEY)                         */
     size_t rect;                 /* [M] ushort4 tile rectangles [x0, y0, x1, y1)             */
     size_t counts;               /* [M] uint32 entries per (view, Gaussian)                  */
     size_t offsets;              /* [M] uint32 exclusive prefix sum of counts                */

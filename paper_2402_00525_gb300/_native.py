@@ -71,7 +71,7 @@ class RunStatus(C.Structure):
                 ("counters", C.c_uint64 * 5), ("invalid_gaussians", C.c_uint64)]
 
 
-_LAYOUT_SIZE_FIELDS = ["status", "views", "scenes", "geom", "color", "rect", "counts", "offsets", "keep_mask",
+_LAYOUT_SIZE_FIELDS = ["status", "views", "scenes", "geom", "view_z", "rect", "counts", "offsets", "keep_mask",
                        "scan_partials", "keys", "vals", "keys_alt", "vals_alt", "sorted_keys",
                        "sorted_vals", "ranges", "tfinal", "pix_state", "scratch", "dbg_nblend",
                        "dbg_hash", "dbg_delta", "grad_geom", "dbg_trace", "tile_counts", "tile_offsets",

@@ -195,7 +195,7 @@ void make_plan(const int64_t* ns, const int32_t* vps, int32_t nscenes, const stp
     L.views = take(sizeof(stp::ViewDesc) * nviews);
     L.scenes = take(sizeof(stp::SceneDesc) * nscenes);
     L.geom = take((size_t)P.m * 16 * stp::kRecFloat4);
-    L.color = take((size_t)P.m * 16);
+    L.view_z = take((size_t)P.m * 4);
     L.rect = take((size_t)P.m * 8);
     L.counts = take((size_t)P.m * 4);
     L.offsets = take((size_t)P.m * 4);
@@ -257,7 +257,7 @@ stp::PipeArgs make_args(const stp_params* p, const Plan& P, void* ws)
     a.views = (const stp::ViewDesc*)(b + L.views);
     a.status = (stp::Status*)(b + L.status);
     a.geom = (float4*)(b + L.geom);
-    a.color = (float4*)(b + L.color);
+    a.view_z = (float*)(b + L.view_z);
     a.rect = (ushort4*)(b + L.rect);
     a.counts = (uint32_t*)(b + L.counts);
     a.offsets = (uint32_t*)(b + L.offsets);

@@ -81,10 +81,13 @@ struct SceneDesc {
 // 96-byte per-(view, Gaussian) record written by Preprocess:
 //   r0 = (mean2.x hi, mean2.y hi, mean2.x lo, mean2.y lo)   mean2 = hi + lo (projected in FP64)
 //   r1 = (e.x, e.y, 1/lambda_max, 1/lambda_min)             conic A = Sigma2^-1 in eigen form
-//   r2 = (opacity, c0, c1, c2)
+//   r2 = (opacity, colour r, g, b)
 //   r3 = (m0.x, m0.y, m0.z, m1.x)
 //   r4 = (m1.y, m1.z, m2.x, m2.y)
-//   r5 = (m2.z, p.z, 0, 0)
+//   r5 = (m2.z, c0, c1, c2)
+// r0..r2 are all a blend needs (alpha and colour), so the backward over a stored blend order
+// loads three vectors per blend; r3..r5 are the depth factors. The camera-space depth p.z of
+// the mean (the tile key of ablation B only) lives in a separate float per record.
 // The conic is kept as its unit major axis e and inverse eigenvalues, so the 2D Mahalanobis
 // form q(D) = (e.D)^2 / lambda_max + (e_perp.D)^2 / lambda_min is a sum of non-negative terms,
 // and the mean as an unevaluated float pair, so D = x - mean2 keeps its relative accuracy:
@@ -191,7 +194,7 @@ __device__ __forceinline__ float depth_uvn(const Rec& r, float u, float w, float
     const float a0 = __fmaf_rn(r.r3.x, u, __fmaf_rn(r.r3.y, w, r.r3.z));
     const float a1 = __fmaf_rn(r.r3.w, u, __fmaf_rn(r.r4.x, w, r.r4.y));
     const float a2 = __fmaf_rn(r.r4.z, u, __fmaf_rn(r.r4.w, w, r.r5.x));
-    const float num = __fmaf_rn(a0, r.r2.y, __fmaf_rn(a1, r.r2.z, __fmul_rn(a2, r.r2.w)));
+    const float num = __fmaf_rn(a0, r.r5.y, __fmaf_rn(a1, r.r5.z, __fmul_rn(a2, r.r5.w)));
     const float den = __fmaf_rn(a0, a0, __fmaf_rn(a1, a1, __fmul_rn(a2, a2)));
     return __fmul_rn(n, __fdividef(num, den));
 }

@@ -25,7 +25,7 @@ struct PipeArgs {
     const ViewDesc* views;
     Status* status;
     float4* geom;            // [m*kRecFloat4]
-    float4* color;           // [V*N]
+    float* view_z;           // [V*N] camera-space depth of the mean (ablation B's tile key)
     ushort4* rect;           // [V*N]
     uint32_t* counts;        // [V*N]
     uint32_t* keep_mask;     // [V*N] kept candidate tiles of the per-thread path (bit k = k-th tile)

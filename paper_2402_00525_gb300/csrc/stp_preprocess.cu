@@ -55,12 +55,28 @@ __device__ __forceinline__ bool sh_colour(const float* __restrict__ c, int K, fl
         }
     }
     float s0 = 0.5f, s1 = 0.5f, s2 = 0.5f;
+    if (K == 16 && (reinterpret_cast<uintptr_t>(c) & 15) == 0) {
+        // degree 3 (48 floats): twelve 16-byte loads, summed in the same order as below
+        const float4* c4 = reinterpret_cast<const float4*>(c);
 #pragma unroll
-    for (int j = 0; j < 16; j++) {           // static indices: Y stays in registers
-        if (j < K) {
-            s0 += Y[j] * __ldg(c + 3 * j);
-            s1 += Y[j] * __ldg(c + 3 * j + 1);
-            s2 += Y[j] * __ldg(c + 3 * j + 2);
+        for (int q = 0; q < 4; q++) {
+            const float4 v0 = __ldg(c4 + 3 * q), v1 = __ldg(c4 + 3 * q + 1), v2 = __ldg(c4 + 3 * q + 2);
+            const float cr[4] = {v0.x, v0.w, v1.z, v2.y}, cg[4] = {v0.y, v1.x, v1.w, v2.z}, cb[4] = {v0.z, v1.y, v2.x, v2.w};
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                s0 += Y[4 * q + u] * cr[u];
+                s1 += Y[4 * q + u] * cg[u];
+                s2 += Y[4 * q + u] * cb[u];
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; j++) {           // static indices: Y stays in registers
+            if (j < K) {
+                s0 += Y[j] * __ldg(c + 3 * j);
+                s1 += Y[j] * __ldg(c + 3 * j + 1);
+                s2 += Y[j] * __ldg(c + 3 * j + 2);
+            }
         }
     }
     out[0] = fmaxf(s0, 0.f);
@@ -150,11 +166,11 @@ __device__ __forceinline__ int invalid(const PipeArgs& a, bool count)
 // (M = R_q diag(s), Sigma = M M^T), so det Sigma2 = |b0 x b1|^2 + dil (|b0|^2 + |b1|^2) + dil^2
 // is a sum of non-negative terms instead of the cancelling a c - b^2.
 __device__ int make_record(const PipeArgs& a, const ViewDesc& V, const GaussIn& g, int i,
-                           Rec& rec, float4& col, ushort4& rect, bool count)
+                           Rec& rec, float& vz, ushort4& rect, bool count)
 {
     rect = make_ushort4(0, 0, 0, 0);
     rec.r0 = rec.r1 = rec.r2 = rec.r3 = rec.r4 = rec.r5 = make_float4(0.f, 0.f, 0.f, 0.f);
-    col = make_float4(0.f, 0.f, 0.f, 0.f);
+    vz = 0.f;
     if (!g.valid) return invalid(a, count);
     double pd[3];
     for (int k = 0; k < 3; k++)
@@ -217,19 +233,20 @@ __device__ int make_record(const PipeArgs& a, const ViewDesc& V, const GaussIn& 
     }
     rec.r0 = make_float4(mx_hi, my_hi, mx_lo, my_lo);
     rec.r1 = make_float4(ex, ey, 1.f / lmax, 1.f / lmin);
-    rec.r2 = make_float4(g.opacity, c[0], c[1], c[2]);
     rec.r3 = make_float4(m[0][0], m[0][1], m[0][2], m[1][0]);
     rec.r4 = make_float4(m[1][1], m[1][2], m[2][0], m[2][1]);
-    rec.r5 = make_float4(m[2][2], p[2], 0.f, 0.f);
+    rec.r5 = make_float4(m[2][2], c[0], c[1], c[2]);
+    vz = p[2];
     // colour: SH with the direction from the camera centre to the mean
     float d[3] = {g.mu[0] - V.o[0], g.mu[1] - V.o[1], g.mu[2] - V.o[2]};
     const float dl = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     float rgb[3];
     if (!sh_colour(g.sh, g.sh_k, d[0] * dl, d[1] * dl, d[2] * dl, rgb)) {
         rec.r0 = rec.r1 = rec.r2 = rec.r3 = rec.r4 = rec.r5 = make_float4(0.f, 0.f, 0.f, 0.f);
+        vz = 0.f;
         return invalid(a, count);
     }
-    col = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
+    rec.r2 = make_float4(g.opacity, rgb[0], rgb[1], rgb[2]);
     // Candidate tiles. With the opacity-aware radius of appendix B.2, o G >= eps_O holds only on
     // the ellipse (x - mean2)^T A (x - mean2) <= t_O^2, whose axis-aligned half-widths are
     // t_O sqrt(Sigma2_xx) and t_O sqrt(Sigma2_yy) -- never more than the paper's square radius
@@ -261,13 +278,13 @@ __device__ __forceinline__ Rec shfl_rec(const Rec& r, int src)
                        __shfl_sync(kFull, r.r0.z, src), __shfl_sync(kFull, r.r0.w, src));
     o.r1 = make_float4(__shfl_sync(kFull, r.r1.x, src), __shfl_sync(kFull, r.r1.y, src),
                        __shfl_sync(kFull, r.r1.z, src), __shfl_sync(kFull, r.r1.w, src));
-    o.r2 = make_float4(__shfl_sync(kFull, r.r2.x, src), __shfl_sync(kFull, r.r2.y, src),
-                       __shfl_sync(kFull, r.r2.z, src), __shfl_sync(kFull, r.r2.w, src));
+    o.r2 = make_float4(__shfl_sync(kFull, r.r2.x, src), 0.f, 0.f, 0.f);   // opacity (no colour here)
     o.r3 = make_float4(__shfl_sync(kFull, r.r3.x, src), __shfl_sync(kFull, r.r3.y, src),
                        __shfl_sync(kFull, r.r3.z, src), __shfl_sync(kFull, r.r3.w, src));
     o.r4 = make_float4(__shfl_sync(kFull, r.r4.x, src), __shfl_sync(kFull, r.r4.y, src),
                        __shfl_sync(kFull, r.r4.z, src), __shfl_sync(kFull, r.r4.w, src));
-    o.r5 = make_float4(__shfl_sync(kFull, r.r5.x, src), __shfl_sync(kFull, r.r5.y, src), 0.f, 0.f);
+    o.r5 = make_float4(__shfl_sync(kFull, r.r5.x, src), __shfl_sync(kFull, r.r5.y, src),
+                       __shfl_sync(kFull, r.r5.z, src), __shfl_sync(kFull, r.r5.w, src));
     return o;
 }
 
@@ -278,13 +295,13 @@ __device__ __forceinline__ float tile_cull_eps(const PipeArgs& a)
 
 // Depth key of one (Gaussian, tile) pair if the tile is kept: ordered bits of t_opt on the ray
 // through the tile's x_hat (or the tile centre / the view-space depth, by flag).
-__device__ __forceinline__ bool tile_depth_key(const PipeArgs& a, const ViewDesc& V, const Rec& r,
+__device__ __forceinline__ bool tile_depth_key(const PipeArgs& a, const ViewDesc& V, const Rec& r, float vz,
                                                int tx, int ty, uint32_t* dkey)
 {
     const Box b = block_box(tx * kTile, ty * kTile, kTile, V.W, V.H);
     float t = 0.f;
     if (!box_keep_depth(r, b, V, tile_cull_eps(a), (a.flags & 4) != 0, &t)) return false;
-    if (a.flags & 8) t = r.r5.y;
+    if (a.flags & 8) t = vz;
     *dkey = fkey(t);
     return true;
 }
@@ -317,11 +334,12 @@ __device__ __forceinline__ void place_entry(const PipeArgs& a, uint32_t gt, uint
 }
 
 // depth key of a tile Preprocess found kept
-__device__ __forceinline__ uint32_t kept_depth_key(const PipeArgs& a, const ViewDesc& V, const Rec& r, int tx, int ty)
+__device__ __forceinline__ uint32_t kept_depth_key(const PipeArgs& a, const ViewDesc& V, const Rec& r, float vz,
+                                                   int tx, int ty)
 {
     const Box b = block_box(tx * kTile, ty * kTile, kTile, V.W, V.H);
     float t = box_depth(r, b, V, (a.flags & 4) != 0);
-    if (a.flags & 8) t = r.r5.y;
+    if (a.flags & 8) t = vz;
     return fkey(t);
 }
 
@@ -332,7 +350,7 @@ __device__ __forceinline__ uint32_t kept_depth_key(const PipeArgs& a, const View
 // With the global radix sort the keys go to the Gaussian's own range [off, off + want) in
 // tile order; with the partitioned sort they go to their tiles' ranges.
 template <bool EMIT>
-__device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, int vidx, bool has, const Rec& r,
+__device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, int vidx, bool has, const Rec& r, float vz,
                                ushort4 rc, uint32_t off, uint32_t want, uint32_t gid, uint32_t* mask_io)
 {
     const int lane = threadIdx.x & 31;
@@ -367,7 +385,7 @@ __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, int vidx, b
                         mask &= mask - 1;
                         const int tx = rc.x + k % w, ty = rc.y + k / w;
                         gts[j] = (uint32_t)(V.tile_off + ty * V.tiles_x + tx);
-                        dks[j] = kept_depth_key(a, V, r, tx, ty);
+                        dks[j] = kept_depth_key(a, V, r, vz, tx, ty);
                         np = j + 1;
                     }
                 }
@@ -408,7 +426,7 @@ __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, int vidx, b
                 const int tx = rc.x + k % w, ty = rc.y + k / w;
                 const uint32_t gt = (uint32_t)(V.tile_off + ty * V.tiles_x + tx);
                 uint32_t dk;
-                if (tile_depth_key(a, V, r, tx, ty, &dk)) {
+                if (tile_depth_key(a, V, r, vz, tx, ty, &dk)) {
                     if (part) {
                         place_entry(a, gt, dk, gid);
                     } else {
@@ -433,6 +451,7 @@ __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, int vidx, b
         const uint32_t offs = __shfl_sync(kFull, off, src), wants = __shfl_sync(kFull, want, src);
         const uint32_t gids = __shfl_sync(kFull, gid, src);
         const ViewDesc& Vs = a.views[__shfl_sync(kFull, vidx, src)];    // the source lane's view
+        const float vzs = __shfl_sync(kFull, vz, src);
         uint32_t base = 0;
         for (int k0 = 0; k0 < nc; k0 += 32) {
             const int k = k0 + lane;
@@ -441,7 +460,7 @@ __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, int vidx, b
             if (k < nc) {
                 const int tx = x0 + k % ws, ty = y0 + k / ws;
                 gt = (uint32_t)(Vs.tile_off + ty * Vs.tiles_x + tx);
-                if (EMIT) keep = tile_depth_key(a, Vs, rs, tx, ty, &dk);
+                if (EMIT) keep = tile_depth_key(a, Vs, rs, vzs, tx, ty, &dk);
                 else keep = tile_keep(a, rs, block_box(tx * kTile, ty * kTile, kTile, Vs.W, Vs.H));
             }
             const unsigned m = __ballot_sync(kFull, keep);
@@ -516,25 +535,25 @@ __global__ void __launch_bounds__(128, STP_PRE_MIN_BLOCKS) k_preprocess(PipeArgs
     const int i = th.i;
     const ViewDesc& V = a.views[th.v];
     Rec r;
-    float4 col;
+    float vz = 0.f;
     ushort4 rc = make_ushort4(0, 0, 0, 0);
     bool vis = false;
     if (th.live) {
         GaussIn g;
         load_gauss(a, th.S, i, g);
-        vis = make_record(a, V, g, i, r, col, rc, th.v == th.S.view_begin) == kRecVisible;
+        vis = make_record(a, V, g, i, r, vz, rc, th.v == th.S.view_begin) == kRecVisible;
     } else {
         r.r0 = r.r1 = r.r2 = r.r3 = r.r4 = r.r5 = make_float4(0.f, 0.f, 0.f, 0.f);
-        col = make_float4(0.f, 0.f, 0.f, 0.f);
+        vz = 0.f;
     }
     uint32_t mask = 0;
-    const uint32_t cnt = tiles_pass<false>(a, V, th.v, vis, r, rc, 0, 0, 0, &mask);
+    const uint32_t cnt = tiles_pass<false>(a, V, th.v, vis, r, vz, rc, 0, 0, 0, &mask);
     if (th.live) {
         const long long o = V.rec_off + i;
         a.keep_mask[o] = mask;
         float4* gp = a.geom + kRecFloat4 * o;
         gp[0] = r.r0; gp[1] = r.r1; gp[2] = r.r2; gp[3] = r.r3; gp[4] = r.r4; gp[5] = r.r5;
-        a.color[o] = col;
+        a.view_z[o] = vz;
         a.rect[o] = rc;
         a.counts[o] = cnt;
     }
@@ -563,7 +582,7 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int n)
 // reads the owning record again (an L1 hit: the owner just loaded it) and computes the key and
 // placement exactly as the owner would; the order inside a tile's range is fixed later by the
 // per-tile sort on (depth, id).
-__device__ void place_spread(const PipeArgs& a, int vidx, ushort4 rc, uint32_t gid, uint32_t mask)
+__device__ void place_spread(const PipeArgs& a, int vidx, ushort4 rc, uint32_t gid, float vz, uint32_t mask)
 {
     const int lane = threadIdx.x & 31;
     const int n = __popc(mask);
@@ -588,12 +607,13 @@ __device__ void place_spread(const PipeArgs& a, int vidx, ushort4 rc, uint32_t g
         const int ws = __shfl_sync(kFull, w, src);
         const uint32_t gs = __shfl_sync(kFull, gid, src);
         const int vs = __shfl_sync(kFull, vidx, src);
+        const float zs = __shfl_sync(kFull, vz, src);
         if (p < total) {
             const int k = nth_set_bit(ms, p - first);
             const int tx = x0 + k % ws, ty = y0 + k / ws;
             const ViewDesc& Vs = a.views[vs];
             const Rec rs = load_rec(a.geom, Vs.rec_off + gs);
-            place_entry(a, (uint32_t)(Vs.tile_off + ty * Vs.tiles_x + tx), kept_depth_key(a, Vs, rs, tx, ty), gs);
+            place_entry(a, (uint32_t)(Vs.tile_off + ty * Vs.tiles_x + tx), kept_depth_key(a, Vs, rs, zs, tx, ty), gs);
         }
     }
 }
@@ -607,8 +627,10 @@ __global__ void __launch_bounds__(128, STP_DUP_MIN_BLOCKS) k_duplicate(PipeArgs 
     Rec r;
     ushort4 rc = make_ushort4(0, 0, 0, 0);
     uint32_t off = 0, want = 0, mask = 0;
+    float vz = 0.f;
     if (th.live) {
         r = load_rec(a.geom, o);
+        if (a.flags & 8) vz = a.view_z[o];
         rc = a.rect[o];
         off = a.partitioned ? 0u : a.offsets[o];
         want = a.counts[o];
@@ -623,13 +645,13 @@ __global__ void __launch_bounds__(128, STP_DUP_MIN_BLOCKS) k_duplicate(PipeArgs 
         // rest keep the two-phase path, which then sees neither their tiles nor their mask
         const int nc = has ? ((int)rc.z - (int)rc.x) * ((int)rc.w - (int)rc.y) : 0;
         const bool spread = has && nc <= 32 && nc <= a.lb_threshold;
-        place_spread(a, th.v, rc, (uint32_t)i, spread ? mask : 0u);
+        place_spread(a, th.v, rc, (uint32_t)i, vz, spread ? mask : 0u);
         if (spread) {
             has = false;
             mask = 0u;
         }
     }
-    const uint32_t got = tiles_pass<true>(a, V, th.v, has, r, rc, off, want, (uint32_t)i, &mask);
+    const uint32_t got = tiles_pass<true>(a, V, th.v, has, r, vz, rc, off, want, (uint32_t)i, &mask);
     if (th.live && got != want && !a.partitioned) {
         // Preprocess and Duplicate disagree (cannot happen with the shared rounding of the
         // decision arithmetic; kept as the paper's safety net, appendix B.4): pad with

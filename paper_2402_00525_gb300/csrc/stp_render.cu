@@ -179,16 +179,15 @@ __device__ __forceinline__ void grad_terms(const PipeArgs& a, const PixCtx& c, l
     }
     if (c.gz != 0.f) {
         // t = |d| N / D with a_k = m_k . d, N = sum a_k c_k, D = sum a_k^2 (record layout);
-        // the depth factors r2..r5 are loaded only here
+        // the depth factors r3..r5 are loaded only here
         float* gg = a.grad_geom + ri * kGradStride;
         const float4* rp = a.geom + kRecFloat4 * ri;
-        r.r2 = __ldg(rp + 2);
         r.r3 = __ldg(rp + 3);
         r.r4 = __ldg(rp + 4);
         r.r5 = __ldg(rp + 5);
         const float u = c.u, w = c.w;
         const float m[3][3] = {{r.r3.x, r.r3.y, r.r3.z}, {r.r3.w, r.r4.x, r.r4.y}, {r.r4.z, r.r4.w, r.r5.x}};
-        const float cc[3] = {r.r2.y, r.r2.z, r.r2.w};
+        const float cc[3] = {r.r5.y, r.r5.z, r.r5.w};
         float ak[3], dak[3];
         for (int k = 0; k < 3; k++) ak[k] = m[k][0] * u + m[k][1] * w + m[k][2];
         const float num = ak[0] * cc[0] + ak[1] * cc[1] + ak[2] * cc[2];
@@ -225,7 +224,8 @@ __device__ __forceinline__ void blend(const PipeArgs& a, const ViewDesc& V, Px<H
         return;
     }
     const long long ri = V.rec_off + id;
-    const float4 col = __ldg(a.color + ri);
+    const float4 r2 = __ldg(a.geom + kRecFloat4 * ri + 2);       // (opacity, colour)
+    const float4 col = make_float4(r2.y, r2.z, r2.w, 0.f);
     const float wgt = alpha * s.T;
     s.C0 += col.x * wgt;
     s.C1 += col.y * wgt;
@@ -839,7 +839,7 @@ __global__ void __launch_bounds__(32 * kRenderWarps, STP_BWD_LIST_MIN_BLOCKS * 4
                 t = depth_uvn(r, c.u, c.w, c.n);
             }
             const float alpha = fminf(a.alpha_max, val);
-            const float4 col = __ldg(a.color + ri);
+            const float4 col = make_float4(r.r2.y, r.r2.z, r.r2.w, 0.f);   // r2 holds the colour
             const float wgt = alpha * T;
             C0 += col.x * wgt;
             C1 += col.y * wgt;

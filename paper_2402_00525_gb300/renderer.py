@@ -291,16 +291,19 @@ class Renderer:
         return ranges, keys, vals
 
     def records(self):
-        """(geom [V, N, 24], colour [V, N, 4], rect [V, N, 4], counts [V, N]) of one scene."""
+        """(geom [V, N, 24], view_z [V, N], rect [V, N, 4], counts [V, N]) of one scene. A record's
+        24 floats: projected mean as hi, lo pairs (0-3), conic in eigen form (4-7), opacity (8),
+        colour (9-11), depth factors m_0, m_1, m_2 (12-20) and c_0..c_2 (21-23); view_z is the
+        camera-space depth of the mean."""
         if self.batched:
             raise RuntimeError("records() reads single-scene workspaces")
         L = self.layout
         m = self.n * len(self.cams)
         geom = self._region(L.geom, m * 24, torch.float32).view(len(self.cams), self.n, 24)
-        color = self._region(L.color, m * 4, torch.float32).view(len(self.cams), self.n, 4)
+        view_z = self._region(L.view_z, m, torch.float32).view(len(self.cams), self.n)
         rect = self._region(L.rect, m * 4, torch.int16).view(len(self.cams), self.n, 4)
         counts = self._region(L.counts, m, torch.int32).view(len(self.cams), self.n)
-        return geom, color, rect, counts
+        return geom, view_z, rect, counts
 
 
 class StaleForwardError(RuntimeError):

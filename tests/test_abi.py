@@ -133,7 +133,7 @@ def test_batched_layout_adds_up_over_scenes(lib):
     m = sum(n * v for n, v in zip(ns, vps))
     assert L.total_tiles == sum(c.num_tiles for c in cams)
     assert L.total_pixels == sum(c.num_pixels for c in cams)
-    assert L.color + m * 16 <= L.rect                  # colour region holds one record per (view, Gaussian)
+    assert L.view_z + m * 4 <= L.rect                  # one camera-space depth per (view, Gaussian)
     assert L.grad_geom and L.total >= L.grad_geom + m * 24 * 4
     arr_n = (C.c_int64 * 3)(*ns)
     arr_v = (C.c_int32 * 3)(*vps)

@@ -41,7 +41,7 @@ def test_preprocess_records_match_oracle(oracle):
     cam = I.look_at((0.5, -0.3, -6), (0, 0, 0), (0, 1, 0), 333, 250, 50.0)
     prm = I.RenderParams()
     gpu = gpu_render(sc, [cam], prm, debug=False)
-    geom, color, rect, counts = [x.cpu().numpy() for x in gpu["renderer"].records()]
+    geom, view_z, rect, counts = [x.cpu().numpy() for x in gpu["renderer"].records()]
     with oracle.OracleRun(sc, cam, prm) as r:
         pp = r.preprocess()
     g = geom[0].astype(np.float64)
@@ -67,7 +67,7 @@ def test_preprocess_records_match_oracle(oracle):
     lam = np.linalg.eigvalsh(np.stack([np.stack([A[:, 0], A[:, 1]], 1), np.stack([A[:, 1], A[:, 2]], 1)], 1))
     assert np.allclose(np.sort(g[:, 6:8], 1), lam, rtol=2e-5)
     assert np.allclose(g[:, 8], pp["opacity"][v], rtol=1e-6)
-    assert np.allclose(color[0][v][:, :3], pp["color"][v], atol=2e-5)
+    assert np.allclose(g[:, 9:12], pp["color"][v], atol=2e-5)
     # depth factors: sum_k m_k m_k^T is the camera-space Sigma^-1 and sum_k c_k m_k = Sigma^-1 p
     Rc = cam.R
     s6 = pp["sinv6"][v]
@@ -75,7 +75,7 @@ def test_preprocess_records_match_oracle(oracle):
                    np.stack([s6[:, 2], s6[:, 4], s6[:, 5]], 1)], 1)
     Sc = Rc @ Sw @ Rc.T
     m = np.stack([g[:, 12:15], g[:, 15:18], g[:, 18:21]], 1)     # [n, k, 3]
-    cfac = g[:, 9:12]
+    cfac = g[:, 21:24]
     Sg = np.einsum("nki,nkj->nij", m, m)
     scale = np.abs(Sc).reshape(len(Sc), -1).max(1)[:, None, None]
     assert (np.abs(Sg - Sc) / scale).max() < 2e-5
@@ -86,7 +86,7 @@ def test_preprocess_records_match_oracle(oracle):
     dw = (Rc.T @ (d / np.linalg.norm(d, axis=1, keepdims=True)).T).T
     t_ora = np.einsum("ni,ni->n", dw, pp["v"][v]) / np.einsum("ni,nij,nj->n", dw, Sw, dw)
     assert np.allclose(t_gpu, t_ora, rtol=2e-6)
-    assert np.allclose(g[:, 21], pp["pcam"][v][:, 2], rtol=1e-6)
+    assert np.allclose(view_z[0][v], pp["pcam"][v][:, 2], rtol=1e-6)
     # candidate tiles: the GPU tests the tiles of the ellipse o G >= eps_O's axis-aligned box
     # (never more than the paper's square rectangle, which the oracle uses); the kept counts agree
     rr = rect[0][v].astype(np.int64)
