@@ -529,6 +529,63 @@ __device__ __forceinline__ RecThread rec_thread(const PipeArgs& a)
     return t;
 }
 
+// Tile-culling count of the records with at most 32 candidate tiles (not above the
+// load-balancing threshold), spread over the warp: the warp's (record, candidate tile) pairs are
+// numbered by a scan of the lanes' candidate counts and tested 32 at a time, one per lane, with
+// the owning record's mean, conic and opacity taken by shuffle. Each owner assembles its kept-
+// tile mask (bit k = k-th candidate, row major) from the rounds' ballots and returns its count.
+// The decisions are the ones the owner's own loop would take (same arithmetic, same inputs).
+__device__ uint32_t count_spread(const PipeArgs& a, int vidx, const Rec& r, ushort4 rc, int n, uint32_t* mask_out)
+{
+    const int lane = threadIdx.x & 31;
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(kFull, incl, 31);
+    const int first_me = incl - n;
+    const int w = (int)rc.z - (int)rc.x;
+    uint32_t mask = 0;
+    for (int base = 0; base < total; base += 32) {
+        const int p = base + lane;
+        int own = 0;                                   // first lane whose inclusive count exceeds p
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1)
+            if (__shfl_sync(kFull, incl, own + st - 1) <= p) own += st;
+        const int src = p < total ? own : 0;
+        const int first = __shfl_sync(kFull, first_me, src);
+        const int x0 = __shfl_sync(kFull, (int)rc.x, src), y0 = __shfl_sync(kFull, (int)rc.y, src);
+        const int ws = __shfl_sync(kFull, w, src);
+        const int vs = __shfl_sync(kFull, vidx, src);
+        Rec rs;                                        // what the cull test reads: mean, conic, opacity
+        rs.r0 = make_float4(__shfl_sync(kFull, r.r0.x, src), __shfl_sync(kFull, r.r0.y, src),
+                            __shfl_sync(kFull, r.r0.z, src), __shfl_sync(kFull, r.r0.w, src));
+        rs.r1 = make_float4(__shfl_sync(kFull, r.r1.x, src), __shfl_sync(kFull, r.r1.y, src),
+                            __shfl_sync(kFull, r.r1.z, src), __shfl_sync(kFull, r.r1.w, src));
+        rs.r2 = make_float4(__shfl_sync(kFull, r.r2.x, src), 0.f, 0.f, 0.f);
+        rs.r3 = rs.r4 = rs.r5 = make_float4(0.f, 0.f, 0.f, 0.f);
+        bool keep = false;
+        if (p < total) {
+            const int k = p - first;
+            const int tx = x0 + k % ws, ty = y0 + k / ws;
+            const ViewDesc& Vs = a.views[vs];
+            keep = tile_keep(a, rs, block_box(tx * kTile, ty * kTile, kTile, Vs.W, Vs.H));
+            if (keep && a.partitioned) count_entry(a, (uint32_t)(Vs.tile_off + ty * Vs.tiles_x + tx));
+        }
+        const unsigned bal = __ballot_sync(kFull, keep);
+        const int lo = max(first_me, base), hi = min(first_me + n, base + 32);
+        if (hi > lo) {
+            const int wd = hi - lo;
+            const unsigned bits = (bal >> (lo - base)) & (wd >= 32 ? 0xFFFFFFFFu : ((1u << wd) - 1u));
+            mask |= bits << (lo - first_me);
+        }
+    }
+    *mask_out = mask;
+    return (uint32_t)__popc(mask);
+}
+
 __global__ void __launch_bounds__(128, STP_PRE_MIN_BLOCKS) k_preprocess(PipeArgs a)
 {
     const RecThread th = rec_thread(a);
@@ -546,8 +603,20 @@ __global__ void __launch_bounds__(128, STP_PRE_MIN_BLOCKS) k_preprocess(PipeArgs
         r.r0 = r.r1 = r.r2 = r.r3 = r.r4 = r.r5 = make_float4(0.f, 0.f, 0.f, 0.f);
         vz = 0.f;
     }
-    uint32_t mask = 0;
-    const uint32_t cnt = tiles_pass<false>(a, V, th.v, vis, r, vz, rc, 0, 0, 0, &mask);
+    // every lane takes both calls (both hold warp-wide shuffles): the spread count for the
+    // records of at most 32 candidates, the two-phase count (its big-rectangle path) for the rest
+    uint32_t mask = 0, smask = 0, scnt = 0;
+    bool spread = false;
+    if (!(a.flags & 16)) {
+        const int nc = vis ? ((int)rc.z - (int)rc.x) * ((int)rc.w - (int)rc.y) : 0;
+        spread = vis && nc <= 32 && nc <= a.lb_threshold;
+        scnt = count_spread(a, th.v, r, rc, spread ? nc : 0, &smask);
+    }
+    uint32_t cnt = tiles_pass<false>(a, V, th.v, vis && !spread, r, vz, rc, 0, 0, 0, &mask);
+    if (spread) {
+        cnt = scnt;
+        mask = smask;
+    }
     if (th.live) {
         const long long o = V.rec_off + i;
         a.keep_mask[o] = mask;
