@@ -393,9 +393,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--per-view-rounds", type=int, default=2)
     ap.add_argument("--no-extra", action="store_true", help="skip the 64-view and 8-scene legs")
-    ap.add_argument("--profile-forward", action="store_true",
-                    help="only run warm-up + steps batched forwards (no backward flag: a small workspace), "
-                         "for profiler captures; prints the forward time")
+    ap.add_argument("--views", type=int, default=16, help="views per GPU (default: the workload's 16)")
+    ap.add_argument("--profile", choices=["forward", "step"], default=None,
+                    help="only run warm-up + steps of the batched forward (no backward flag: a small "
+                         "workspace) or of the forward + backward step, for profiler captures")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -418,20 +419,25 @@ def main():
     from paper_2402_00525_gb300 import renderer as R
 
     scene, _, prm = I.full_hd_workload(n=args.n, nviews=1)
-    all_cams = I.orbit_cameras(16 * world, 15.0, 2.0, I.C2_SIZES, 50.0)
+    all_cams = I.orbit_cameras(args.views * world, 15.0, 2.0, I.C2_SIZES, 50.0)
     cams = shard_views(all_cams, rank, world)
     V = len(cams)
     P = sum(c.num_pixels for c in cams)
     g = R.scene_to_device(scene)
-    if args.profile_forward:
-        fr = R.Renderer(scene.n, cams, prm)
+    if args.profile:
+        step_too = args.profile == "step"
+        fr = R.Renderer(scene.n, cams, prm, backward=step_too)
         fr.forward(g)                                        # sizes the capacity (may render twice)
+        d = torch.full((P, 3), 1.0 / (3 * P), device="cuda")
+        gr = {k: torch.zeros_like(g[k]) for k in R.FIELDS}
         for _ in range(args.warmup + args.steps):
             fr.forward(g, check=False)
+            if step_too:
+                fr.backward(g, d, None, gr)
         torch.cuda.synchronize()
         assert fr.status().error_bits == 0
-        print(json.dumps({"profile_forward": True, "gaussians": scene.n, "views": V,
-                          "launches_per_forward": 9}), flush=True)
+        print(json.dumps({"profile": args.profile, "gaussians": scene.n, "views": V,
+                          "workspace_gb": fr.workspace_bytes / 1e9}), flush=True)
         return
     rnd = R.Renderer(scene.n, cams, prm, backward=True)
     out = (torch.empty((P, 3), device="cuda"), torch.empty((P,), device="cuda"), torch.empty((P,), device="cuda"))
