@@ -157,12 +157,83 @@ __device__ __forceinline__ int invalid(const PipeArgs& a, bool count)
     return kRecInvalid;
 }
 
+// ---------------------------------------------------------------- float-float arithmetic
+// An unevaluated pair hi + lo of FP32 values (about 44 significant bits) built from the
+// error-free transformations of Dekker and Knuth: the product of two floats is exactly
+// p + e with p = a*b rounded and e = fma(a, b, -p); the sum is exactly s + e with Knuth's
+// six-operation two-sum. The FP64 pipe of this GPU issues at 1/64 of the FP32 rate, so these
+// pairs carry the precision the projected mean and the depth factors need.
+struct ff { float hi, lo; };
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ ff renorm(float s, float e)      // |e| small against s
+{
+    const float h = __fadd_rn(s, e);
+    return ff{h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+// c + sum_j a_j b_j over three terms, compensated: accurate to about the pair's precision
+__device__ __forceinline__ ff dot3_ff(const float a[3], const float b[3], float c)
+{
+    float s = c, err = 0.f;
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        const float p = __fmul_rn(a[j], b[j]);
+        const float pe = __fmaf_rn(a[j], b[j], -p);
+        float e;
+        two_sum(s, p, s, e);
+        err = __fadd_rn(err, __fadd_rn(e, pe));
+    }
+    return renorm(s, err);
+}
+// sum_j a_j x_j with float a_j and pair x_j
+__device__ __forceinline__ ff dot3_f_ff(const float a[3], const ff x[3])
+{
+    float s = 0.f, err = 0.f;
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        const float p = __fmul_rn(a[j], x[j].hi);
+        const float pe = __fmaf_rn(a[j], x[j].hi, -p);
+        float e;
+        two_sum(s, p, s, e);
+        err = __fadd_rn(err, __fadd_rn(e, __fmaf_rn(a[j], x[j].lo, pe)));
+    }
+    return renorm(s, err);
+}
+__device__ __forceinline__ ff mul_ff(ff x, ff y)
+{
+    const float p = __fmul_rn(x.hi, y.hi);
+    const float e = __fmaf_rn(x.hi, y.hi, -p);
+    return renorm(p, __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, e)));
+}
+__device__ __forceinline__ ff rcp_ff(ff x)                  // 1 / x, one Newton correction
+{
+    const float y = __frcp_rn(x.hi);
+    const float p = __fmul_rn(x.hi, y);
+    const float pe = __fmaf_rn(x.hi, y, -p);
+    const float r = __fsub_rn(__fsub_rn(__fsub_rn(1.f, p), pe), __fmul_rn(x.lo, y));   // 1 - x y
+    return renorm(y, __fmul_rn(y, r));
+}
+// a x + b with float a, b and pair x
+__device__ __forceinline__ ff fma_f_ff(float a, ff x, float b)
+{
+    const float p = __fmul_rn(a, x.hi);
+    const float pe = __fmaf_rn(a, x.hi, -p);
+    float s, e;
+    two_sum(p, b, s, e);
+    return renorm(s, __fadd_rn(e, __fmaf_rn(a, x.lo, pe)));
+}
+
 // Per-(view, Gaussian) record (layout in stp_common.cuh). Returns kRecVisible, kRecInvisible
 // (near plane, opacity below eps_O, degenerate splat: the colour is not evaluated) or
 // kRecInvalid (non-finite inputs); the record stays zero unless visible.
-// The camera-space mean and its projection are evaluated in FP64 (a handful of operations per
-// Gaussian and view): mean2 is ~1e3 px, where an FP32 rounding of 6e-5 px would move the alpha
-// of a sub-pixel-wide splat by ~1e-3 relative. Sigma2 = B B^T + dilation I with B = T M
+// The camera-space mean and its projection are evaluated in float-float pairs (about 44 bits):
+// mean2 is ~1e3 px, where an FP32 rounding of 6e-5 px would move the alpha of a sub-pixel-wide
+// splat by ~1e-3 relative; the record keeps mean2 as such a pair. Sigma2 = B B^T + dilation I with B = T M
 // (M = R_q diag(s), Sigma = M M^T), so det Sigma2 = |b0 x b1|^2 + dil (|b0|^2 + |b1|^2) + dil^2
 // is a sum of non-negative terms instead of the cancelling a c - b^2.
 __device__ int make_record(const PipeArgs& a, const ViewDesc& V, const GaussIn& g, int i,
@@ -172,18 +243,19 @@ __device__ int make_record(const PipeArgs& a, const ViewDesc& V, const GaussIn& 
     rec.r0 = rec.r1 = rec.r2 = rec.r3 = rec.r4 = rec.r5 = make_float4(0.f, 0.f, 0.f, 0.f);
     vz = 0.f;
     if (!g.valid) return invalid(a, count);
-    double pd[3];
-    for (int k = 0; k < 3; k++)
-        pd[k] = (double)V.R[3 * k] * g.mu[0] + (double)V.R[3 * k + 1] * g.mu[1] + (double)V.R[3 * k + 2] * g.mu[2] +
-                (double)V.t[k];
-    if (!(pd[2] > (double)a.znear)) return invisible(a, g, count);
+    ff pd[3];                                     // camera-space mean R mu + t
+    for (int k = 0; k < 3; k++) {
+        const float rk[3] = {V.R[3 * k], V.R[3 * k + 1], V.R[3 * k + 2]};
+        pd[k] = dot3_ff(rk, g.mu, V.t[k]);
+    }
+    if (!(pd[2].hi > a.znear)) return invisible(a, g, count);
     if (!(g.opacity >= a.eps_o)) return invisible(a, g, count);
-    const double izd = 1.0 / pd[2];               // one FP64 division (the FP64 pipe is slow here)
-    const double uxd = pd[0] * izd, uyd = pd[1] * izd;
-    const double mxd = (double)V.fx * uxd + (double)V.cx, myd = (double)V.fy * uyd + (double)V.cy;
-    const float p[3] = {(float)pd[0], (float)pd[1], (float)pd[2]};
+    const ff izd = rcp_ff(pd[2]);
+    const ff uxd = mul_ff(pd[0], izd), uyd = mul_ff(pd[1], izd);
+    const ff mxd = fma_f_ff(V.fx, uxd, V.cx), myd = fma_f_ff(V.fy, uyd, V.cy);
+    const float p[3] = {pd[0].hi, pd[1].hi, pd[2].hi};
     const float iz = 1.f / p[2];
-    const float ux = (float)uxd, uy = (float)uyd;
+    const float ux = uxd.hi, uy = uyd.hi;
     const float cx = fminf(V.limx, fmaxf(-V.limx, ux)), cy = fminf(V.limy, fmaxf(-V.limy, uy));
     const float J00 = V.fx * iz, J02 = -V.fx * cx * iz, J11 = V.fy * iz, J12 = -V.fy * cy * iz;
     float T[2][3];
@@ -222,14 +294,15 @@ __device__ int make_record(const PipeArgs& a, const ViewDesc& V, const GaussIn& 
         ex = 1.f;
         ey = 0.f;
     }
-    const float mx_hi = (float)mxd, my_hi = (float)myd;
-    const float mx_lo = (float)(mxd - (double)mx_hi), my_lo = (float)(myd - (double)my_hi);
+    const float mx_hi = mxd.hi, my_hi = myd.hi;
+    const float mx_lo = mxd.lo, my_lo = myd.lo;
     // camera-space axes scaled by the clamped inverse scales, and their projections of p
     float m[3][3], c[3];
     for (int k = 0; k < 3; k++) {
         for (int r = 0; r < 3; r++)
             m[k][r] = g.si[k] * (V.R[3 * r] * g.Rq[k] + V.R[3 * r + 1] * g.Rq[3 + k] + V.R[3 * r + 2] * g.Rq[6 + k]);
-        c[k] = (float)((double)m[k][0] * pd[0] + (double)m[k][1] * pd[1] + (double)m[k][2] * pd[2]);
+        const ff ck = dot3_f_ff(m[k], pd);
+        c[k] = __fadd_rn(ck.hi, ck.lo);
     }
     rec.r0 = make_float4(mx_hi, my_hi, mx_lo, my_lo);
     rec.r1 = make_float4(ex, ey, 1.f / lmax, 1.f / lmin);
@@ -260,7 +333,7 @@ __device__ int make_record(const PipeArgs& a, const ViewDesc& V, const GaussIn& 
     const bool square = (a.flags & kFlagNoTileCull) != 0;
     const float hx = square ? rad : fminf(rad, fmaf(tO * sqrtf(ca), 1.0001f, 0.01f));
     const float hy = square ? rad : fminf(rad, fmaf(tO * sqrtf(cc), 1.0001f, 0.01f));
-    const float mx = (float)mxd, my = (float)myd;
+    const float mx = mxd.hi, my = myd.hi;
     const float fx0 = ceilf((mx - hx - 15.5f) * (1.f / 16.f)), fx1 = floorf((mx + hx - 0.5f) * (1.f / 16.f));
     const float fy0 = ceilf((my - hy - 15.5f) * (1.f / 16.f)), fy1 = floorf((my + hy - 0.5f) * (1.f / 16.f));
     const int tx0 = (int)fmaxf(0.f, fx0), ty0 = (int)fmaxf(0.f, fy0);
