@@ -110,7 +110,6 @@ __global__ void __launch_bounds__(128, STP_BWDPRE_MIN_BLOCKS) k_backward_pre(Pip
     for (int v = S.view_begin; v < S.view_end; v++) {
         const ViewDesc& V = a.views[v];
         const long long ri = V.rec_off + i;
-        if (a.geom[kRecFloat4 * ri + 2].x == 0.f) continue;      // invisible in this view
         const float4* gg = reinterpret_cast<const float4*>(a.grad_geom + ri * kGradStride);
         float g[24];
         bool nz = false;
@@ -124,6 +123,8 @@ __global__ void __launch_bounds__(128, STP_BWDPRE_MIN_BLOCKS) k_backward_pre(Pip
         }
 #pragma unroll
         for (int k = 0; k < 24; k++) nz |= g[k] != 0.f;
+        // no pixel blended this (view, Gaussian): nothing to chain (this also skips the views
+        // where it is invisible, whose scratch stays zero, without reading their records)
         if (!nz) continue;
         any = true;
         float p[3];
