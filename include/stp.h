@@ -182,7 +182,8 @@ typedef struct {                 /* byte offsets of workspace regions (for inspe
     size_t dbg_hash;             /* [total pixels] uint64 blend-order hash (flag 32), else 0 */
     size_t dbg_delta;            /* [total pixels] float sort error delta (flag 32): the sum
                                     of t_opt steps backwards along the blend order (Sec. 3.3) */
-    size_t grad_geom;            /* [M*24] float backward scratch (flag 64), else 0          */
+    size_t grad_geom;            /* [M*24] float backward scratch (flag 64), else 0: M*12 alpha and
+                                    colour terms, then M*12 depth-factor terms (used with d_depth) */
     size_t dbg_trace;            /* [total pixels][STP_TRACE_LEN] int32 blend ids (flag 128)  */
     size_t tile_counts;          /* [total tiles] uint32 entries per tile (partitioned sort)  */
     size_t tile_offsets;         /* [total tiles] uint32 first entry of each tile            */

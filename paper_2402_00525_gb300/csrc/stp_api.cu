@@ -223,7 +223,7 @@ void make_plan(const int64_t* ns, const int32_t* vps, int32_t nscenes, const stp
     L.tile_cursor = take((size_t)tiles * 4);
     L.tile_partials = take(stp::scan_partials_count(tiles) * 8);
     L.grad_geom = 0;
-    if (p->flags & kFlagBackward) L.grad_geom = take((size_t)P.m * stp::kGradStride * 4);
+    if (p->flags & kFlagBackward) L.grad_geom = take((size_t)P.m * 2 * stp::kGradStride * 4);   // both regions
     L.blend_ids = L.blend_count = L.replay_warps = 0;
     if ((p->flags & kFlagBackward) && p->mode == STP_MODE_HIER && p->blend_cap > 0) {
         L.blend_ids = take((size_t)tiles * 256 * (size_t)p->blend_cap * 4);
@@ -282,6 +282,7 @@ stp::PipeArgs make_args(const stp_params* p, const Plan& P, void* ws)
     a.sort_temp_bytes = stp::sort_hist_bytes();
     a.key_bits = L.key_bits;
     a.grad_geom = L.grad_geom ? (float*)(b + L.grad_geom) : nullptr;
+    a.grad_depth = L.grad_geom ? a.grad_geom + (size_t)P.m * stp::kGradStride : nullptr;
     a.blist = L.blend_ids ? (uint32_t*)(b + L.blend_ids) : nullptr;
     a.blist_count = L.blend_count ? (uint32_t*)(b + L.blend_count) : nullptr;
     a.replay_warps = L.replay_warps ? (uint32_t*)(b + L.replay_warps) : nullptr;
@@ -423,7 +424,9 @@ stp_status backward_impl(const stp_gaussians* scenes, int32_t nscenes, const int
                                      nscenes, const_cast<stp::SceneDesc*>(a.scenes), s)) != cudaSuccess)
         return cuda_fail(e, "view and scene tables");
     prof_mark(5, s);
-    if ((e = cudaMemsetAsync(a.grad_geom, 0, (size_t)P.m * stp::kGradStride * 4, s)) != cudaSuccess)
+    // the depth-factor region is written (and read) only when the loss has a depth term
+    const size_t scratch = (size_t)P.m * stp::kGradStride * 4 * (a.d_depth ? 2 : 1);
+    if ((e = cudaMemsetAsync(a.grad_geom, 0, scratch, s)) != cudaSuccess)
         return cuda_fail(e, "clear gradient scratch");
     // empty replay queue (the stored-order kernel fills it)
     if (a.blist && (e = cudaMemsetAsync(&a.status->replay_n, 0, 2 * sizeof(unsigned int), s)) != cudaSuccess)

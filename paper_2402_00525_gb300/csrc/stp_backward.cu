@@ -111,11 +111,13 @@ __global__ void __launch_bounds__(128, STP_BWDPRE_MIN_BLOCKS) k_backward_pre(Pip
         const ViewDesc& V = a.views[v];
         const long long ri = V.rec_off + i;
         const float4* gg = reinterpret_cast<const float4*>(a.grad_geom + ri * kGradStride);
+        const float4* gd = reinterpret_cast<const float4*>(a.grad_depth + ri * kGradStride);
         float g[24];
         bool nz = false;
 #pragma unroll
         for (int k = 0; k < 6; k++) {
-            const float4 q = gg[k];
+            // g[12..23], the depth-factor terms, exist only when the loss has a depth term
+            const float4 q = k < 3 ? gg[k] : (a.d_depth ? gd[k - 3] : make_float4(0.f, 0.f, 0.f, 0.f));
             g[4 * k] = q.x;
             g[4 * k + 1] = q.y;
             g[4 * k + 2] = q.z;

@@ -62,7 +62,8 @@ struct PipeArgs {
     // backward
     const float* d_rgb;
     const float* d_depth;
-    float* grad_geom;        // [m*kGradStride] per-(view, Gaussian) 2D gradients
+    float* grad_geom;        // [m*kGradStride] per-(view, Gaussian) 2D gradients (alpha and colour terms)
+    float* grad_depth;       // [m*kGradStride] the depth-factor terms (written only with d_depth)
     // stored blend order (HIER forward with a backward to follow): per tile warp (8 per tile)
     // blend_cap x 32 ids, slot k of lane l at (warp * blend_cap + k) * 32 + l; null = replay
     uint32_t* blist;
@@ -97,7 +98,10 @@ __device__ __forceinline__ int scene_of_rec(const PipeArgs& a, long long t0)
 }
 
 constexpr int kTraceLen = 64;
-constexpr int kGradStride = 24;   // sum dGG d(2) dconic(3) sum dGG(1) dcolour(3) pad(3) dm(9) dc(3)
+// gradient scratch per (view, Gaussian), two regions of kGradStride floats a record:
+// grad_geom: sum dGG d (2), dconic (3), sum dGG (1), dcolour (3), pad (3);
+// grad_depth: dm (9), dc (3) -- cleared and read only when the loss has a depth term
+constexpr int kGradStride = 12;
 
 cudaError_t launch_tables_init(const ViewDesc* host_views, int nviews, ViewDesc* dev_views,
                                const SceneDesc* host_scenes, int nscenes, SceneDesc* dev_scenes,

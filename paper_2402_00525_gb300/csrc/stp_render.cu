@@ -146,10 +146,10 @@ struct PixCtx {
 // Gradient terms of one blended Gaussian (Sec. 3.5), given the pixel's state just after the
 // blend: T = T_i (transmittance in front of it), C / Z = colour and depth accumulated up to
 // and including it. dL/dalpha_i uses the suffix C_final - C_i and T_N / (1 - alpha_i).
-// Per-(view, Gaussian) scratch, 24 floats: [0..7] (sum dGG d.xy, dA00, dA01, dA11, sum dGG,
-// dcolour.rg), [8] dcolour.b, [12..23] depth factors (dm_k 9, dc_k 3). The first nine are
-// returned in (q0, q1, qc) for the caller to accumulate; the depth factors (only with a
-// depth gradient) are accumulated here with vector reductions (red.global.add.v4.f32).
+// Per-(view, Gaussian) scratch: [0..7] (sum dGG d.xy, dA00, dA01, dA11, sum dGG, dcolour.rg),
+// [8] dcolour.b in grad_geom, and the depth factors (dm_k 9, dc_k 3) in grad_depth. The first
+// nine are returned in (q0, q1, qc) for the caller to accumulate; the depth factors (only with
+// a depth gradient) are accumulated here with vector reductions (red.global.add.v4.f32).
 __device__ __forceinline__ void grad_terms(const PipeArgs& a, const PixCtx& c, long long ri, const float4 col,
                                            const float4 r0, float alpha, float val, float t, float T,
                                            float C0, float C1, float C2, float Z,
@@ -180,7 +180,7 @@ __device__ __forceinline__ void grad_terms(const PipeArgs& a, const PixCtx& c, l
     if (c.gz != 0.f) {
         // t = |d| N / D with a_k = m_k . d, N = sum a_k c_k, D = sum a_k^2 (record layout);
         // the depth factors r3..r5 are loaded only here
-        float* gg = a.grad_geom + ri * kGradStride;
+        float* gd = a.grad_depth + ri * kGradStride;
         const float4* rp = a.geom + kRecFloat4 * ri;
         r.r3 = __ldg(rp + 3);
         r.r4 = __ldg(rp + 4);
@@ -197,9 +197,9 @@ __device__ __forceinline__ void grad_terms(const PipeArgs& a, const PixCtx& c, l
         const float tq = num / den;
         for (int k = 0; k < 3; k++) dak[k] = dt * n * (cc[k] - 2.f * tq * ak[k]) / den;   // dt/da_k
         const float fc = dt * n / den;                                                   // dt/dc_k = fc a_k
-        atomicAdd(reinterpret_cast<float4*>(gg + 12), make_float4(dak[0] * u, dak[0] * w, dak[0], dak[1] * u));
-        atomicAdd(reinterpret_cast<float4*>(gg + 16), make_float4(dak[1] * w, dak[1], dak[2] * u, dak[2] * w));
-        atomicAdd(reinterpret_cast<float4*>(gg + 20), make_float4(dak[2], fc * ak[0], fc * ak[1], fc * ak[2]));
+        atomicAdd(reinterpret_cast<float4*>(gd), make_float4(dak[0] * u, dak[0] * w, dak[0], dak[1] * u));
+        atomicAdd(reinterpret_cast<float4*>(gd + 4), make_float4(dak[1] * w, dak[1], dak[2] * u, dak[2] * w));
+        atomicAdd(reinterpret_cast<float4*>(gd + 8), make_float4(dak[2], fc * ak[0], fc * ak[1], fc * ak[2]));
     }
 }
 
