@@ -722,7 +722,8 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int n)
 // and taken 32 at a time, one pair per lane, so every lane works whatever its own record's
 // tile count (a lane's own loop over its tiles leaves the lanes of small records idle). A lane
 // reads the owning record again (an L1 hit: the owner just loaded it) and computes the key and
-// placement exactly as the owner would; the order inside a tile's range is fixed later by the
+// placement exactly as the owner would; lanes of a round that place into the same tile take
+// their slots with one cursor atomic. The order inside a tile's range is fixed later by the
 // per-tile sort on (depth, id).
 __device__ void place_spread(const PipeArgs& a, int vidx, ushort4 rc, uint32_t gid, float vz, uint32_t mask)
 {
@@ -750,19 +751,65 @@ __device__ void place_spread(const PipeArgs& a, int vidx, ushort4 rc, uint32_t g
         const uint32_t gs = __shfl_sync(kFull, gid, src);
         const int vs = __shfl_sync(kFull, vidx, src);
         const float zs = __shfl_sync(kFull, vz, src);
+        uint32_t gt = 0xFFFFFFFFu - lane, dk = 0;
         if (p < total) {
             const int k = nth_set_bit(ms, p - first);
             const int tx = x0 + k % ws, ty = y0 + k / ws;
             const ViewDesc& Vs = a.views[vs];
             const Rec rs = load_rec(a.geom, Vs.rec_off + gs);
-            place_entry(a, (uint32_t)(Vs.tile_off + ty * Vs.tiles_x + tx), kept_depth_key(a, Vs, rs, zs, tx, ty), gs);
+            gt = (uint32_t)(Vs.tile_off + ty * Vs.tiles_x + tx);
+            dk = kept_depth_key(a, Vs, rs, zs, tx, ty);
+        }
+        // lanes placing into the same tile reserve their slots with one cursor atomic
+        const unsigned peers = __match_any_sync(kFull, gt);
+        const int leader = __ffs(peers) - 1;
+        uint32_t sbase = 0;
+        if (p < total && lane == leader) sbase = atomicAdd(&a.tile_cursor[gt], (uint32_t)__popc(peers));
+        sbase = __shfl_sync(kFull, sbase, leader);
+        if (p < total) {
+            const uint32_t slot = sbase + __popc(peers & lanemask_lt());
+            if (slot >= a.tile_counts[gt]) {
+                atomicOr(&a.status->error_bits, 2u);
+            } else {
+                const unsigned long long pos = (unsigned long long)a.tile_offsets[gt] + slot;
+                if (pos < a.capacity) a.dup_keys[pos] = ((unsigned long long)dk << 32) | gs;
+            }
         }
     }
 }
 
+// Duplicate's mapping: thread t of the scene takes Gaussian t % n of view view_begin + t / n,
+// so a warp holds consecutive Gaussians of one view: its record loads are coalesced, and
+// neighbouring Gaussians (close in space in a trained or clustered scene) often share tiles,
+// whose lanes then reserve their slots together (place_spread). Preprocess keeps the views of a
+// Gaussian in neighbouring lanes, which read its SH coefficients once.
+__device__ __forceinline__ RecThread rec_thread_view_major(const PipeArgs& a)
+{
+    RecThread t;
+    const long long t0 = (long long)blockIdx.x * blockDim.x;
+    t.S = a.scenes[scene_of_rec(a, t0)];
+    const int nv = t.S.view_end - t.S.view_begin;
+    const long long lt = t0 - t.S.rec_thread_off + threadIdx.x;
+    const long long n = t.S.n;
+    long long q = 0, rm = 0;
+    if (n > 0) {
+        if (lt < 0xFFFFFFFFll && n < 0xFFFFFFFFll) {
+            q = (uint32_t)lt / (uint32_t)n;
+            rm = (uint32_t)lt - (uint32_t)q * (uint32_t)n;
+        } else {
+            q = lt / n;
+            rm = lt - q * n;
+        }
+    }
+    t.i = (int)rm;
+    t.v = t.S.view_begin + (int)(q < nv ? q : 0);
+    t.live = n > 0 && q < nv;
+    return t;
+}
+
 __global__ void __launch_bounds__(128, STP_DUP_MIN_BLOCKS) k_duplicate(PipeArgs a)
 {
-    const RecThread th = rec_thread(a);
+    const RecThread th = rec_thread_view_major(a);
     const int i = th.i;
     const ViewDesc& V = a.views[th.v];
     const long long o = V.rec_off + i;
