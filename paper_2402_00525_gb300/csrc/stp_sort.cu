@@ -328,6 +328,19 @@ __device__ __forceinline__ uint32_t bucket_mul(unsigned long long span)
     return m > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)m;
 }
 
+// The passes over a tile's words are load-latency bound: each thread fetches the four words
+// i0 + u*kSegThreads (u < 4) before it uses any of them; words past n read as 0 and are skipped.
+constexpr int kSegUnroll = 4;
+__device__ __forceinline__ void load_words(const unsigned long long* src, uint32_t i0, uint32_t n,
+                                           unsigned long long (&w)[kSegUnroll])
+{
+#pragma unroll
+    for (int u = 0; u < kSegUnroll; u++) {
+        const uint32_t i = i0 + u * kSegThreads;
+        w[u] = i < n ? src[i] : 0ull;
+    }
+}
+
 // Histogram + scan of the bucket counts; returns false (nothing written) if a bucket is too
 // full. On success bcur[b] holds the start of bucket b.
 template <int NB>
@@ -336,10 +349,16 @@ __device__ bool bucket_plan(const unsigned long long* src, uint32_t n, uint32_t*
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t lo = 0xFFFFFFFFu, hi = 0u;
-    for (uint32_t i = threadIdx.x; i < n; i += kSegThreads) {
-        const uint32_t d = (uint32_t)(src[i] >> 32);
-        lo = min(lo, d);
-        hi = max(hi, d);
+    for (uint32_t i0 = threadIdx.x; i0 < n; i0 += kSegUnroll * kSegThreads) {
+        unsigned long long w[kSegUnroll];
+        load_words(src, i0, n, w);
+#pragma unroll
+        for (int u = 0; u < kSegUnroll; u++) {
+            if (i0 + u * kSegThreads >= n) break;
+            const uint32_t d = (uint32_t)(w[u] >> 32);
+            lo = min(lo, d);
+            hi = max(hi, d);
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         lo = min(lo, __shfl_xor_sync(kFull, lo, o));
@@ -359,8 +378,15 @@ __device__ bool bucket_plan(const unsigned long long* src, uint32_t n, uint32_t*
     }
     kmin = lo;
     mul = bucket_mul<NB>((unsigned long long)(hi - lo) + 1ull);
-    for (uint32_t i = threadIdx.x; i < n; i += kSegThreads)
-        atomicAdd(&bcnt[bucket_of((uint32_t)(src[i] >> 32), kmin, mul)], 1u);
+    for (uint32_t i0 = threadIdx.x; i0 < n; i0 += kSegUnroll * kSegThreads) {
+        unsigned long long w[kSegUnroll];
+        load_words(src, i0, n, w);
+#pragma unroll
+        for (int u = 0; u < kSegUnroll; u++) {
+            if (i0 + u * kSegThreads >= n) break;
+            atomicAdd(&bcnt[bucket_of((uint32_t)(w[u] >> 32), kmin, mul)], 1u);
+        }
+    }
     __syncthreads();
     // exclusive scan of the counts: thread j owns buckets kPer*j .. kPer*j + kPer - 1
     constexpr int kPer = NB / kSegThreads;
@@ -403,9 +429,14 @@ __device__ void bucket_rank(const unsigned long long* src, unsigned long long* s
                             const uint32_t* bcnt, uint32_t* bcur, uint32_t kmin, uint32_t mul,
                             unsigned long long hi, uint64_t* keys, uint32_t* vals, unsigned long long* ranked)
 {
-    for (uint32_t i = threadIdx.x; i < n; i += kSegThreads) {
-        const unsigned long long x = src[i];
-        scat[atomicAdd(&bcur[bucket_of((uint32_t)(x >> 32), kmin, mul)], 1u)] = x;
+    for (uint32_t i0 = threadIdx.x; i0 < n; i0 += kSegUnroll * kSegThreads) {
+        unsigned long long w[kSegUnroll];
+        load_words(src, i0, n, w);
+#pragma unroll
+        for (int u = 0; u < kSegUnroll; u++) {
+            if (i0 + u * kSegThreads >= n) break;
+            scat[atomicAdd(&bcur[bucket_of((uint32_t)(w[u] >> 32), kmin, mul)], 1u)] = w[u];
+        }
     }
     __syncthreads();
     // bcur[b] is now the end of bucket b
