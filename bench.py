@@ -574,7 +574,7 @@ def main():
     torch.cuda.synchronize()
     rp_rel = max(float((one[k] - two[k]).double().norm() / max(two[k].double().norm().item(), 1e-30)) for k in R.FIELDS)
     replay = {"fwd_bwd_ms_per_view": rp_step / V, "ms_per_step": rp_step, "fwd_ms": rp_fwd,
-              "stage_ms": {"forward": {n: round(float(x), 4) for n, x in zip(N.STAGE_NAMES, rp_stages[0::2].mean(0))},
+              "stage_ms": {"forward": {n: round(float(x), 4) for n, x in zip(N.FWD_STAGE_NAMES, rp_stages[0::2].mean(0))},
                            "backward": {n: round(float(x), 4) for n, x in zip(N.STAGE_NAMES, rp_stages[1::2].mean(0))}},
               "grad_rel_l2_vs_stored_order": rp_rel,
               "note": "blend_cap 0: the backward replays the hierarchical queues (recomputed k-buffers, no "
@@ -666,7 +666,7 @@ def main():
                            "stored_order": {"fwd_bwd_ms_per_view": step_ms / V, "ms_per_step": step_ms,
                                             "workspace_gb": rnd_ws_gb},
                            "replay": replay},
-        "stage_ms": {"forward": {n: round(float(x), 4) for n, x in zip(N.STAGE_NAMES, fwd_stage)},
+        "stage_ms": {"forward": {n: round(float(x), 4) for n, x in zip(N.FWD_STAGE_NAMES, fwd_stage)},
                      "backward": {n: round(float(x), 4) for n, x in zip(N.STAGE_NAMES, bwd_stage)}},
         "per_view": {"fwd_mpix_s": total_px / world / (pv_ms * 1e-3) / 1e6, "fwd_ms_16_views": pv_ms,
                      "batched_speedup": pv_ms / fwd_ms, "identical_to_batched": bool(same)},

@@ -62,20 +62,21 @@ class Params(C.Structure):
                 ("frustum_clamp", C.c_float), ("znear", C.c_float), ("bg", C.c_float * 3),
                 ("mode", C.c_int32), ("window_k", C.c_int32), ("flags", C.c_int32),
                 ("blend_cap", C.c_int32), ("max_entries", C.c_int64), ("full_max_passes", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("slice_k", C.c_int32)]
 
 
 class RunStatus(C.Structure):
     _fields_ = [("error_bits", C.c_uint32), ("mismatched", C.c_uint32),
                 ("num_entries", C.c_uint64), ("capacity", C.c_uint64),
-                ("counters", C.c_uint64 * 5), ("invalid_gaussians", C.c_uint64)]
+                ("counters", C.c_uint64 * 5), ("invalid_gaussians", C.c_uint64), ("redo_warps", C.c_uint64)]
 
 
 _LAYOUT_SIZE_FIELDS = ["status", "views", "scenes", "geom", "view_z", "rect", "counts", "offsets", "keep_mask",
                        "scan_partials", "keys", "vals", "keys_alt", "vals_alt", "sorted_keys",
                        "sorted_vals", "ranges", "tfinal", "pix_state", "scratch", "dbg_nblend",
                        "dbg_hash", "dbg_delta", "grad_geom", "dbg_trace", "tile_counts", "tile_offsets",
-                       "tile_cursor", "tile_partials", "blend_ids", "blend_count", "replay_warps", "total"]
+                       "tile_cursor", "tile_partials", "blend_ids", "blend_count", "replay_warps", "tile_hist",
+                       "tile_front", "tile_cut", "tile_redo", "redo_sat", "redo_warps", "total"]
 
 
 class Layout(C.Structure):
@@ -96,6 +97,9 @@ EXPORTS = ["stp_workspace_size", "stp_workspace_layout_get", "stp_render", "stp_
 
 NUM_STAGES = 8
 STAGE_NAMES = ["setup", "preprocess", "scan", "duplicate", "sort", "ranges", "render", "bwd_preprocess"]
+# the forward's stage 7 is the second depth-slice pass (its kernels return at once when the
+# first pass finished every tile); the backward's is the backward Preprocess
+FWD_STAGE_NAMES = STAGE_NAMES[:7] + ["second_pass"]
 
 _lib = None
 
@@ -188,6 +192,7 @@ def params_struct(prm: RenderParams, extra_flags: int = 0, max_entries: int = 0)
     p.blend_cap = int(prm.blend_cap)
     p.max_entries = int(max_entries)
     p.full_max_passes = int(prm.full_max_passes)
+    p.slice_k = int(prm.slice_k)
     return p
 
 

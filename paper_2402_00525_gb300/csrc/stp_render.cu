@@ -121,6 +121,7 @@ template <bool DBG> struct PxDbg {};
 template <> struct PxDbg<true> {
     unsigned long long hash;
     float last_t, delta;         // sort error: sum of the backward steps of the blended t_opt
+    unsigned long long nq, npx;  // work counters (entry, 2x2) and (entry, pixel), added at the end
 };
 
 template <int HEAD, bool DBG>
@@ -381,6 +382,7 @@ __device__ __forceinline__ void px_init(Px<HEAD, DBG>& s, bool inside)
         s.hash = kHashInit;
         s.last_t = 0.f;
         s.delta = 0.f;
+        s.nq = s.npx = 0;
     }
 #pragma unroll
     for (int j = 0; j < HEAD; j++) {
@@ -409,7 +411,7 @@ __device__ __forceinline__ void head_consume(const PipeArgs& a, const ViewDesc& 
         const uint32_t gid = fq[k];
         const Rec r = load_rec(a.geom, V.rec_off + gid);
         const float val = splat_value(r, c.xc, c.yc);
-        if (DBG && !BWD && a.dbg_nblend != nullptr) atomicAdd(&a.status->counters[4], 1ull);
+        if constexpr (DBG && !BWD) s.npx++;
         if (fminf(a.alpha_max, val) >= a.eps_o) {
             const float t = depth_uvn(r, c.u, c.w, c.n);
             head_push<HEAD, BWD, DBG>(a, V, s, c, head_depth(t), gid, val, evict_first);
@@ -467,10 +469,7 @@ __device__ void midstage(const PipeArgs& a, const ViewDesc& V, Px<HEAD, DBG>& s,
         }
         const unsigned bal = __ballot_sync(kFull, key != kInvalidKey);
         const int nn = __popc((bal >> qbase) & 0xFu);
-        if (DBG && !BWD && a.dbg_nblend != nullptr) {
-            const unsigned ev = __ballot_sync(kFull, e < cnt && qval);
-            if (lane == 0) atomicAdd(&a.status->counters[2], (unsigned long long)__popc(ev));
-        }
+        if constexpr (DBG && !BWD) s.nq += (unsigned long long)__popc(__ballot_sync(kFull, e < cnt && qval));
         uint32_t nk[4];
 #pragma unroll
         for (int k = 0; k < 4; k++) nk[k] = __shfl_sync(kFull, key, qbase | k);
@@ -598,7 +597,15 @@ __device__ __forceinline__ void render_warp(const PipeArgs& a, const int gtile, 
     uint32_t* fq = fifob + (h * 4 + q) * kFifo;
 
     const uint2 rg = a.ranges[gtile];
-    const int lst = (int)rg.x, nL = (int)(rg.y - rg.x);
+    const int lst = (int)rg.x;
+    int nL = (int)(rg.y - rg.x);
+    // Depth slices: a list that is only a prefix of the tile's sorted entries renders as far as
+    // its complete 32-entry batches, which are the whole list's first batches; a warp with a pixel
+    // still unsaturated when it needs the next batch is queued for the second pass, which
+    // renders it again over the completed list.
+    const bool trunc = a.slice_k && a.tile_front[gtile] < a.tile_counts[gtile];
+    if (trunc) nL &= ~31;
+    bool redo = false;
     const bool centre = (a.flags & 2) != 0;
     const float cull_eps = level_cull_eps(a);
     const bool count = DBG && !BWD && a.dbg_nblend != nullptr;
@@ -611,6 +618,10 @@ __device__ __forceinline__ void render_warp(const PipeArgs& a, const int gtile, 
     for (;;) {
         const bool batch = b0 < nL;
         if (__all_sync(kFull, s.done)) break;
+        if (trunc && !batch) {
+            redo = true;
+            break;
+        }
         bool last = false;
         if (batch) {
             const int idx = b0 + lane;
@@ -685,13 +696,33 @@ __device__ __forceinline__ void render_warp(const PipeArgs& a, const int gtile, 
         if (__any_sync(kFull, wq.fc > 0)) head_consume<HEAD, BWD, DBG>(a, V, s, c, wq, fq);
         if (last) break;
     }
-    head_flush<HEAD, BWD, DBG>(a, V, s, c);
-    if (count) {
+    if (redo) {
+        // the outputs, blend order and counters of this warp come from the second pass (in the
+        // backward this cannot happen: the forward ended this warp within the prefix)
         if (lane == 0) {
-            atomicAdd(&a.status->counters[0], n_eval_s);
-            atomicAdd(&a.status->counters[1], n_surv_s);
+            if (BWD) {
+                atomicOr(&a.status->error_bits, 8u);
+            } else if (a.slice_pass) {        // the completed list is still short: cannot happen
+                atomicOr(&a.status->error_bits, 2u);
+            } else {
+                const unsigned slot = atomicAdd(&a.status->redo_n, 1u);
+                if (slot < (unsigned)a.total_tiles * 8u) a.redo_warps[slot] = (uint32_t)(gtile * 8 + warp);
+                a.tile_redo[gtile] = 1u;
+            }
         }
-        atomicAdd(&a.status->counters[3], (unsigned long long)s.nbl);
+        return;
+    }
+    head_flush<HEAD, BWD, DBG>(a, V, s, c);
+    if constexpr (DBG && !BWD) {
+        if (count) {
+            if (lane == 0) {
+                atomicAdd(&a.status->counters[0], n_eval_s);
+                atomicAdd(&a.status->counters[1], n_surv_s);
+                atomicAdd(&a.status->counters[2], s.nq);
+            }
+            atomicAdd(&a.status->counters[3], (unsigned long long)s.nbl);
+            atomicAdd(&a.status->counters[4], s.npx);
+        }
     }
     if (!inside) return;
     const long long p = c.pix;
@@ -714,14 +745,36 @@ __device__ __forceinline__ void render_warp(const PipeArgs& a, const int gtile, 
     }
 }
 
+// One block per kBlocksPerTile-th of a tile; or, for the forward's second depth-slice pass
+// (slice_pass = 1), a grid of resident blocks whose warps take the queued tile warps one at a
+// time (a single call site, so that render_warp is inlined once).
 template <int HEAD, bool BWD, bool DBG>
 __global__ void __launch_bounds__(32 * kRenderWarps, (render_min_blocks<HEAD, BWD>())) k_render(PipeArgs a)
 {
     extern __shared__ uint2 sm[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    if (a.status->error_bits & 1u) return;
-    render_warp<HEAD, BWD, DBG>(a, (int)(blockIdx.x / kBlocksPerTile), (int)(blockIdx.x % kBlocksPerTile) * kRenderWarps + wib,
-                           lane, sm + wib * render_warp_smem(a.tail, a.mid));
+    const bool queue = !BWD && a.slice_pass != 0;
+    // the second depth-slice pass also stops on counts that disagreed (error bit 2)
+    if (a.status->error_bits & (queue ? 3u : 1u)) return;
+    const unsigned n = queue ? a.status->redo_n : 1u;
+    for (unsigned it = 0;; it++) {
+        int gtile, warp;
+        if (queue) {
+            unsigned item = 0;
+            if (lane == 0) item = atomicAdd(&a.status->redo_next, 1u);
+            item = __shfl_sync(kFull, item, 0);
+            if (item >= n) break;
+            const uint32_t w = a.redo_warps[item];
+            gtile = (int)(w >> 3);
+            warp = (int)(w & 7);
+        } else {
+            if (it > 0) break;
+            gtile = (int)(blockIdx.x / kBlocksPerTile);
+            warp = (int)(blockIdx.x % kBlocksPerTile) * kRenderWarps + wib;
+        }
+        render_warp<HEAD, BWD, DBG>(a, gtile, warp, lane, sm + wib * render_warp_smem(a.tail, a.mid));
+        __syncwarp();
+    }
 }
 
 // Backward replay of the tile warps the stored-order kernel queued (a pixel past blend_cap):
@@ -903,7 +956,14 @@ cudaError_t launch_head(const PipeArgs& a, bool bwd, size_t smem, cudaStream_t s
         }
     } else {
         if ((e = ensure_smem_limit(k_render<HEAD, false, DBG>, smem, set_fwd, 64)) != cudaSuccess) return e;
-        k_render<HEAD, false, DBG><<<a.total_tiles * kBlocksPerTile, 32 * kRenderWarps, smem, s>>>(a);
+        long long grid = (long long)a.total_tiles * kBlocksPerTile;
+        if (a.slice_pass) {      // the second depth-slice pass: resident blocks over the queue
+            int dev = 0, nsm = 0;
+            if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+            if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+            grid = std::min<long long>(grid, (long long)nsm * render_min_blocks<HEAD, false>());
+        }
+        k_render<HEAD, false, DBG><<<(unsigned)grid, 32 * kRenderWarps, smem, s>>>(a);
         note_launches(1);
     }
     return cudaGetLastError();

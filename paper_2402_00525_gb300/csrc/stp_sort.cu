@@ -465,21 +465,41 @@ __global__ void __launch_bounds__(kSegThreads) k_tile_sort(PipeArgs a)
         return;
     }
     const uint32_t cnt = a.tile_counts[t];
-    const uint32_t n = min(a.tile_cursor[t], cnt);
+    const uint32_t cur = a.tile_cursor[t];
     const uint32_t off = a.tile_offsets[t];
-    if (threadIdx.x == 0) a.ranges[t] = make_uint2(off, off + n);
+    // Depth slices: the first pass sorts the tile's prefix; the second, for the tiles it
+    // completes, sorts the remaining entries placed behind the prefix (all their keys are
+    // larger) and marks the list whole. A cursor that is not exactly at the end of what the pass
+    // placed means Preprocess and Duplicate disagreed (error bit 2; cannot happen).
+    uint32_t sub = 0, n = min(cur, cnt);
+    if (a.slice_k) {
+        const uint32_t front = a.tile_front[t];
+        if (a.slice_pass) {
+            // counts that disagreed in the first pass stop the second (error bit 2)
+            if (a.tile_redo[t] == 0u || (a.status->error_bits & 2u)) return;
+            sub = front;
+            n = cur > front ? min(cur, cnt) - front : 0u;
+            __syncthreads();                  // every thread has read tile_front
+            if (threadIdx.x == 0) a.tile_front[t] = front + n;
+        } else {
+            n = min(cur, front);
+        }
+        if (threadIdx.x == 0 && cur != (a.slice_pass ? cnt : front)) atomicOr(&a.status->error_bits, 2u);
+    }
+    if (threadIdx.x == 0) a.ranges[t] = make_uint2(off, off + sub + n);
     if (n == 0) return;
-    unsigned long long* g0 = (unsigned long long*)a.dup_keys + off;   // placed words (buffer A)
-    unsigned long long* g1 = (unsigned long long*)a.keys + off;   // partner (buffer B)
+    unsigned long long* g0 = (unsigned long long*)a.dup_keys + off + sub;   // placed words (buffer A)
+    unsigned long long* g1 = (unsigned long long*)a.keys + off + sub;       // partner (buffer B)
+    uint32_t* ov = a.vals + off + sub;
     const unsigned long long hi = (unsigned long long)t << 32;
     // the Render reads only the ids; the (tile, depth) keys are written for inspection only
-    uint64_t* okeys = (a.flags & kFlagDebugStats) ? a.keys + off : nullptr;
+    uint64_t* okeys = (a.flags & kFlagDebugStats) ? a.keys + off + sub : nullptr;
     uint32_t kmin, mul;
     if (n <= (uint32_t)kSegCap) {
         uint32_t* bcnt = reinterpret_cast<uint32_t*>(seg_smem + kSegCap);
         uint32_t* bcur = bcnt + kBucketsSmall;
         if (bucket_plan<kBucketsSmall>(g0, n, bcnt, bcur, red, kmin, mul)) {
-            bucket_rank<kBucketsSmall>(g0, seg_smem, n, bcnt, bcur, kmin, mul, hi, okeys, a.vals + off, nullptr);
+            bucket_rank<kBucketsSmall>(g0, seg_smem, n, bcnt, bcur, kmin, mul, hi, okeys, ov, nullptr);
             return;
         }
     } else {
@@ -492,7 +512,7 @@ __global__ void __launch_bounds__(kSegThreads) k_tile_sort(PipeArgs a)
             for (uint32_t i = threadIdx.x; i < n; i += kSegThreads) {
                 const unsigned long long v = g0[i];
                 if (okeys) okeys[i] = hi | (v >> 32);
-                a.vals[off + i] = (uint32_t)v;
+                ov[i] = (uint32_t)v;
             }
             return;
         }
@@ -506,7 +526,7 @@ __global__ void __launch_bounds__(kSegThreads) k_tile_sort(PipeArgs a)
     for (uint32_t i = threadIdx.x; i < n; i += kSegThreads) {
         const unsigned long long v = g0[i];
         if (okeys) okeys[i] = hi | (v >> 32);
-        a.vals[off + i] = (uint32_t)v;
+        ov[i] = (uint32_t)v;
     }
 }
 

@@ -68,6 +68,9 @@ class RenderParams:
     blend_cap: int = 192
     # FULL order only: bound on the peeling passes over a tile's list (0 = enough for any list)
     full_max_passes: int = 0
+    # HIER with the partitioned sort: lists built in depth slices, about the slice_k nearest
+    # entries of each tile first (0 = whole lists in one pass); the images are the same
+    slice_k: int = 2048
 
     def validate(self) -> None:
         if self.tail < 64 or self.tail % 32 != 0:

@@ -116,7 +116,7 @@ def test_preprocess_records_match_oracle(oracle):
 def test_sorted_tile_lists_match_oracle(oracle):
     sc = I.cluster_scene(30000, 78, nclusters=8, centre_range=1.5, scale_range=(0.003, 0.2))
     cam = I.look_at((0.2, 0.4, -6), (0, 0, 0), (0, 1, 0), 320, 256, 50.0)
-    prm = I.RenderParams()
+    prm = I.RenderParams(slice_k=0)          # whole lists (depth slices build prefixes)
     gpu = gpu_render(sc, [cam], prm)
     ranges, keys, vals = [x.cpu().numpy() for x in gpu["renderer"].sorted_lists()]
     with oracle.OracleRun(sc, cam, prm) as r:
@@ -341,12 +341,13 @@ def test_stored_blend_order_backward_equals_replay():
 
 def test_partitioned_sort_equals_global_radix_sort():
     """Appendix B.3's per-tile sort (default) and the global radix sort give the same lists and
-    therefore bit-identical images (ties by Gaussian id in both)."""
+    therefore bit-identical images (ties by Gaussian id in both); so do depth slices."""
     sc = I.cluster_scene(60000, 80, nclusters=8, centre_range=1.5, scale_range=(0.003, 0.3))
     cams = I.orbit_cameras(3, 6.0, 1.0, [(320, 240), (256, 256), (200, 120)], 50.0)
-    prm = I.RenderParams()
+    prm = I.RenderParams(slice_k=0)
     a = gpu_render(sc, cams, prm)
     b = gpu_render(sc, cams, dataclasses.replace(prm, flags=I.FLAG_GLOBAL_SORT))
+    c = gpu_render(sc, cams, dataclasses.replace(prm, slice_k=256))
     ra, ka, va = [x.cpu().numpy() for x in a["renderer"].sorted_lists()]
     rb, kb, vb = [x.cpu().numpy() for x in b["renderer"].sorted_lists()]
     na, nb_ = np.diff(ra, axis=1)[:, 0], np.diff(rb, axis=1)[:, 0]
@@ -358,6 +359,7 @@ def test_partitioned_sort_equals_global_radix_sort():
     assert big > 4096          # at least one tile took the long-range (global memory) path
     for k in range(len(cams)):
         assert np.array_equal(a["rgb"][k], b["rgb"][k]) and np.array_equal(a["hash"][k], b["hash"][k])
+        assert np.array_equal(c["rgb"][k], b["rgb"][k]) and np.array_equal(c["hash"][k], b["hash"][k])
 
 
 def _skewed_scene(n_near, seed):
@@ -383,9 +385,10 @@ def test_per_tile_sort_falls_back_on_skewed_depths(n_near):
     identical to the global radix sort."""
     sc = _skewed_scene(n_near, 90 + n_near)
     cam = I.look_at((0, 0, 0), (0, 0, 5), (0, 1, 0), 64, 64, 40.0)
-    prm = I.RenderParams()
+    prm = I.RenderParams(slice_k=0)
     a = gpu_render(sc, [cam], prm)
     b = gpu_render(sc, [cam], dataclasses.replace(prm, flags=I.FLAG_GLOBAL_SORT))
+    c = gpu_render(sc, [cam], dataclasses.replace(prm, slice_k=1024))
     ra, ka, va = [x.cpu().numpy() for x in a["renderer"].sorted_lists()]
     rb, kb, vb = [x.cpu().numpy() for x in b["renderer"].sorted_lists()]
     na = np.diff(ra, axis=1)[:, 0]
@@ -393,6 +396,7 @@ def test_per_tile_sort_falls_back_on_skewed_depths(n_near):
     assert np.array_equal(na, np.diff(rb, axis=1)[:, 0])
     assert np.array_equal(ka, kb) and np.array_equal(va, vb)
     assert np.array_equal(a["rgb"][0], b["rgb"][0]) and np.array_equal(a["hash"][0], b["hash"][0])
+    assert np.array_equal(c["rgb"][0], b["rgb"][0]) and np.array_equal(c["hash"][0], b["hash"][0])
 
 
 def test_forward_is_deterministic_despite_atomic_placement():
