@@ -134,18 +134,17 @@ typedef struct {
                                     depth order). 0 = list length / 16 + 2, which always
                                     suffices; a smaller bound that runs out stops the tile and
                                     sets status error bit 4 (STP_ERR_TIMEOUT). >= 0        */
-    int32_t slice_k;             /* STP_MODE_HIER with the partitioned sort: depth-slice list
-                                    building. Preprocess histograms every tile's entries over
-                                    log-depth buckets counted from znear; Duplicate and the
-                                    per-tile sort then build only the prefix of each tile's
-                                    sorted list up to the first bucket boundary that holds at
+    int32_t slice_k;             /* STP_MODE_HIER with the partitioned sort: depth-slice lists.
+                                    The per-tile sort orders only the prefix of a tile's list up
+                                    to the first boundary of its depth buckets (the sort's own
+                                    equal-width buckets over the tile's key range) that holds at
                                     least slice_k entries. A Render warp whose pixels all
                                     terminate within the complete 32-entry batches of that
-                                    prefix produced exactly the full list's result; the others
+                                    prefix produced exactly the whole list's result; the others
                                     (counted in stp_run_status.redo_warps) are rendered again
-                                    after their tiles' remaining entries are placed and sorted
-                                    behind the prefix. Same images, hashes, blend orders and
-                                    gradients as slice_k = 0 (whole lists). >= 0            */
+                                    after their tiles' whole lists are sorted. Same images,
+                                    hashes, blend orders and gradients as slice_k = 0 (whole
+                                    lists). >= 0                                            */
 } stp_params;
 
 typedef struct {                 /* device status block, read back by stp_read_status        */
@@ -209,15 +208,10 @@ typedef struct {                 /* byte offsets of workspace regions (for inspe
     size_t blend_count;          /* [total pixels] uint32 blends per pixel (with blend_ids)  */
     size_t replay_warps;         /* [total tiles * 8] uint32 backward work list: tile warps with
                                     a pixel past blend_cap, replayed (with blend_ids)        */
-    size_t tile_hist;            /* [total tiles][256] uint32 entries per log-depth bucket
-                                    (slice_k > 0, else 0, like the next five regions)         */
-    size_t tile_front;           /* [total tiles] uint32 entries of the prefix the first pass
-                                    builds (set to the whole count for re-rendered tiles)     */
-    size_t tile_cut;             /* [total tiles] uint32 last bucket of the prefix            */
-    size_t tile_redo;            /* [total tiles] uint32 1 = the second pass completes the list */
-    size_t redo_sat;             /* per view [(tiles_y + 1) * (tiles_x + 1)] uint32 summed-area
-                                    table of tile_redo (locates the records the second pass
-                                    needs)                                                    */
+    size_t tile_front;           /* [total tiles] uint32 entries of the sorted prefix (the whole
+                                    count when the list is whole); slice_k > 0, else 0, like
+                                    the next two regions                                       */
+    size_t tile_redo;            /* [total tiles] uint32 1 = the second pass sorts the whole list */
     size_t redo_warps;           /* [total tiles * 8] uint32 tile warps (gtile * 8 + warp) the
                                     second pass renders                                       */
     size_t total;                /* total bytes                                              */

@@ -75,8 +75,8 @@ _LAYOUT_SIZE_FIELDS = ["status", "views", "scenes", "geom", "view_z", "rect", "c
                        "scan_partials", "keys", "vals", "keys_alt", "vals_alt", "sorted_keys",
                        "sorted_vals", "ranges", "tfinal", "pix_state", "scratch", "dbg_nblend",
                        "dbg_hash", "dbg_delta", "grad_geom", "dbg_trace", "tile_counts", "tile_offsets",
-                       "tile_cursor", "tile_partials", "blend_ids", "blend_count", "replay_warps", "tile_hist",
-                       "tile_front", "tile_cut", "tile_redo", "redo_sat", "redo_warps", "total"]
+                       "tile_cursor", "tile_partials", "blend_ids", "blend_count", "replay_warps", "tile_front",
+                       "tile_redo", "redo_warps", "total"]
 
 
 class Layout(C.Structure):

@@ -145,23 +145,13 @@ bool slicing(const stp_params* p)
     return p->slice_k > 0 && p->mode == STP_MODE_HIER && !(p->flags & kFlagGlobalSort);
 }
 
-// Bucket origin of the depth slices: the log-depth bucket of znear (host copy of the kernels'
-// order-preserving float key).
-int slice_base(float znear)
-{
-    uint32_t u;
-    std::memcpy(&u, &znear, 4);
-    const uint32_t key = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-    return (int)(key >> stp::kSliceShift);
-}
-
 void make_plan(const int64_t* ns, const int32_t* vps, int32_t nscenes, const stp_camera* cams, int32_t nviews,
                const stp_params* p, Plan& P)
 {
     std::memset(&P.L, 0, sizeof P.L);
     P.views.resize(nviews);
     P.scenes.resize(nscenes);
-    long long tiles = 0, pixels = 0, rec = 0, threads = 0, rec_threads = 0, sat = 0;
+    long long tiles = 0, pixels = 0, rec = 0, threads = 0, rec_threads = 0;
     int v = 0;
     for (int sc = 0; sc < nscenes; sc++) {
         stp::SceneDesc& S = P.scenes[sc];
@@ -189,11 +179,9 @@ void make_plan(const int64_t* ns, const int32_t* vps, int32_t nscenes, const stp
             d.tiles_x = (c.width + 15) / 16;
             d.tiles_y = (c.height + 15) / 16;
             d.tile_off = (int)tiles;
-            d.sat_off = (int)sat;
             d.pix_off = pixels;
             d.rec_off = rec;
             tiles += (long long)d.tiles_x * d.tiles_y;
-            sat += (long long)(d.tiles_x + 1) * (d.tiles_y + 1);
             pixels += (long long)c.width * c.height;
             rec += ns[sc];
         }
@@ -251,13 +239,10 @@ void make_plan(const int64_t* ns, const int32_t* vps, int32_t nscenes, const stp
     }
     L.dbg_trace = 0;
     if (p->flags & kFlagTrace) L.dbg_trace = take((size_t)pixels * stp::kTraceLen * 4);
-    L.tile_hist = L.tile_front = L.tile_cut = L.tile_redo = L.redo_sat = L.redo_warps = 0;
+    L.tile_front = L.tile_redo = L.redo_warps = 0;
     if (slicing(p)) {
-        L.tile_hist = take((size_t)tiles * stp::kSliceBins * 4);
         L.tile_front = take((size_t)tiles * 4);
-        L.tile_cut = take((size_t)tiles * 4);
         L.tile_redo = take((size_t)tiles * 4);
-        L.redo_sat = take((size_t)sat * 4);
         L.redo_warps = take((size_t)tiles * 8 * 4);
     }
     L.total = o;
@@ -322,14 +307,10 @@ stp::PipeArgs make_args(const stp_params* p, const Plan& P, void* ws)
     a.tile_offsets = (uint32_t*)(b + L.tile_offsets);
     a.tile_cursor = (uint32_t*)(b + L.tile_cursor);
     a.tile_partials = (unsigned long long*)(b + L.tile_partials);
-    a.slice_k = L.tile_hist ? p->slice_k : 0;
+    a.slice_k = L.tile_front ? p->slice_k : 0;
     a.slice_pass = 0;
-    a.slice_base = slice_base(p->znear);
-    a.tile_hist = L.tile_hist ? (uint32_t*)(b + L.tile_hist) : nullptr;
     a.tile_front = L.tile_front ? (uint32_t*)(b + L.tile_front) : nullptr;
-    a.tile_cut = L.tile_cut ? (uint32_t*)(b + L.tile_cut) : nullptr;
     a.tile_redo = L.tile_redo ? (uint32_t*)(b + L.tile_redo) : nullptr;
-    a.redo_sat = L.redo_sat ? (uint32_t*)(b + L.redo_sat) : nullptr;
     a.redo_warps = L.redo_warps ? (uint32_t*)(b + L.redo_warps) : nullptr;
     return a;
 }
@@ -402,17 +383,13 @@ stp_status render_impl(const stp_gaussians* scenes, int32_t nscenes, const int32
                                      nscenes, const_cast<stp::SceneDesc*>(a.scenes), s)) != cudaSuccess)
         return cuda_fail(e, "view and scene tables");
     if (a.partitioned) {
-        // with depth slices Preprocess fills the bucket histogram and k_slice_cut the counts
-        if ((!a.slice_k && (e = cudaMemsetAsync(a.tile_counts, 0, (size_t)a.total_tiles * 4, s)) != cudaSuccess) ||
-            (a.slice_k &&
-             (e = cudaMemsetAsync(a.tile_hist, 0, (size_t)a.total_tiles * stp::kSliceBins * 4, s)) != cudaSuccess) ||
+        if ((e = cudaMemsetAsync(a.tile_counts, 0, (size_t)a.total_tiles * 4, s)) != cudaSuccess ||
             (e = cudaMemsetAsync(a.tile_cursor, 0, (size_t)a.total_tiles * 4, s)) != cudaSuccess)
             return cuda_fail(e, "clear tile counters");
     }
     prof_mark(1, s);
     if ((e = stp::launch_preprocess(a, s)) != cudaSuccess) return cuda_fail(e, "preprocess");
     prof_mark(2, s);
-    if (a.slice_k && (e = stp::launch_slice_cut(a, s)) != cudaSuccess) return cuda_fail(e, "slice cut");
     if ((e = a.partitioned ? stp::launch_scan_tiles(a, s) : stp::launch_scan_counts(a, s)) != cudaSuccess)
         return cuda_fail(e, "scan");
     prof_mark(3, s);
@@ -432,12 +409,10 @@ stp_status render_impl(const stp_gaussians* scenes, int32_t nscenes, const int32
     if ((e = stp::launch_render(a, false, s)) != cudaSuccess) return cuda_fail(e, "render");
     prof_mark(7, s);
     if (a.slice_k) {
-        // second depth-slice pass: complete the lists of the tiles with queued warps (the
+        // second depth-slice pass: sort the whole lists of the tiles with queued warps (the
         // kernels return at once when the queue is empty) and render those warps again
         stp::PipeArgs b = a;
         b.slice_pass = 1;
-        if ((e = stp::launch_redo_sat(b, s)) != cudaSuccess) return cuda_fail(e, "second pass: table");
-        if ((e = stp::launch_duplicate(b, s)) != cudaSuccess) return cuda_fail(e, "second pass: duplicate");
         if ((e = stp::launch_tile_sort(b, s)) != cudaSuccess) return cuda_fail(e, "second pass: tile sort");
         if ((e = stp::launch_render(b, false, s)) != cudaSuccess) return cuda_fail(e, "second pass: render");
     }

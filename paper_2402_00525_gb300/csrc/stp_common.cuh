@@ -51,7 +51,7 @@ struct ViewDesc {
     float limx, limy;            // Jacobian clamp limits on x/z and y/z
     int W, H, tiles_x, tiles_y;
     int tile_off;                // first global tile id of this view
-    int sat_off;                 // first entry of this view's summed-area table of re-rendered tiles
+    int pad;
     long long pix_off;           // first pixel of this view in the packed image arrays
     long long rec_off;           // first render record of this view (sum of N over earlier views)
 };
@@ -130,18 +130,6 @@ __device__ __forceinline__ float fkey_inv(uint32_t k)
 {
     uint32_t u = (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
     return __uint_as_float(u);
-}
-
-// Log-depth bucket of a tile key (depth-slice list building): 2^kSliceShift key units a
-// bucket, which is 2^(23 - kSliceShift) buckets an octave for a positive depth (the key of a
-// positive float is its bit pattern with the sign bit set), counted from the bucket of znear
-// (`base`) and clamped to [0, kSliceBins). Monotone in the key, so the entries of buckets
-// 0..c of a tile are a prefix of its list sorted by (key, id).
-constexpr int kSliceBins = 256, kSliceShift = 19;
-__device__ __forceinline__ uint32_t slice_bin(uint32_t key, int base)
-{
-    const int b = (int)(key >> kSliceShift) - base;
-    return (uint32_t)min(max(b, 0), kSliceBins - 1);
 }
 
 // offset of pixel-space coordinate x from the mean, x - (hi + lo)

@@ -71,17 +71,13 @@ struct PipeArgs {
     uint32_t* replay_warps;  // [total_tiles * 8] tile warps (gtile * 8 + warp) the backward replays
     int blend_cap;
     int full_max_passes;     // FULL order: host bound on peeling passes (0 = always enough)
-    // depth slices (HIER, partitioned sort, slice_k > 0): the first pass builds each tile's list
-    // up to the first log-depth bucket boundary holding >= slice_k entries; the second pass
-    // completes the lists of the tiles whose Render warps needed more and renders those warps
+    // depth slices (HIER, partitioned sort, slice_k > 0): the first pass sorts each tile's list
+    // only up to the first bucket boundary holding >= slice_k entries; the second pass sorts the
+    // whole lists of the tiles whose Render warps needed more and renders those warps again
     int slice_k;             // 0 = whole lists in one pass
-    int slice_pass;          // 0 first pass, 1 second pass (Duplicate, per-tile sort, Render)
-    int slice_base;          // bucket origin: fkey(znear) >> kSliceShift
-    uint32_t* tile_hist;     // [total_tiles * kSliceBins] entries per bucket (Preprocess)
-    uint32_t* tile_front;    // [total_tiles] prefix length (the whole count once completed)
-    uint32_t* tile_cut;      // [total_tiles] last bucket of the prefix
-    uint32_t* tile_redo;     // [total_tiles] 1 = completed by the second pass
-    uint32_t* redo_sat;      // per view summed-area table of tile_redo (ViewDesc::sat_off)
+    int slice_pass;          // 0 first pass, 1 second pass (per-tile sort, Render)
+    uint32_t* tile_front;    // [total_tiles] sorted prefix length (tile_counts when whole)
+    uint32_t* tile_redo;     // [total_tiles] 1 = sorted whole by the second pass
     uint32_t* redo_warps;    // [total_tiles * 8] queued tile warps (gtile * 8 + warp)
 };
 
@@ -122,8 +118,6 @@ cudaError_t launch_tables_init(const ViewDesc* host_views, int nviews, ViewDesc*
 void note_launches(int n);
 
 cudaError_t launch_preprocess(const PipeArgs& a, cudaStream_t s);
-cudaError_t launch_slice_cut(const PipeArgs& a, cudaStream_t s);
-cudaError_t launch_redo_sat(const PipeArgs& a, cudaStream_t s);
 cudaError_t launch_scan_counts(const PipeArgs& a, cudaStream_t s);
 cudaError_t launch_scan_tiles(const PipeArgs& a, cudaStream_t s);
 cudaError_t launch_tile_sort(const PipeArgs& a, cudaStream_t s);

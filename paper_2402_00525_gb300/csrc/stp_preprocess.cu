@@ -386,41 +386,19 @@ __device__ __forceinline__ bool tile_keep(const PipeArgs& a, const Rec& r, const
     return box_keep(r, b, tile_cull_eps(a));
 }
 
-// Partitioned sort (appendix B.3): count a kept entry of global tile `gt`; with depth slices
-// (SLICE), in the log-depth bucket of its key (the tile's count is then the sum of its buckets,
-// formed by k_slice_cut). (Aggregating the lanes of a warp that hit the same tile measured
-// slower than plain atomics here.)
-template <bool SLICE>
-__device__ __forceinline__ void count_entry(const PipeArgs& a, uint32_t gt, uint32_t dkey)
+// Partitioned sort (appendix B.3): count a kept entry of global tile `gt`. (Aggregating the
+// lanes of a warp that hit the same tile measured slower than plain atomics here.)
+__device__ __forceinline__ void count_entry(const PipeArgs& a, uint32_t gt)
 {
-    if (SLICE) atomicAdd(&a.tile_hist[(size_t)gt * kSliceBins + slice_bin(dkey, a.slice_base)], 1u);
-    else atomicAdd(&a.tile_counts[gt], 1u);
-}
-
-// Depth slices: does this pass place the kept entry (gt, dkey)? The first pass places the
-// entries of the tile's prefix (buckets up to the cut), the second the remaining entries of the
-// tiles it completes. Without slices every entry is placed in the one pass.
-__device__ __forceinline__ bool slice_take(const PipeArgs& a, uint32_t gt, uint32_t dkey)
-{
-    if (!a.slice_k) return true;
-    const bool front = slice_bin(dkey, a.slice_base) <= a.tile_cut[gt];
-    return a.slice_pass == 0 ? front : (!front && a.tile_redo[gt] != 0u);
-}
-
-// Slots of a tile's range this pass may fill: the prefix in the first pass of depth slices, the
-// whole list otherwise (the second pass continues the cursor behind the prefix).
-__device__ __forceinline__ uint32_t slot_limit(const PipeArgs& a, uint32_t gt)
-{
-    return (a.slice_k && a.slice_pass == 0) ? a.tile_front[gt] : a.tile_counts[gt];
+    atomicAdd(&a.tile_counts[gt], 1u);
 }
 
 // Partitioned sort: place an entry in its tile's range through the tile's atomic cursor. The
 // order inside a range is arbitrary here and fixed by the per-tile sort on (depth, id).
 __device__ __forceinline__ void place_entry(const PipeArgs& a, uint32_t gt, uint32_t dkey, uint32_t gid)
 {
-    if (!slice_take(a, gt, dkey)) return;
     const uint32_t slot = atomicAdd(&a.tile_cursor[gt], 1u);
-    if (slot >= slot_limit(a, gt)) {   // more entries than Preprocess counted: cannot happen
+    if (slot >= a.tile_counts[gt]) {   // more entries than Preprocess counted: cannot happen
         atomicOr(&a.status->error_bits, 2u);
         return;
     }
@@ -444,8 +422,7 @@ __device__ __forceinline__ uint32_t kept_depth_key(const PipeArgs& a, const View
 // Duplicate computes depths only for kept tiles and never re-takes a cull decision there.
 // With the global radix sort the keys go to the Gaussian's own range [off, off + want) in
 // tile order; with the partitioned sort they go to their tiles' ranges.
-// SLICE (counting only): the kept tiles' keys go to the depth-slice histogram.
-template <bool EMIT, bool SLICE = false>
+template <bool EMIT>
 __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, int vidx, bool has, const Rec& r, float vz,
                                ushort4 rc, uint32_t off, uint32_t want, uint32_t gid, uint32_t* mask_io)
 {
@@ -460,13 +437,11 @@ __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, int vidx, b
             uint32_t mask = 0;
             for (int k = 0; k < ncand; k++) {
                 const int tx = rc.x + k % w, ty = rc.y + k / w;
-                uint32_t dk = 0;
-                const bool keep = SLICE ? tile_depth_key(a, V, r, vz, tx, ty, &dk)
-                                        : tile_keep(a, r, block_box(tx * kTile, ty * kTile, kTile, V.W, V.H));
-                if (keep) {
+                const Box b = block_box(tx * kTile, ty * kTile, kTile, V.W, V.H);
+                if (tile_keep(a, r, b)) {
                     cnt++;
                     if (k < 32) mask |= 1u << k;
-                    if (part) count_entry<SLICE>(a, (uint32_t)(V.tile_off + ty * V.tiles_x + tx), dk);
+                    if (part) count_entry(a, (uint32_t)(V.tile_off + ty * V.tiles_x + tx));
                 }
             }
             *mask_io = mask;
@@ -489,16 +464,13 @@ __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, int vidx, b
                 }
                 if (part) {
                     uint32_t slot[4];
-                    bool take[4];
+#pragma unroll
+                    for (int j = 0; j < 4; j++)
+                        if (j < np) slot[j] = atomicAdd(&a.tile_cursor[gts[j]], 1u);
 #pragma unroll
                     for (int j = 0; j < 4; j++) {
-                        take[j] = j < np && slice_take(a, gts[j], dks[j]);
-                        if (take[j]) slot[j] = atomicAdd(&a.tile_cursor[gts[j]], 1u);
-                    }
-#pragma unroll
-                    for (int j = 0; j < 4; j++) {
-                        if (take[j]) {
-                            if (slot[j] >= slot_limit(a, gts[j])) {
+                        if (j < np) {
+                            if (slot[j] >= a.tile_counts[gts[j]]) {
                                 atomicOr(&a.status->error_bits, 2u);
                             } else {
                                 const unsigned long long pos = (unsigned long long)a.tile_offsets[gts[j]] + slot[j];
@@ -561,7 +533,7 @@ __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, int vidx, b
             if (k < nc) {
                 const int tx = x0 + k % ws, ty = y0 + k / ws;
                 gt = (uint32_t)(Vs.tile_off + ty * Vs.tiles_x + tx);
-                if (EMIT || SLICE) keep = tile_depth_key(a, Vs, rs, vzs, tx, ty, &dk);
+                if (EMIT) keep = tile_depth_key(a, Vs, rs, vzs, tx, ty, &dk);
                 else keep = tile_keep(a, rs, block_box(tx * kTile, ty * kTile, kTile, Vs.W, Vs.H));
             }
             const unsigned m = __ballot_sync(kFull, keep);
@@ -578,7 +550,7 @@ __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, int vidx, b
                         }
                     }
                 } else if (part) {
-                    count_entry<SLICE>(a, gt, dk);
+                    count_entry(a, gt);
                 }
             }
             base += __popc(m);
@@ -636,10 +608,7 @@ __device__ __forceinline__ RecThread rec_thread(const PipeArgs& a)
 // the owning record's mean, conic and opacity taken by shuffle. Each owner assembles its kept-
 // tile mask (bit k = k-th candidate, row major) from the rounds' ballots and returns its count.
 // The decisions are the ones the owner's own loop would take (same arithmetic, same inputs).
-// With depth slices (SLICE) the lanes also take the depth factors and key each kept tile.
-template <bool SLICE>
-__device__ uint32_t count_spread(const PipeArgs& a, int vidx, const Rec& r, float vz, ushort4 rc, int n,
-                                 uint32_t* mask_out)
+__device__ uint32_t count_spread(const PipeArgs& a, int vidx, const Rec& r, ushort4 rc, int n, uint32_t* mask_out)
 {
     const int lane = threadIdx.x & 31;
     int incl = n;
@@ -670,25 +639,13 @@ __device__ uint32_t count_spread(const PipeArgs& a, int vidx, const Rec& r, floa
                             __shfl_sync(kFull, r.r1.z, src), __shfl_sync(kFull, r.r1.w, src));
         rs.r2 = make_float4(__shfl_sync(kFull, r.r2.x, src), 0.f, 0.f, 0.f);
         rs.r3 = rs.r4 = rs.r5 = make_float4(0.f, 0.f, 0.f, 0.f);
-        float zs = 0.f;
-        if (SLICE) {
-            rs.r3 = make_float4(__shfl_sync(kFull, r.r3.x, src), __shfl_sync(kFull, r.r3.y, src),
-                                __shfl_sync(kFull, r.r3.z, src), __shfl_sync(kFull, r.r3.w, src));
-            rs.r4 = make_float4(__shfl_sync(kFull, r.r4.x, src), __shfl_sync(kFull, r.r4.y, src),
-                                __shfl_sync(kFull, r.r4.z, src), __shfl_sync(kFull, r.r4.w, src));
-            rs.r5 = make_float4(__shfl_sync(kFull, r.r5.x, src), __shfl_sync(kFull, r.r5.y, src),
-                                __shfl_sync(kFull, r.r5.z, src), __shfl_sync(kFull, r.r5.w, src));
-            zs = __shfl_sync(kFull, vz, src);
-        }
         bool keep = false;
         if (p < total) {
             const int k = p - first;
             const int tx = x0 + k % ws, ty = y0 + k / ws;
             const ViewDesc& Vs = a.views[vs];
-            uint32_t dk = 0;
-            keep = SLICE ? tile_depth_key(a, Vs, rs, zs, tx, ty, &dk)
-                         : tile_keep(a, rs, block_box(tx * kTile, ty * kTile, kTile, Vs.W, Vs.H));
-            if (keep && a.partitioned) count_entry<SLICE>(a, (uint32_t)(Vs.tile_off + ty * Vs.tiles_x + tx), dk);
+            keep = tile_keep(a, rs, block_box(tx * kTile, ty * kTile, kTile, Vs.W, Vs.H));
+            if (keep && a.partitioned) count_entry(a, (uint32_t)(Vs.tile_off + ty * Vs.tiles_x + tx));
         }
         const unsigned bal = __ballot_sync(kFull, keep);
         const int lo = max(first_me, base), hi = min(first_me + n, base + 32);
@@ -702,8 +659,6 @@ __device__ uint32_t count_spread(const PipeArgs& a, int vidx, const Rec& r, floa
     return (uint32_t)__popc(mask);
 }
 
-// SLICE: depth-slice list building (the kept tiles are counted in log-depth buckets).
-template <bool SLICE>
 __global__ void __launch_bounds__(128, STP_PRE_MIN_BLOCKS) k_preprocess(PipeArgs a)
 {
     const RecThread th = rec_thread(a);
@@ -728,9 +683,9 @@ __global__ void __launch_bounds__(128, STP_PRE_MIN_BLOCKS) k_preprocess(PipeArgs
     if (!(a.flags & 16)) {
         const int nc = vis ? ((int)rc.z - (int)rc.x) * ((int)rc.w - (int)rc.y) : 0;
         spread = vis && nc <= 32 && nc <= a.lb_threshold;
-        scnt = count_spread<SLICE>(a, th.v, r, vz, rc, spread ? nc : 0, &smask);
+        scnt = count_spread(a, th.v, r, rc, spread ? nc : 0, &smask);
     }
-    uint32_t cnt = tiles_pass<false, SLICE>(a, V, th.v, vis && !spread, r, vz, rc, 0, 0, 0, &mask);
+    uint32_t cnt = tiles_pass<false>(a, V, th.v, vis && !spread, r, vz, rc, 0, 0, 0, &mask);
     if (spread) {
         cnt = scnt;
         mask = smask;
@@ -797,26 +752,23 @@ __device__ void place_spread(const PipeArgs& a, int vidx, ushort4 rc, uint32_t g
         const int vs = __shfl_sync(kFull, vidx, src);
         const float zs = __shfl_sync(kFull, vz, src);
         uint32_t gt = 0xFFFFFFFFu - lane, dk = 0;
-        bool take = false;
         if (p < total) {
             const int k = nth_set_bit(ms, p - first);
             const int tx = x0 + k % ws, ty = y0 + k / ws;
             const ViewDesc& Vs = a.views[vs];
             const Rec rs = load_rec(a.geom, Vs.rec_off + gs);
-            const uint32_t g = (uint32_t)(Vs.tile_off + ty * Vs.tiles_x + tx);
+            gt = (uint32_t)(Vs.tile_off + ty * Vs.tiles_x + tx);
             dk = kept_depth_key(a, Vs, rs, zs, tx, ty);
-            take = slice_take(a, g, dk);
-            if (take) gt = g;
         }
         // lanes placing into the same tile reserve their slots with one cursor atomic
         const unsigned peers = __match_any_sync(kFull, gt);
         const int leader = __ffs(peers) - 1;
         uint32_t sbase = 0;
-        if (take && lane == leader) sbase = atomicAdd(&a.tile_cursor[gt], (uint32_t)__popc(peers));
+        if (p < total && lane == leader) sbase = atomicAdd(&a.tile_cursor[gt], (uint32_t)__popc(peers));
         sbase = __shfl_sync(kFull, sbase, leader);
-        if (take) {
+        if (p < total) {
             const uint32_t slot = sbase + __popc(peers & lanemask_lt());
-            if (slot >= slot_limit(a, gt)) {
+            if (slot >= a.tile_counts[gt]) {
                 atomicOr(&a.status->error_bits, 2u);
             } else {
                 const unsigned long long pos = (unsigned long long)a.tile_offsets[gt] + slot;
@@ -831,10 +783,10 @@ __device__ void place_spread(const PipeArgs& a, int vidx, ushort4 rc, uint32_t g
 // neighbouring Gaussians (close in space in a trained or clustered scene) often share tiles,
 // whose lanes then reserve their slots together (place_spread). Preprocess keeps the views of a
 // Gaussian in neighbouring lanes, which read its SH coefficients once.
-__device__ __forceinline__ RecThread rec_thread_view_major(const PipeArgs& a, long long blk)
+__device__ __forceinline__ RecThread rec_thread_view_major(const PipeArgs& a)
 {
     RecThread t;
-    const long long t0 = blk * blockDim.x;
+    const long long t0 = (long long)blockIdx.x * blockDim.x;
     t.S = a.scenes[scene_of_rec(a, t0)];
     const int nv = t.S.view_end - t.S.view_begin;
     const long long lt = t0 - t.S.rec_thread_off + threadIdx.x;
@@ -855,20 +807,9 @@ __device__ __forceinline__ RecThread rec_thread_view_major(const PipeArgs& a, lo
     return t;
 }
 
-// Depth slices, second pass: does the record's tile rectangle [x0, x1) x [y0, y1) hold a tile
-// the second pass completes? Four reads of the view's summed-area table of the flags.
-__device__ __forceinline__ bool rect_has_redo(const PipeArgs& a, const ViewDesc& V, ushort4 rc)
+__global__ void __launch_bounds__(128, STP_DUP_MIN_BLOCKS) k_duplicate(PipeArgs a)
 {
-    const uint32_t* S = a.redo_sat + V.sat_off;
-    const size_t P = (size_t)V.tiles_x + 1;
-    const uint32_t n = S[rc.w * P + rc.z] - S[rc.y * P + rc.z] - S[rc.w * P + rc.x] + S[rc.y * P + rc.x];
-    return n != 0u;
-}
-
-// The records of per-record thread block `blk`.
-__device__ __forceinline__ void duplicate_block(const PipeArgs& a, long long blk)
-{
-    const RecThread th = rec_thread_view_major(a, blk);
+    const RecThread th = rec_thread_view_major(a);
     const int i = th.i;
     const ViewDesc& V = a.views[th.v];
     const long long o = V.rec_off + i;
@@ -876,21 +817,17 @@ __device__ __forceinline__ void duplicate_block(const PipeArgs& a, long long blk
     ushort4 rc = make_ushort4(0, 0, 0, 0);
     uint32_t off = 0, want = 0, mask = 0;
     float vz = 0.f;
-    bool has = false;
     if (th.live) {
-        rc = a.rect[o];
-        want = a.counts[o];
-        // the second depth-slice pass takes only records that reach a tile it completes
-        has = want > 0 && (!a.slice_pass || rect_has_redo(a, V, rc));
-    }
-    if (has) {
         r = load_rec(a.geom, o);
         if (a.flags & 8) vz = a.view_z[o];
+        rc = a.rect[o];
         off = a.partitioned ? 0u : a.offsets[o];
+        want = a.counts[o];
         mask = a.keep_mask[o];
     } else {
         r.r0 = r.r1 = r.r2 = r.r3 = r.r4 = r.r5 = make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    bool has = th.live && want > 0;
     if (a.partitioned && !(a.flags & 16)) {
         // the records whose kept tiles Preprocess recorded in a mask (at most 32 candidates,
         // not above the load-balancing threshold) are placed by the whole warp together; the
@@ -904,7 +841,7 @@ __device__ __forceinline__ void duplicate_block(const PipeArgs& a, long long blk
         }
     }
     const uint32_t got = tiles_pass<true>(a, V, th.v, has, r, vz, rc, off, want, (uint32_t)i, &mask);
-    if (has && got != want && !a.partitioned) {
+    if (th.live && got != want && !a.partitioned) {
         // Preprocess and Duplicate disagree (cannot happen with the shared rounding of the
         // decision arithmetic; kept as the paper's safety net, appendix B.4): pad with
         // dummy keys that sort behind every tile.
@@ -915,21 +852,6 @@ __device__ __forceinline__ void duplicate_block(const PipeArgs& a, long long blk
         atomicOr(&a.status->error_bits, 2u);
         atomicAdd(&a.status->mismatched, 1u);
     }
-}
-
-// One block of records per thread block. The second depth-slice pass (REDO) runs a grid of
-// resident blocks over all record blocks instead, and only when the Render queued warps, so
-// that the usual empty pass costs a few thousand blocks rather than one per record block.
-template <bool REDO>
-__global__ void __launch_bounds__(128, STP_DUP_MIN_BLOCKS) k_duplicate(PipeArgs a)
-{
-    if (!REDO) {
-        duplicate_block(a, blockIdx.x);
-        return;
-    }
-    // nothing queued, or counts that disagreed (the prefixes may then have unwritten slots)
-    if (a.status->redo_n == 0u || (a.status->error_bits & 3u)) return;
-    for (long long blk = blockIdx.x; blk < a.rec_threads / 128; blk += gridDim.x) duplicate_block(a, blk);
 }
 
 // ---------------------------------------------------------------- scan of the counts
@@ -1052,8 +974,7 @@ cudaError_t launch_tables_init(const ViewDesc* host_views, int nviews, ViewDesc*
 cudaError_t launch_preprocess(const PipeArgs& a, cudaStream_t s)
 {
     if (a.rec_threads == 0) return cudaSuccess;
-    if (a.slice_k) k_preprocess<true><<<(unsigned)(a.rec_threads / 128), 128, 0, s>>>(a);
-    else k_preprocess<false><<<(unsigned)(a.rec_threads / 128), 128, 0, s>>>(a);
+    k_preprocess<<<(unsigned)(a.rec_threads / 128), 128, 0, s>>>(a);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -1079,112 +1000,10 @@ cudaError_t launch_scan_tiles(const PipeArgs& a, cudaStream_t s)
     return scan_u32(a.tile_counts, a.tile_offsets, a.tile_partials, (long long)a.total_tiles, a.status, s);
 }
 
-// Depth slices: per tile, the whole count (the sum of its buckets) and the prefix the first pass
-// builds -- buckets 0..c, c the first bucket at which the running count reaches slice_k (every
-// bucket when the tile holds at most slice_k entries). Clears the tile's second-pass flag. One
-// warp per tile, eight buckets a lane.
-__global__ void __launch_bounds__(256) k_slice_cut(PipeArgs a)
-{
-    const int lane = threadIdx.x & 31;
-    const long long t = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (t >= a.total_tiles) return;                       // whole warps
-    const uint4* hp = reinterpret_cast<const uint4*>(a.tile_hist + (size_t)t * kSliceBins) + 2 * lane;
-    const uint4 h0 = hp[0], h1 = hp[1];
-    const uint32_t c[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
-    uint32_t sum = 0;
-#pragma unroll
-    for (int k = 0; k < 8; k++) sum += c[k];
-    uint32_t incl = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += y;
-    }
-    const uint32_t total = __shfl_sync(kFull, incl, 31);
-    const uint32_t K = (uint32_t)a.slice_k;
-    uint32_t cut = kSliceBins - 1, front = total;
-    if (total > K) {
-        const int fl = __ffs(__ballot_sync(kFull, incl >= K)) - 1;    // lane 31 reaches K
-        uint32_t run = incl - sum, cb = 0, fr = 0;
-        bool found = false;
-#pragma unroll
-        for (int k = 0; k < 8; k++) {
-            run += c[k];
-            if (!found && run >= K) {
-                cb = (uint32_t)(8 * lane + k);
-                fr = run;
-                found = true;
-            }
-        }
-        cut = __shfl_sync(kFull, cb, fl);
-        front = __shfl_sync(kFull, fr, fl);
-    }
-    if (lane == 0) {
-        a.tile_counts[t] = total;
-        a.tile_front[t] = front;
-        a.tile_cut[t] = cut;
-        a.tile_redo[t] = 0u;
-    }
-}
-
-// Depth slices, after the first Render: per view, the summed-area table S of the second-pass
-// flags, S[y][x] = flagged tiles in [0, x) x [0, y), (tiles_y + 1) rows of tiles_x + 1 entries.
-// One block per view; nothing to do when no warp was queued (or the counts disagreed).
-__global__ void __launch_bounds__(256) k_redo_sat(PipeArgs a)
-{
-    if (a.status->redo_n == 0u || (a.status->error_bits & 3u)) return;
-    const ViewDesc& V = a.views[blockIdx.x];
-    const int TX = V.tiles_x, TY = V.tiles_y;
-    const size_t P = (size_t)TX + 1;
-    uint32_t* S = a.redo_sat + V.sat_off;
-    for (int y = threadIdx.x; y <= TY; y += blockDim.x) {       // row sums
-        uint32_t run = 0;
-        S[y * P] = 0u;
-        for (int x = 0; x < TX; x++) {
-            if (y > 0) run += a.tile_redo[V.tile_off + (y - 1) * TX + x] != 0u ? 1u : 0u;
-            S[y * P + x + 1] = run;
-        }
-    }
-    __syncthreads();
-    for (int x = threadIdx.x + 1; x <= TX; x += blockDim.x) {   // then down the columns
-        uint32_t run = 0;
-        for (int y = 1; y <= TY; y++) {
-            run += S[y * P + x];
-            S[y * P + x] = run;
-        }
-    }
-}
-
-cudaError_t launch_slice_cut(const PipeArgs& a, cudaStream_t s)
-{
-    if (a.total_tiles == 0) return cudaSuccess;
-    k_slice_cut<<<(unsigned)((a.total_tiles + 7) / 8), 256, 0, s>>>(a);
-    note_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_redo_sat(const PipeArgs& a, cudaStream_t s)
-{
-    if (a.nviews == 0) return cudaSuccess;
-    k_redo_sat<<<(unsigned)a.nviews, 256, 0, s>>>(a);
-    note_launches(1);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_duplicate(const PipeArgs& a, cudaStream_t s)
 {
     if (a.rec_threads == 0) return cudaSuccess;
-    long long grid = a.rec_threads / 128;
-    if (a.slice_pass) {
-        int dev = 0, nsm = 0;
-        cudaError_t e;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        grid = std::min<long long>(grid, (long long)nsm * STP_DUP_MIN_BLOCKS);
-        k_duplicate<true><<<(unsigned)grid, 128, 0, s>>>(a);
-    } else {
-        k_duplicate<false><<<(unsigned)grid, 128, 0, s>>>(a);
-    }
+    k_duplicate<<<(unsigned)(a.rec_threads / 128), 128, 0, s>>>(a);
     note_launches(1);
     return cudaGetLastError();
 }

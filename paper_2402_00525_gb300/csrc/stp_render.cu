@@ -34,7 +34,7 @@
 // so the blends are visited front to back in the forward's order. A forward that a backward
 // follows stores each pixel's first blend_cap blended ids (4 bytes a blend), and
 // k_render_bwd_list walks them, recomputing alpha with the forward's rounding. A warp with a
-// pixel past blend_cap is queued and replayed: k_render_replay runs the forward code with
+// pixel past blend_cap is queued and replayed: k_render_queue runs the forward code with
 // BWD = true, which recomputes the identical decisions and forms the same terms at each
 // blend. With blend_cap 0, k_render<HEAD, true> replays every warp (the paper's way).
 #include <algorithm>
@@ -745,56 +745,38 @@ __device__ __forceinline__ void render_warp(const PipeArgs& a, const int gtile, 
     }
 }
 
-// One block per kBlocksPerTile-th of a tile; or, for the forward's second depth-slice pass
-// (slice_pass = 1), a grid of resident blocks whose warps take the queued tile warps one at a
-// time (a single call site, so that render_warp is inlined once).
 template <int HEAD, bool BWD, bool DBG>
 __global__ void __launch_bounds__(32 * kRenderWarps, (render_min_blocks<HEAD, BWD>())) k_render(PipeArgs a)
 {
     extern __shared__ uint2 sm[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const bool queue = !BWD && a.slice_pass != 0;
-    // the second depth-slice pass also stops on counts that disagreed (error bit 2)
-    if (a.status->error_bits & (queue ? 3u : 1u)) return;
-    const unsigned n = queue ? a.status->redo_n : 1u;
-    for (unsigned it = 0;; it++) {
-        int gtile, warp;
-        if (queue) {
-            unsigned item = 0;
-            if (lane == 0) item = atomicAdd(&a.status->redo_next, 1u);
-            item = __shfl_sync(kFull, item, 0);
-            if (item >= n) break;
-            const uint32_t w = a.redo_warps[item];
-            gtile = (int)(w >> 3);
-            warp = (int)(w & 7);
-        } else {
-            if (it > 0) break;
-            gtile = (int)(blockIdx.x / kBlocksPerTile);
-            warp = (int)(blockIdx.x % kBlocksPerTile) * kRenderWarps + wib;
-        }
-        render_warp<HEAD, BWD, DBG>(a, gtile, warp, lane, sm + wib * render_warp_smem(a.tail, a.mid));
-        __syncwarp();
-    }
+    if (a.status->error_bits & 1u) return;
+    render_warp<HEAD, BWD, DBG>(a, (int)(blockIdx.x / kBlocksPerTile), (int)(blockIdx.x % kBlocksPerTile) * kRenderWarps + wib,
+                           lane, sm + wib * render_warp_smem(a.tail, a.mid));
 }
 
-// Backward replay of the tile warps the stored-order kernel queued (a pixel past blend_cap):
-// a grid of resident blocks whose warps take queued tile warps one at a time, so that the
-// few replays cost no launch of a block per tile.
-template <int HEAD, bool DBG>
-__global__ void __launch_bounds__(32 * kRenderWarps, (render_min_blocks<HEAD, true>())) k_render_replay(PipeArgs a)
+// Work-list kernels: a grid of resident blocks whose warps take queued tile warps one at a
+// time, so that a few queued warps cost no launch of a block per tile. BWD: the backward replay
+// of the warps the stored-order kernel queued (a pixel past blend_cap). Forward: the second
+// depth-slice pass over the warps the first could not finish within their tiles' prefixes
+// (their lists are whole now).
+template <int HEAD, bool BWD, bool DBG>
+__global__ void __launch_bounds__(32 * kRenderWarps, (render_min_blocks<HEAD, BWD>())) k_render_queue(PipeArgs a)
 {
     extern __shared__ uint2 sm[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     if (a.status->error_bits & 1u) return;
-    const unsigned n = a.status->replay_n;
+    const unsigned n = BWD ? a.status->replay_n : a.status->redo_n;
+    unsigned* next = BWD ? &a.status->replay_next : &a.status->redo_next;
+    const uint32_t* list = BWD ? a.replay_warps : a.redo_warps;
     uint2* tailb = sm + wib * render_warp_smem(a.tail, a.mid);
     for (;;) {
         unsigned item = 0;
-        if (lane == 0) item = atomicAdd(&a.status->replay_next, 1u);
+        if (lane == 0) item = atomicAdd(next, 1u);
         item = __shfl_sync(kFull, item, 0);
         if (item >= n) break;
-        const uint32_t w = a.replay_warps[item];
-        render_warp<HEAD, true, DBG>(a, (int)(w >> 3), (int)(w & 7), lane, tailb);
+        const uint32_t w = list[item];
+        render_warp<HEAD, BWD, DBG>(a, (int)(w >> 3), (int)(w & 7), lane, tailb);
         __syncwarp();
     }
 }
@@ -941,29 +923,33 @@ cudaError_t launch_head(const PipeArgs& a, bool bwd, size_t smem, cudaStream_t s
         if ((e = ensure_smem_limit(k_render<HEAD, true, DBG>, smem, set_bwd, 64)) != cudaSuccess) return e;
         if (a.blist) {
             static int set_rep[64];
-            if ((e = ensure_smem_limit(k_render_replay<HEAD, DBG>, smem, set_rep, 64)) != cudaSuccess) return e;
+            if ((e = ensure_smem_limit(k_render_queue<HEAD, true, DBG>, smem, set_rep, 64)) != cudaSuccess) return e;
             int dev = 0, nsm = 0;
             if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
             if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
             const long long resident = (long long)nsm * render_min_blocks<HEAD, true>();
             const unsigned grid = (unsigned)std::min<long long>(resident, (long long)a.total_tiles * kBlocksPerTile);
             k_render_bwd_list<<<a.total_tiles * kBlocksPerTile, 32 * kRenderWarps, 0, s>>>(a);
-            k_render_replay<HEAD, DBG><<<grid, 32 * kRenderWarps, smem, s>>>(a);
+            k_render_queue<HEAD, true, DBG><<<grid, 32 * kRenderWarps, smem, s>>>(a);
             note_launches(2);
         } else {
             k_render<HEAD, true, DBG><<<a.total_tiles * kBlocksPerTile, 32 * kRenderWarps, smem, s>>>(a);
             note_launches(1);
         }
     } else {
-        if ((e = ensure_smem_limit(k_render<HEAD, false, DBG>, smem, set_fwd, 64)) != cudaSuccess) return e;
-        long long grid = (long long)a.total_tiles * kBlocksPerTile;
         if (a.slice_pass) {      // the second depth-slice pass: resident blocks over the queue
+            static int set_redo[64];
+            if ((e = ensure_smem_limit(k_render_queue<HEAD, false, DBG>, smem, set_redo, 64)) != cudaSuccess) return e;
             int dev = 0, nsm = 0;
             if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
             if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-            grid = std::min<long long>(grid, (long long)nsm * render_min_blocks<HEAD, false>());
+            const long long resident = (long long)nsm * render_min_blocks<HEAD, false>();
+            const unsigned grid = (unsigned)std::min<long long>(resident, (long long)a.total_tiles * kBlocksPerTile);
+            k_render_queue<HEAD, false, DBG><<<grid, 32 * kRenderWarps, smem, s>>>(a);
+        } else {
+            if ((e = ensure_smem_limit(k_render<HEAD, false, DBG>, smem, set_fwd, 64)) != cudaSuccess) return e;
+            k_render<HEAD, false, DBG><<<a.total_tiles * kBlocksPerTile, 32 * kRenderWarps, smem, s>>>(a);
         }
-        k_render<HEAD, false, DBG><<<(unsigned)grid, 32 * kRenderWarps, smem, s>>>(a);
         note_launches(1);
     }
     return cudaGetLastError();

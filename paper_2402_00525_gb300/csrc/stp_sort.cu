@@ -15,6 +15,8 @@
 // __match_any_sync, so the write order preserves the input order (stability).
 // The grid is fixed (a multiple of the SM count) and the entry count may be read from device
 // memory, so the whole sequence needs no host synchronisation and can be graph-captured.
+#include <algorithm>
+
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -210,6 +212,14 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // atomic placement order: ranges of at most kSegCap entries by the bucket-and-rank scheme of
 // k_tile_sort in shared memory, longer ones (and badly skewed ones) with four stable 8-bit
 // passes in place in global memory (the second buffer of the range is the ping-pong partner).
+//
+// Depth slices (slice_k > 0): a warp stops reading its tile's list once its 32 pixels have
+// saturated, which on dense scenes is after a small fraction of the list. So the first pass
+// orders only the words of the smallest buckets that together hold at least slice_k of them
+// (bucket order is depth order, so they are the list's prefix), publishes that prefix length
+// in tile_front and leaves the placed words untouched. The Render queues any warp that would
+// need a batch beyond the prefix; the second pass sorts those tiles' whole lists, after which
+// the queued warps are rendered again. The result is the whole-list result exactly.
 constexpr int kSegThreads = 256, kSegWarps = kSegThreads / 32, kSegCap = 4096;
 
 __device__ __forceinline__ uint32_t seg_digit(unsigned long long x, int shift)
@@ -421,13 +431,15 @@ __device__ bool bucket_plan(const unsigned long long* src, uint32_t n, uint32_t*
     return fullest <= (uint32_t)kBucketMax;
 }
 
-// Scatter src into its buckets in `scat`, then rank each word inside its bucket. With `vals`
-// set, the ranked words go straight to the output ids (and, with `keys` set too, to the
-// output keys); otherwise to ranked[].
+// Scatter the words of buckets 0..cut of src (m of them) into `scat`, then rank each inside its
+// bucket: the m smallest words in order (cut = NB - 1, m = n: all of them). With `vals` set,
+// the ranked words go straight to the output ids (and, with `keys` set too, to the output
+// keys); otherwise to ranked[].
 template <int NB>
 __device__ void bucket_rank(const unsigned long long* src, unsigned long long* scat, uint32_t n,
                             const uint32_t* bcnt, uint32_t* bcur, uint32_t kmin, uint32_t mul,
-                            unsigned long long hi, uint64_t* keys, uint32_t* vals, unsigned long long* ranked)
+                            unsigned long long hi, uint64_t* keys, uint32_t* vals, unsigned long long* ranked,
+                            uint32_t cut, uint32_t m)
 {
     for (uint32_t i0 = threadIdx.x; i0 < n; i0 += kSegUnroll * kSegThreads) {
         unsigned long long w[kSegUnroll];
@@ -435,12 +447,13 @@ __device__ void bucket_rank(const unsigned long long* src, unsigned long long* s
 #pragma unroll
         for (int u = 0; u < kSegUnroll; u++) {
             if (i0 + u * kSegThreads >= n) break;
-            scat[atomicAdd(&bcur[bucket_of((uint32_t)(w[u] >> 32), kmin, mul)], 1u)] = w[u];
+            const uint32_t b = bucket_of((uint32_t)(w[u] >> 32), kmin, mul);
+            if (b <= cut) scat[atomicAdd(&bcur[b], 1u)] = w[u];
         }
     }
     __syncthreads();
-    // bcur[b] is now the end of bucket b
-    for (uint32_t i = threadIdx.x; i < n; i += kSegThreads) {
+    // bcur[b] is now the end of bucket b (b <= cut)
+    for (uint32_t i = threadIdx.x; i < m; i += kSegThreads) {
         const unsigned long long x = scat[i];
         const uint32_t b = bucket_of((uint32_t)(x >> 32), kmin, mul);
         const uint32_t end = bcur[b], beg = end - bcnt[b];
@@ -455,68 +468,102 @@ __device__ void bucket_rank(const unsigned long long* src, unsigned long long* s
     }
 }
 
-__global__ void __launch_bounds__(kSegThreads) k_tile_sort(PipeArgs a)
+__device__ __forceinline__ void sort_tile(const PipeArgs& a, const int t, unsigned long long* seg_smem, uint32_t* red)
 {
-    extern __shared__ unsigned long long seg_smem[];               // [kSegCap] words + counters
-    __shared__ uint32_t red[3 * kSegWarps];
-    const int t = blockIdx.x;
     if (a.status->error_bits & 1u) {
         if (threadIdx.x == 0) a.ranges[t] = make_uint2(0u, 0u);
         return;
     }
     const uint32_t cnt = a.tile_counts[t];
-    const uint32_t cur = a.tile_cursor[t];
+    const uint32_t n = min(a.tile_cursor[t], cnt);
     const uint32_t off = a.tile_offsets[t];
-    // Depth slices: the first pass sorts the tile's prefix; the second, for the tiles it
-    // completes, sorts the remaining entries placed behind the prefix (all their keys are
-    // larger) and marks the list whole. A cursor that is not exactly at the end of what the pass
-    // placed means Preprocess and Duplicate disagreed (error bit 2; cannot happen).
-    uint32_t sub = 0, n = min(cur, cnt);
+    // Depth slices: the first pass may sort only the prefix of a list longer than slice_k (the
+    // placed words stay untouched behind it); the second sorts the whole lists of the tiles whose
+    // warps the Render queued.
+    bool prefix_ok = false;
     if (a.slice_k) {
-        const uint32_t front = a.tile_front[t];
         if (a.slice_pass) {
-            // counts that disagreed in the first pass stop the second (error bit 2)
-            if (a.tile_redo[t] == 0u || (a.status->error_bits & 2u)) return;
-            sub = front;
-            n = cur > front ? min(cur, cnt) - front : 0u;
-            __syncthreads();                  // every thread has read tile_front
-            if (threadIdx.x == 0) a.tile_front[t] = front + n;
+            if (a.tile_redo[t] == 0u) return;
         } else {
-            n = min(cur, front);
+            prefix_ok = n > (uint32_t)a.slice_k;
+            if (threadIdx.x == 0) a.tile_redo[t] = 0u;
         }
-        if (threadIdx.x == 0 && cur != (a.slice_pass ? cnt : front)) atomicOr(&a.status->error_bits, 2u);
     }
-    if (threadIdx.x == 0) a.ranges[t] = make_uint2(off, off + sub + n);
-    if (n == 0) return;
-    unsigned long long* g0 = (unsigned long long*)a.dup_keys + off + sub;   // placed words (buffer A)
-    unsigned long long* g1 = (unsigned long long*)a.keys + off + sub;       // partner (buffer B)
-    uint32_t* ov = a.vals + off + sub;
+    // the sorted range: m words (m < n: a prefix, which the Render sees through tile_front)
+    auto publish = [&](uint32_t m) {
+        if (threadIdx.x == 0) {
+            a.ranges[t] = make_uint2(off, off + m);
+            if (a.slice_k) a.tile_front[t] = m < n ? m : cnt;
+        }
+    };
+    if (n == 0) {
+        publish(0);
+        return;
+    }
+    unsigned long long* g0 = (unsigned long long*)a.dup_keys + off;   // placed words (buffer A)
+    unsigned long long* g1 = (unsigned long long*)a.keys + off;   // partner (buffer B)
+    uint32_t* ov = a.vals + off;
     const unsigned long long hi = (unsigned long long)t << 32;
     // the Render reads only the ids; the (tile, depth) keys are written for inspection only
-    uint64_t* okeys = (a.flags & kFlagDebugStats) ? a.keys + off + sub : nullptr;
+    uint64_t* okeys = (a.flags & kFlagDebugStats) ? a.keys + off : nullptr;
     uint32_t kmin, mul;
+    // smallest prefix of whole buckets holding >= slice_k words: the first bucket whose end
+    // (bucket starts bcur after bucket_plan, plus its count) reaches slice_k
+    auto prefix_cut = [&](const uint32_t* bcnt, const uint32_t* bcur, int nb, uint32_t& cut, uint32_t& m) {
+        cut = (uint32_t)nb - 1u;
+        m = n;
+        if (!prefix_ok) return;
+        uint32_t lo = 0, hb = (uint32_t)nb - 1u;
+        while (lo < hb) {
+            const uint32_t md = (lo + hb) >> 1;
+            if (bcur[md] + bcnt[md] >= (uint32_t)a.slice_k) hb = md; else lo = md + 1;
+        }
+        cut = lo;
+        m = bcur[lo] + bcnt[lo];
+    };
+    // every thread takes the cut before any thread's scatter moves the bucket cursors
+    auto prefix_cut_sync = [&](const uint32_t* bcnt, const uint32_t* bcur, int nb, uint32_t& cut, uint32_t& m) {
+        prefix_cut(bcnt, bcur, nb, cut, m);
+        __syncthreads();
+    };
     if (n <= (uint32_t)kSegCap) {
         uint32_t* bcnt = reinterpret_cast<uint32_t*>(seg_smem + kSegCap);
         uint32_t* bcur = bcnt + kBucketsSmall;
         if (bucket_plan<kBucketsSmall>(g0, n, bcnt, bcur, red, kmin, mul)) {
-            bucket_rank<kBucketsSmall>(g0, seg_smem, n, bcnt, bcur, kmin, mul, hi, okeys, ov, nullptr);
+            uint32_t cut, m;
+            prefix_cut_sync(bcnt, bcur, kBucketsSmall, cut, m);
+            publish(m);
+            bucket_rank<kBucketsSmall>(g0, seg_smem, n, bcnt, bcur, kmin, mul, hi, okeys, ov, nullptr, cut, m);
             return;
         }
     } else {
         uint32_t* bcnt = reinterpret_cast<uint32_t*>(seg_smem);      // 2 x 4096 counters
         uint32_t* bcur = bcnt + kBucketsLarge;
         if (bucket_plan<kBucketsLarge>(g0, n, bcnt, bcur, red, kmin, mul)) {
-            // scatter into the partner range, rank back into the placed range, then write out
-            bucket_rank<kBucketsLarge>(g0, g1, n, bcnt, bcur, kmin, mul, hi, nullptr, nullptr, g0);
+            if (!okeys) {
+                // scatter into the partner range and rank straight into the ids: the placed
+                // words stay intact for a later whole sort
+                uint32_t cut, m;
+                prefix_cut_sync(bcnt, bcur, kBucketsLarge, cut, m);
+                publish(m);
+                bucket_rank<kBucketsLarge>(g0, g1, n, bcnt, bcur, kmin, mul, hi, nullptr, ov, nullptr, cut, m);
+                return;
+            }
+            // with the inspection keys (written over the partner range): the whole list, ranked
+            // back into the placed range and written out
+            publish(n);
+            bucket_rank<kBucketsLarge>(g0, g1, n, bcnt, bcur, kmin, mul, hi, nullptr, nullptr, g0,
+                                       kBucketsLarge - 1, n);
             __syncthreads();
             for (uint32_t i = threadIdx.x; i < n; i += kSegThreads) {
                 const unsigned long long v = g0[i];
-                if (okeys) okeys[i] = hi | (v >> 32);
+                okeys[i] = hi | (v >> 32);
                 ov[i] = (uint32_t)v;
             }
             return;
         }
     }
+    publish(n);
     __syncthreads();                      // shared memory is reused by the radix passes
     // four stable 8-bit passes in global memory, then ties ordered by id
     uint32_t (*whist)[kRadix] = reinterpret_cast<uint32_t (*)[kRadix]>(seg_smem);
@@ -527,6 +574,24 @@ __global__ void __launch_bounds__(kSegThreads) k_tile_sort(PipeArgs a)
         const unsigned long long v = g0[i];
         if (okeys) okeys[i] = hi | (v >> 32);
         ov[i] = (uint32_t)v;
+    }
+}
+
+// One block per tile. The second depth-slice pass (REDO) runs a grid of resident blocks over
+// the tiles instead, which returns at once when the Render queued no warp.
+template <bool REDO>
+__global__ void __launch_bounds__(kSegThreads) k_tile_sort(PipeArgs a)
+{
+    extern __shared__ unsigned long long seg_smem[];               // [kSegCap] words + counters
+    __shared__ uint32_t red[3 * kSegWarps];
+    if (!REDO) {
+        sort_tile(a, blockIdx.x, seg_smem, red);
+        return;
+    }
+    if (a.status->redo_n == 0u) return;
+    for (int t = blockIdx.x; t < a.total_tiles; t += gridDim.x) {
+        sort_tile(a, t, seg_smem, red);
+        __syncthreads();                  // shared memory is reused by the next tile
     }
 }
 
@@ -672,10 +737,20 @@ cudaError_t launch_tile_sort(const PipeArgs& a, cudaStream_t s)
 {
     if (a.total_tiles == 0) return cudaSuccess;
     const size_t smem = tile_sort_smem_bytes();
-    static int set_dev[64];
-    cudaError_t e = ensure_smem_limit(k_tile_sort, smem, set_dev, 64);
-    if (e != cudaSuccess) return e;
-    k_tile_sort<<<a.total_tiles, kSegThreads, smem, s>>>(a);
+    cudaError_t e;
+    if (a.slice_pass) {      // the second depth-slice pass: resident blocks (40 KB each) over the tiles
+        static int set_redo[64];
+        if ((e = ensure_smem_limit(k_tile_sort<true>, smem, set_redo, 64)) != cudaSuccess) return e;
+        int dev = 0, nsm = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        const unsigned grid = (unsigned)std::min<long long>((long long)nsm * 4, a.total_tiles);
+        k_tile_sort<true><<<grid, kSegThreads, smem, s>>>(a);
+    } else {
+        static int set_dev[64];
+        if ((e = ensure_smem_limit(k_tile_sort<false>, smem, set_dev, 64)) != cudaSuccess) return e;
+        k_tile_sort<false><<<a.total_tiles, kSegThreads, smem, s>>>(a);
+    }
     note_launches(1);
     return cudaGetLastError();
 }
