@@ -142,7 +142,23 @@ struct PixCtx {
     float g0, g1, g2, gz, gbg;   // backward: dL/drgb, dL/ddepth, <dL/drgb, bg>
     float Cf0, Cf1, Cf2, Zf, Tf; // backward: final colour (no background), depth, T
     long long bl;                // stored blend order: slot 0 of this pixel (slot k at bl + 32 k)
+    const float4* vrec;          // this view's first record (records of view-local ids follow)
 };
+
+// Record `i` of a view from the view's first record: one 32 x 32 -> 64-bit multiply-add for
+// the address instead of 64-bit index arithmetic at every load.
+__device__ __forceinline__ Rec load_rec_v(const float4* __restrict__ base, uint32_t i)
+{
+    Rec r;
+    const float4* p = base + (unsigned long long)i * kRecFloat4;
+    r.r0 = __ldg(p);
+    r.r1 = __ldg(p + 1);
+    r.r2 = __ldg(p + 2);
+    r.r3 = __ldg(p + 3);
+    r.r4 = __ldg(p + 4);
+    r.r5 = __ldg(p + 5);
+    return r;
+}
 
 // Gradient terms of one blended Gaussian (Sec. 3.5), given the pixel's state just after the
 // blend: T = T_i (transmittance in front of it), C / Z = colour and depth accumulated up to
@@ -217,15 +233,32 @@ template <int HEAD, bool BWD, bool DBG>
 __device__ __forceinline__ void blend(const PipeArgs& a, const ViewDesc& V, Px<HEAD, DBG>& s,
                                       const PixCtx& c, float t, uint32_t id, float val)
 {
-    if (s.done) return;
     const float alpha = fminf(a.alpha_max, val);
     const float Tn = __fmul_rn(s.T, __fsub_rn(1.f, alpha));
+    if (!BWD && !DBG) {
+        // The timed forward blends without branches: a saturated or saturating pixel adds a
+        // zero weight (its record, a valid one, is loaded all the same) and stores nothing, so
+        // the warp takes no divergent region per blend.
+        const bool go = !s.done && !(Tn < a.t_min);
+        s.done = !go;
+        const float4 r2 = __ldg(c.vrec + (unsigned long long)id * kRecFloat4 + 2);   // (opacity, colour)
+        const float wgt = go ? alpha * s.T : 0.f;
+        s.C0 += r2.y * wgt;
+        s.C1 += r2.z * wgt;
+        s.C2 += r2.w * wgt;
+        s.Z += t * wgt;
+        if (go && a.blist && s.nbl < (uint32_t)a.blend_cap) __stcs(a.blist + c.bl + 32ll * s.nbl, id);
+        s.T = go ? Tn : s.T;
+        s.nbl += go ? 1u : 0u;
+        return;
+    }
+    if (s.done) return;
     if (Tn < a.t_min) {
         s.done = true;
         return;
     }
     const long long ri = V.rec_off + id;
-    const float4 r2 = __ldg(a.geom + kRecFloat4 * ri + 2);       // (opacity, colour)
+    const float4 r2 = __ldg(c.vrec + (unsigned long long)id * kRecFloat4 + 2);       // (opacity, colour)
     const float4 col = make_float4(r2.y, r2.z, r2.w, 0.f);
     const float wgt = alpha * s.T;
     s.C0 += col.x * wgt;
@@ -409,7 +442,7 @@ __device__ __forceinline__ void head_consume(const PipeArgs& a, const ViewDesc& 
 #pragma unroll 1
     for (int k = 0; k < n && !s.done; k++) {
         const uint32_t gid = fq[k];
-        const Rec r = load_rec(a.geom, V.rec_off + gid);
+        const Rec r = load_rec_v(c.vrec, gid);
         const float val = splat_value(r, c.xc, c.yc);
         if constexpr (DBG && !BWD) s.npx++;
         if (fminf(a.alpha_max, val) >= a.eps_o) {
@@ -453,7 +486,7 @@ __device__ void midstage(const PipeArgs& a, const ViewDesc& V, Px<HEAD, DBG>& s,
         if (e < cnt) {
             gid = chunk[e].y;
             if (qlive) {
-                const Rec r = load_rec(a.geom, V.rec_off + gid);
+                const Rec r = load_rec_v(c.vrec, gid);
                 const Box bq = bQ;
                 float t;
                 if (box_keep_depth(r, bq, V, cull_eps, centre, &t)) key = depth_key(t);
@@ -575,6 +608,7 @@ __device__ __forceinline__ void render_warp(const PipeArgs& a, const int gtile, 
     c.n = ray_norm(c.u, c.w);
     c.pix = inside ? V.pix_off + (long long)pyi * W + pxi : -1;
     c.bl = ((long long)(gtile * 8 + warp) * a.blend_cap) * 32 + lane;
+    c.vrec = a.geom + kRecFloat4 * V.rec_off;
     c.g0 = c.g1 = c.g2 = c.gz = c.gbg = 0.f;
     c.Cf0 = c.Cf1 = c.Cf2 = c.Zf = c.Tf = 0.f;
     if (BWD && inside) {
@@ -632,7 +666,7 @@ __device__ __forceinline__ void render_warp(const PipeArgs& a, const int gtile, 
             const unsigned live = __ballot_sync(kFull, !s.done);
             const bool s0 = sval[0] && (live & 0xFFFFu) != 0, s1 = sval[1] && (live >> 16) != 0;
             if (in && (s0 || s1)) {
-                const Rec r = load_rec(a.geom, V.rec_off + gid);
+                const Rec r = load_rec_v(c.vrec, gid);
                 float t;
                 if (s0 && box_keep_depth(r, bS[0], V, cull_eps, centre, &t)) k0 = depth_key(t);
                 if (s1 && box_keep_depth(r, bS[1], V, cull_eps, centre, &t)) k1 = depth_key(t);
@@ -828,6 +862,7 @@ __global__ void __launch_bounds__(32 * kRenderWarps, STP_BWD_LIST_MIN_BLOCKS * 4
     c.n = ray_norm(c.u, c.w);
     c.pix = inside ? V.pix_off + (long long)pyi * V.W + pxi : -1;
     c.bl = ((long long)(gtile * 8 + warp) * a.blend_cap) * 32 + lane;
+    c.vrec = a.geom + kRecFloat4 * V.rec_off;
     const uint32_t nb = inside ? a.blist_count[c.pix] : 0u;
     if (__any_sync(kFull, nb > (uint32_t)a.blend_cap)) {           // queued for the replay
         if (lane == 0) a.replay_warps[atomicAdd(&a.status->replay_n, 1u)] = (uint32_t)(gtile * 8 + warp);
@@ -977,6 +1012,7 @@ __device__ __forceinline__ void flat_init(const PipeArgs& a, const ViewDesc& V, 
     c.n = ray_norm(c.u, c.w);
     c.pix = (pxi < V.W && pyi < V.H) ? V.pix_off + (long long)pyi * V.W + pxi : -1;
     c.bl = 0;                    // the flat orders store no blend order
+    c.vrec = a.geom + kRecFloat4 * V.rec_off;
     c.g0 = c.g1 = c.g2 = c.gz = c.gbg = 0.f;
     c.Cf0 = c.Cf1 = c.Cf2 = c.Zf = c.Tf = 0.f;
 }
