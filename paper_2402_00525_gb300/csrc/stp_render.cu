@@ -882,6 +882,7 @@ __global__ void __launch_bounds__(32 * kRenderWarps, STP_BWD_LIST_MIN_BLOCKS * 4
     }
     const bool with_depth = a.d_depth != nullptr;
     const uint32_t* ids = a.blist + c.bl;
+    float* const vgrad = a.grad_geom + V.rec_off * kGradStride;   // this view's first scratch record
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, Z = 0.f;
     const uint32_t nmax = __reduce_max_sync(kFull, nb);
     uint32_t nxt = nb > 0 ? __ldcs(ids) : 0u;
@@ -895,7 +896,7 @@ __global__ void __launch_bounds__(32 * kRenderWarps, STP_BWD_LIST_MIN_BLOCKS * 4
         float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0;
         float qc = 0.f;
         if (valid) {
-            const float4* rp = a.geom + kRecFloat4 * ri;
+            const float4* rp = c.vrec + (unsigned long long)id * kRecFloat4;
             Rec r;
             r.r0 = __ldg(rp);
             r.r1 = __ldg(rp + 1);
@@ -944,7 +945,12 @@ __global__ void __launch_bounds__(32 * kRenderWarps, STP_BWD_LIST_MIN_BLOCKS * 4
             }
         }
         __syncwarp();                                 // the next step rewrites the staging
-        if (valid && lane == leader) grad_red(a, ri, q0, q1, qc);
+        if (valid && lane == leader) {
+            float* gg = vgrad + (unsigned long long)id * kGradStride;
+            atomicAdd(reinterpret_cast<float4*>(gg), q0);
+            atomicAdd(reinterpret_cast<float4*>(gg + 4), q1);
+            atomicAdd(gg + 8, qc);
+        }
     }
     if (inside && __float_as_uint(T) != __float_as_uint(c.Tf)) atomicOr(&a.status->error_bits, 8u);
 }
