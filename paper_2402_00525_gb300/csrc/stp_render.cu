@@ -143,6 +143,7 @@ struct PixCtx {
     float Cf0, Cf1, Cf2, Zf, Tf; // backward: final colour (no background), depth, T
     long long bl;                // stored blend order: slot 0 of this pixel (slot k at bl + 32 k)
     const float4* vrec;          // this view's first record (records of view-local ids follow)
+    float* vgrad;                // this view's first gradient-scratch record (backward)
 };
 
 // Record `i` of a view from the view's first record: one 32 x 32 -> 64-bit multiply-add for
@@ -268,8 +269,11 @@ __device__ __forceinline__ void blend(const PipeArgs& a, const ViewDesc& V, Px<H
     if (BWD) {
         float4 q0, q1;
         float qc;
-        grad_terms(a, c, ri, col, __ldg(a.geom + kRecFloat4 * ri), alpha, val, t, s.T, s.C0, s.C1, s.C2, s.Z, q0, q1, qc);
-        grad_red(a, ri, q0, q1, qc);
+        grad_terms(a, c, ri, col, __ldg(c.vrec + (unsigned long long)id * kRecFloat4), alpha, val, t, s.T, s.C0, s.C1, s.C2, s.Z, q0, q1, qc);
+        float* gg = c.vgrad + (unsigned long long)id * kGradStride;
+        atomicAdd(reinterpret_cast<float4*>(gg), q0);
+        atomicAdd(reinterpret_cast<float4*>(gg + 4), q1);
+        atomicAdd(gg + 8, qc);
     }
     // the stored blend order (backward without replay): the first blend_cap ids of the pixel,
     // stored and later loaded with the evict-first hint (each id is touched once either way)
@@ -609,6 +613,7 @@ __device__ __forceinline__ void render_warp(const PipeArgs& a, const int gtile, 
     c.pix = inside ? V.pix_off + (long long)pyi * W + pxi : -1;
     c.bl = ((long long)(gtile * 8 + warp) * a.blend_cap) * 32 + lane;
     c.vrec = a.geom + kRecFloat4 * V.rec_off;
+    c.vgrad = a.grad_geom ? a.grad_geom + V.rec_off * kGradStride : nullptr;
     c.g0 = c.g1 = c.g2 = c.gz = c.gbg = 0.f;
     c.Cf0 = c.Cf1 = c.Cf2 = c.Zf = c.Tf = 0.f;
     if (BWD && inside) {
@@ -863,6 +868,7 @@ __global__ void __launch_bounds__(32 * kRenderWarps, STP_BWD_LIST_MIN_BLOCKS * 4
     c.pix = inside ? V.pix_off + (long long)pyi * V.W + pxi : -1;
     c.bl = ((long long)(gtile * 8 + warp) * a.blend_cap) * 32 + lane;
     c.vrec = a.geom + kRecFloat4 * V.rec_off;
+    c.vgrad = a.grad_geom ? a.grad_geom + V.rec_off * kGradStride : nullptr;
     const uint32_t nb = inside ? a.blist_count[c.pix] : 0u;
     if (__any_sync(kFull, nb > (uint32_t)a.blend_cap)) {           // queued for the replay
         if (lane == 0) a.replay_warps[atomicAdd(&a.status->replay_n, 1u)] = (uint32_t)(gtile * 8 + warp);
@@ -1019,6 +1025,7 @@ __device__ __forceinline__ void flat_init(const PipeArgs& a, const ViewDesc& V, 
     c.pix = (pxi < V.W && pyi < V.H) ? V.pix_off + (long long)pyi * V.W + pxi : -1;
     c.bl = 0;                    // the flat orders store no blend order
     c.vrec = a.geom + kRecFloat4 * V.rec_off;
+    c.vgrad = a.grad_geom ? a.grad_geom + V.rec_off * kGradStride : nullptr;
     c.g0 = c.g1 = c.g2 = c.gz = c.gbg = 0.f;
     c.Cf0 = c.Cf1 = c.Cf2 = c.Zf = c.Tf = 0.f;
 }
