@@ -60,6 +60,17 @@ def test_workspace_layout_is_consistent(lib):
         q.blend_cap, q.mode = cap, mode
         Lq = N.layout(sc.n, cams, q)
         assert Lq.blend_ids == 0 and Lq.blend_count == 0 and Lq.replay_warps == 0
+    # depth slices: the prefix lengths, second-pass flags and warp queue exist only for the HIER
+    # order over the partitioned sort with slice_k > 0, one word per tile (eight for the queue)
+    assert prm.slice_k > 0 and d["tile_front"] and d["tile_redo"] and d["redo_warps"]
+    assert d["tile_redo"] >= d["tile_front"] + 256 * 4 and d["redo_warps"] >= d["tile_redo"] + 256 * 4
+    assert d["total"] >= d["redo_warps"] + 256 * 8 * 4
+    for flags, k, mode in ((0, 0, I.MODE_HIER), (N.FLAG_GLOBAL_SORT, 2048, I.MODE_HIER),
+                           (0, 2048, I.MODE_FULL), (0, 2048, I.MODE_WINDOW)):
+        q = N.params_struct(prm, flags)
+        q.slice_k, q.mode = k, mode
+        Lq = N.layout(sc.n, cams, q)
+        assert Lq.tile_front == 0 and Lq.tile_redo == 0 and Lq.redo_warps == 0, (flags, k, mode)
     # several views of mixed sizes: tiles and pixels add up, key bits grow with the tile count
     cams4 = I.orbit_cameras(5, 15.0, 2.0, I.C4_SIZES, 50.0)
     L4 = N.layout(1000, cams4, N.params_struct(I.RenderParams()))
@@ -71,7 +82,8 @@ def test_workspace_layout_is_consistent(lib):
     ("tail", 48, N.STP_ERR_ARG), ("tail", 80, N.STP_ERR_ARG), ("mid", 6, N.STP_ERR_ARG),
     ("mid", 10, N.STP_ERR_ARG), ("head", 5, N.STP_ERR_NOT_SUPPORTED), ("lb_threshold", 0, N.STP_ERR_ARG),
     ("eps_o", 0.0, N.STP_ERR_ARG), ("mode", 7, N.STP_ERR_ARG), ("mode", -1, N.STP_ERR_ARG), ("max_entries", -1, N.STP_ERR_ARG),
-    ("blend_cap", -1, N.STP_ERR_ARG), ("blend_cap", 4097, N.STP_ERR_ARG),
+    ("blend_cap", -1, N.STP_ERR_ARG), ("blend_cap", 4097, N.STP_ERR_ARG), ("slice_k", -1, N.STP_ERR_ARG),
+    ("full_max_passes", -1, N.STP_ERR_ARG),
 ])
 def test_bad_parameters_rejected_on_host(lib, field, value, code):
     sc, cams, prm = I.plain_forward_workload()
