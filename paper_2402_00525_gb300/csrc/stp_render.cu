@@ -387,8 +387,27 @@ __device__ __forceinline__ void head_push(const PipeArgs& a, const ViewDesc& V, 
     if (full) {
         float k = key, v = val;
         uint32_t i = id;
-        if (evict_first) head_pop(s, k, i, v);
-        else head_exchange(s, k, i, v);
+        if (evict_first) {
+            head_pop(s, k, i, v);
+        } else if (key >= s.hk[HEAD - 1]) {
+            // the common case (entries reach a pixel nearly in depth order): the new entry is
+            // behind every held one, so the exchange reduces to a shift -- the front leaves, the
+            // rest move up, the new entry goes last (after equal keys, as the network would put it)
+            k = s.hk[0];
+            i = s.hid[0];
+            v = s.hv[0];
+#pragma unroll
+            for (int j = 0; j + 1 < HEAD; j++) {
+                s.hk[j] = s.hk[j + 1];
+                s.hid[j] = s.hid[j + 1];
+                s.hv[j] = s.hv[j + 1];
+            }
+            s.hk[HEAD - 1] = key;
+            s.hid[HEAD - 1] = id;
+            s.hv[HEAD - 1] = val;
+        } else {
+            head_exchange(s, k, i, v);
+        }
         blend<HEAD, BWD, DBG>(a, V, s, c, k, i, v);
     }
     if (!full || (evict_first && !s.done)) head_insert(s, key, id, val);
