@@ -565,6 +565,13 @@ __device__ void midstage(const PipeArgs& a, const ViewDesc& V, Px<HEAD, DBG>& s,
 
 __device__ __forceinline__ void merge_tail(const uint2* src, int ne, const uint2* nw, int nn, uint2* dst, int lane)
 {
+    // warp-uniform common case: the batch's survivors all lie behind the tail (existing entries
+    // first on equal keys), so the merge is a copy and an append
+    if (nn == 0 || ne == 0 || nw[0].x >= src[ne - 1].x) {
+        for (int e = lane; e < ne; e += 32) dst[e] = src[e];
+        if (lane < nn) dst[ne + lane] = nw[lane];
+        return;
+    }
     for (int e = lane; e < ne; e += 32) {
         const uint2 x = src[e];
         int lo = 0, hi = nn;
