@@ -416,6 +416,18 @@ __device__ __forceinline__ uint32_t kept_depth_key(const PipeArgs& a, const View
     return fkey(t);
 }
 
+// Column and row of the k-th tile (row major) of a rectangle w tiles wide, with rw = 1 / w
+// rounded to nearest, and no integer division: the quotient (k + 1/2) / w lies at least 1/(2w)
+// from an integer, and its float evaluation errs by under 2^-22 of its value, so the floor is
+// exact for every k below 2^20 (a rectangle never holds more tiles than a 16384 x 16384
+// view's 2^20).
+__device__ __forceinline__ int2 rect_cell(int k, int w, float rw)
+{
+    const int y = (int)(((float)k + 0.5f) * rw);
+    return make_int2(k - y * w, y);
+}
+__device__ __forceinline__ float rect_rcp(int w) { return w > 0 ? 1.f / (float)w : 0.f; }
+
 // Count (EMIT = false) or write (EMIT = true) the kept tiles of this lane's Gaussian, with the
 // two-phase warp load balancing. Every lane of the warp must call it. Preprocess records the
 // kept candidates of the per-thread phase in a bit mask (rectangles of at most 32 tiles), so
@@ -435,8 +447,9 @@ __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, int vidx, b
     if (!big) {
         if (!EMIT) {
             uint32_t mask = 0;
-            for (int k = 0; k < ncand; k++) {
-                const int tx = rc.x + k % w, ty = rc.y + k / w;
+            int cx = 0, cy = 0;                          // column and row of candidate k
+            for (int k = 0; k < ncand; k++, cx = cx + 1 < w ? cx + 1 : 0, cy += cx == 0) {
+                const int tx = rc.x + cx, ty = rc.y + cy;
                 const Box b = block_box(tx * kTile, ty * kTile, kTile, V.W, V.H);
                 if (tile_keep(a, r, b)) {
                     cnt++;
@@ -520,6 +533,9 @@ __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, int vidx, b
         bigmask &= bigmask - 1;
         const Rec rs = shfl_rec(r, src);
         const int ws = __shfl_sync(kFull, w, src), nc = __shfl_sync(kFull, ncand, src);
+        // the count divides without an integer division; Duplicate keeps k % w, k / w (the float
+        // path measured slower there, its spread placement being register bound)
+        const float rws = EMIT ? 0.f : __shfl_sync(kFull, rect_rcp(w), src);
         const int x0 = __shfl_sync(kFull, (int)rc.x, src), y0 = __shfl_sync(kFull, (int)rc.y, src);
         const uint32_t offs = __shfl_sync(kFull, off, src), wants = __shfl_sync(kFull, want, src);
         const uint32_t gids = __shfl_sync(kFull, gid, src);
@@ -531,7 +547,8 @@ __device__ uint32_t tiles_pass(const PipeArgs& a, const ViewDesc& V, int vidx, b
             bool keep = false;
             uint32_t dk = 0, gt = 0;
             if (k < nc) {
-                const int tx = x0 + k % ws, ty = y0 + k / ws;
+                const int2 cl = EMIT ? make_int2(k % ws, k / ws) : rect_cell(k, ws, rws);
+                const int tx = x0 + cl.x, ty = y0 + cl.y;
                 gt = (uint32_t)(Vs.tile_off + ty * Vs.tiles_x + tx);
                 if (EMIT) keep = tile_depth_key(a, Vs, rs, vzs, tx, ty, &dk);
                 else keep = tile_keep(a, rs, block_box(tx * kTile, ty * kTile, kTile, Vs.W, Vs.H));
@@ -620,6 +637,7 @@ __device__ uint32_t count_spread(const PipeArgs& a, int vidx, const Rec& r, usho
     const int total = __shfl_sync(kFull, incl, 31);
     const int first_me = incl - n;
     const int w = (int)rc.z - (int)rc.x;
+    const float rw = rect_rcp(w);
     uint32_t mask = 0;
     for (int base = 0; base < total; base += 32) {
         const int p = base + lane;
@@ -631,6 +649,7 @@ __device__ uint32_t count_spread(const PipeArgs& a, int vidx, const Rec& r, usho
         const int first = __shfl_sync(kFull, first_me, src);
         const int x0 = __shfl_sync(kFull, (int)rc.x, src), y0 = __shfl_sync(kFull, (int)rc.y, src);
         const int ws = __shfl_sync(kFull, w, src);
+        const float rws = __shfl_sync(kFull, rw, src);
         const int vs = __shfl_sync(kFull, vidx, src);
         Rec rs;                                        // what the cull test reads: mean, conic, opacity
         rs.r0 = make_float4(__shfl_sync(kFull, r.r0.x, src), __shfl_sync(kFull, r.r0.y, src),
@@ -641,8 +660,8 @@ __device__ uint32_t count_spread(const PipeArgs& a, int vidx, const Rec& r, usho
         rs.r3 = rs.r4 = rs.r5 = make_float4(0.f, 0.f, 0.f, 0.f);
         bool keep = false;
         if (p < total) {
-            const int k = p - first;
-            const int tx = x0 + k % ws, ty = y0 + k / ws;
+            const int2 cl = rect_cell(p - first, ws, rws);
+            const int tx = x0 + cl.x, ty = y0 + cl.y;
             const ViewDesc& Vs = a.views[vs];
             keep = tile_keep(a, rs, block_box(tx * kTile, ty * kTile, kTile, Vs.W, Vs.H));
             if (keep && a.partitioned) count_entry(a, (uint32_t)(Vs.tile_off + ty * Vs.tiles_x + tx));
