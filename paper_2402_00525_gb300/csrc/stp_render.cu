@@ -30,6 +30,11 @@
 // Blending is front to back with the 3DGS early-out (the Gaussian that would take T below
 // t_min is not blended and the ray stops).
 //
+// Depth slices (slice_k > 0): when the per-tile sort ordered only a prefix of a tile's list, a
+// warp renders that prefix's complete 32-entry batches (the whole list's first batches); a warp
+// still holding an unsaturated pixel when it needs the next batch writes nothing and queues
+// itself, and after its tile's list is sorted whole k_render_queue renders it again.
+//
 // Backward (Sec. 3.5): the gradients of a blend need the suffix colour C - C_i and T_N / T_i,
 // so the blends are visited front to back in the forward's order. A forward that a backward
 // follows stores each pixel's first blend_cap blended ids (4 bytes a blend), and
@@ -850,7 +855,7 @@ __global__ void __launch_bounds__(32 * kRenderWarps, (render_min_blocks<HEAD, BW
 // ids it blended in blend order, so the gradients need no replay of the queues: each thread
 // walks its pixel's ids front to back, recomputes alpha (and, for a depth gradient, t_opt) from
 // the record with the forward's own rounding, and forms the same terms as the replay. Warps with
-// a pixel past the capacity are queued for the replay kernel.
+// a pixel past the capacity are queued for the replay (k_render_queue with BWD = true).
 // Same block shape and pixel mapping as the forward. The product of the recomputed (1 - alpha)
 // must reproduce the forward's final T bit for bit; a pixel where it does not sets error bit 8.
 //

@@ -1,10 +1,10 @@
 """Depth-slice list building (RenderParams.slice_k) against whole lists (slice_k = 0).
 
-The first pass builds each tile's sorted list only up to a log-depth bucket boundary holding at
-least slice_k entries. A Render warp whose pixels all terminate within the complete 32-entry
-batches of that prefix has consumed exactly what it would consume from the whole list; the
-others are queued, their tiles' lists are completed and sorted behind the prefix, and the
-warps are rendered again. So every output -- image, depth, final T, blend count, blend-order
+The per-tile sort orders each tile's list only up to the first boundary of its depth buckets
+that holds at least slice_k entries. A Render warp whose pixels all terminate within the
+complete 32-entry batches of that prefix has consumed exactly what it would consume from the
+whole list; the others are queued, their tiles' lists are sorted whole, and the warps are
+rendered again. So every output -- image, depth, final T, blend count, blend-order
 hash, sort error, the stored blend order and the gradients -- must equal the whole-list run.
 slice_k = 1 sends nearly every warp of every covered tile through the second pass.
 """
