@@ -7,9 +7,11 @@ ablation on the GPU at hand and for the caller's workload, and picks a table fro
 Two kinds of knobs are swept:
 
 * knobs that never change the image: Duplicate's load-balancing threshold (which Gaussians
-  are expanded by a warp instead of their own thread, Sec. 3.4) and the sort path (per-tile
-  partitioned sort or one global radix sort, appendix B.3). For these the fastest setting
-  is taken, after checking that its image is bit-identical to the base parameters';
+  are expanded by a warp instead of their own thread, Sec. 3.4), the sort path (per-tile
+  partitioned sort or one global radix sort, appendix B.3) and, for the per-tile sort, the
+  depth-slice size slice_k (how much of each tile's list it orders before the Render asks for
+  more). For these the fastest setting is taken, after checking that its image is
+  bit-identical to the base parameters';
 * the queue sizes (tail = 32n+32, mid = 4m+4, head window k), which set how far the
   hierarchical resort can move a Gaussian (Sec. 3.3) and so change the sort error delta and
   the image. A setting is admissible under policy "same-result" only if it equals the base
@@ -36,10 +38,11 @@ from . import _native as N
 from . import inputs as I
 from . import renderer as R
 
-SPACE = dict(tail=(64, 96, 128), mid=(8, 12, 16, 20), head=(4, 8, 16), lb_threshold=(16, 32, 64))
+SPACE = dict(tail=(64, 96, 128), mid=(8, 12, 16, 20), head=(4, 8, 16), lb_threshold=(16, 32, 64),
+             slice_k=(0, 1024, 2048, 4096))
 POLICIES = ("same-result", "no-worse", "fastest")
 TABLE_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
-_TABLE_KEYS = ("tail", "mid", "head", "lb_threshold", "flags")
+_TABLE_KEYS = ("tail", "mid", "head", "lb_threshold", "flags", "slice_k")
 
 
 def table(workload: str) -> dict | None:
@@ -80,11 +83,13 @@ class Trial:
     delta_avg: float             # sort error over pixels that blend at least one Gaussian
     delta_max: float
     same_image: bool             # bit-identical rgb/depth/T and blend order to the base setting
+    slice_k: int = -1            # depth-slice size of the per-tile sort (-1: the base's)
 
     def params(self, base: I.RenderParams) -> I.RenderParams:
         flags = (base.flags & ~N.FLAG_GLOBAL_SORT) | (N.FLAG_GLOBAL_SORT if self.global_sort else 0)
         return dataclasses.replace(base, tail=self.tail, mid=self.mid, head=self.head,
-                                   lb_threshold=self.lb_threshold, flags=flags)
+                                   lb_threshold=self.lb_threshold, flags=flags,
+                                   slice_k=self.slice_k if self.slice_k >= 0 else base.slice_k)
 
 
 class _Workload:
@@ -161,8 +166,8 @@ def tune(scenes, cams: Sequence[I.Camera], base: I.RenderParams | None = None,
     (b_avg, b_max), b_img = _debug_run(w, base)
     trials: List[Trial] = []
 
-    def run(tail, mid, head, lb, gsort, img_ref):
-        t = Trial(tail, mid, head, lb, gsort, 0.0, 0.0, 0.0, False)
+    def run(tail, mid, head, lb, gsort, img_ref, slice_k=-1):
+        t = Trial(tail, mid, head, lb, gsort, 0.0, 0.0, 0.0, False, slice_k)
         prm = t.params(base)
         (t.delta_avg, t.delta_max), img = _debug_run(w, prm)
         t.same_image = _same(img, img_ref)
@@ -171,15 +176,17 @@ def tune(scenes, cams: Sequence[I.Camera], base: I.RenderParams | None = None,
         del r
         torch.cuda.empty_cache()
         trials.append(t)
-        say("tail %3d mid %2d head %2d lb %2d %s: %8.3f ms  delta avg %.5f max %.4f %s" % (
-            tail, mid, head, lb, "global" if gsort else "tiles ", t.ms, t.delta_avg, t.delta_max,
-            "same image" if t.same_image else ""))
+        say("tail %3d mid %2d head %2d lb %2d %s slice %4d: %8.3f ms  delta avg %.5f max %.4f %s" % (
+            tail, mid, head, lb, "global" if gsort else "tiles ", prm.slice_k, t.ms, t.delta_avg,
+            t.delta_max, "same image" if t.same_image else ""))
         return t
 
-    # 1. knobs that keep the image: load-balancing threshold and sort path, at the base queues
+    # 1. knobs that keep the image: load-balancing threshold, sort path and (per-tile sort only)
+    # depth-slice size, at the base queues
     inv = []
     for lb, gsort in itertools.product(space.get("lb_threshold", (base.lb_threshold,)), (False, True)):
-        inv.append(run(base.tail, base.mid, base.head, lb, gsort, b_img))
+        for k in ((base.slice_k,) if gsort else space.get("slice_k", (base.slice_k,))):
+            inv.append(run(base.tail, base.mid, base.head, lb, gsort, b_img, k))
     bad = [t for t in inv if not t.same_image]
     if bad:
         raise RuntimeError("result-invariant knob changed the image: %s" % bad[0])
@@ -189,7 +196,7 @@ def tune(scenes, cams: Sequence[I.Camera], base: I.RenderParams | None = None,
                                            space.get("head", (base.head,)))
               if q != (base.tail, base.mid, base.head)]
     for tail, mid, head in queues:
-        run(tail, mid, head, best_inv.lb_threshold, best_inv.global_sort, b_img)
+        run(tail, mid, head, best_inv.lb_threshold, best_inv.global_sort, b_img, best_inv.slice_k)
 
     def admissible(t: Trial) -> bool:
         if policy == "same-result":
@@ -206,15 +213,16 @@ def report(trials: Sequence[Trial], chosen: I.RenderParams, base_delta: dict, ti
     lines = ["# %s" % title, "",
              "Policy `%s`. Base sort error: delta avg %.5f, max %.4f." % (policy, base_delta["delta_avg"],
                                                                           base_delta["delta_max"]),
-             "Chosen: tail %d, mid %d, head %d, lb_threshold %d, %s sort." % (
+             "Chosen: tail %d, mid %d, head %d, lb_threshold %d, %s sort, slice_k %d." % (
                  chosen.tail, chosen.mid, chosen.head, chosen.lb_threshold,
-                 "global radix" if chosen.flags & N.FLAG_GLOBAL_SORT else "per-tile"), "",
-             "| tail | mid | head | LB | sort | fwd ms | delta avg | delta max | same image |",
-             "|---:|---:|---:|---:|---|---:|---:|---:|---|"]
+                 "global radix" if chosen.flags & N.FLAG_GLOBAL_SORT else "per-tile", chosen.slice_k), "",
+             "| tail | mid | head | LB | sort | fwd ms | delta avg | delta max | same image | slice_k |",
+             "|---:|---:|---:|---:|---|---:|---:|---:|---|---:|"]
     for t in sorted(trials, key=lambda t: t.ms):
-        lines.append("| %d | %d | %d | %d | %s | %.3f | %.5f | %.4f | %s |" % (
+        lines.append("| %d | %d | %d | %d | %s | %.3f | %.5f | %.4f | %s | %s |" % (
             t.tail, t.mid, t.head, t.lb_threshold, "global" if t.global_sort else "tiles", t.ms,
-            t.delta_avg, t.delta_max, "yes" if t.same_image else "no"))
+            t.delta_avg, t.delta_max, "yes" if t.same_image else "no",
+            "-" if t.global_sort else ("base" if t.slice_k < 0 else str(t.slice_k))))
     return "\n".join(lines) + "\n"
 
 
@@ -261,7 +269,7 @@ def main(argv=None):
     if a.json:
         with open(a.json, "w") as f:
             json.dump(dict(tail=chosen.tail, mid=chosen.mid, head=chosen.head, lb_threshold=chosen.lb_threshold,
-                           flags=chosen.flags), f)
+                           flags=chosen.flags, slice_k=chosen.slice_k), f)
     if a.save_table:
         best = min(trials, key=lambda t: t.ms if t.params(prm) == chosen else float("inf"))
         save_table(a.workload, chosen, "policy %s, %.3f ms forward (%s)" % (a.policy, best.ms,

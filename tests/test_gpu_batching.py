@@ -267,11 +267,12 @@ def test_differentiation_720p_sampled_tiles_match_oracle_adjoint(oracle):
 def test_autotuner_keeps_the_image_under_same_result_policy():
     from paper_2402_00525_gb300 import autotune as A
     sc, cams, prm = I.plain_forward_workload()
-    space = dict(tail=(64, 96), mid=(8, 12), head=(16,), lb_threshold=(16, 32))
+    space = dict(tail=(64, 96), mid=(8, 12), head=(16,), lb_threshold=(16, 32), slice_k=(0, 64))
     chosen, trials, bd = A.tune(sc, cams, prm, policy="same-result", space=space, reps=2, warmup=1)
     assert (chosen.tail, chosen.mid, chosen.head) == (prm.tail, prm.mid, prm.head)
     inv = [t for t in trials if (t.tail, t.mid, t.head) == (prm.tail, prm.mid, prm.head)]
-    assert len(inv) == 4 and all(t.same_image for t in inv)
+    # two thresholds x (per-tile sort at two slice sizes, global sort): all the base image
+    assert len(inv) == 6 and all(t.same_image for t in inv)
     # larger queues never sort worse on average on this scene (Sec. 3.3: a wider window)
     big = [t for t in trials if t.tail == 96 and t.mid == 12]
     assert big and big[0].delta_avg <= 1.1 * bd["delta_avg"] + 1e-6
