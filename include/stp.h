@@ -232,7 +232,9 @@ stp_status stp_workspace_layout_get(int64_t n, const stp_camera* cams /* host */
                                     const stp_params* prm /* host */, stp_workspace_layout* out /* host */);
 
 /* Forward pass (Sec. 3): Preprocess -> Duplicate -> per-tile depth sort (appendix B.3;
- * STP_FLAG_GLOBAL_SORT selects one global radix sort instead) -> hierarchical Render, for
+ * STP_FLAG_GLOBAL_SORT selects one global radix sort instead; with slice_k > 0 it orders only
+ * each list's prefix, and a second sort and Render pass over the queued warps follows, whose
+ * kernels return at once when nothing was queued) -> hierarchical Render, for
  * `nviews` views of one scene (1 <= nviews <= STP_MAX_VIEWS) in one launch per stage. Writes
  * rgb [pixels,3], depth [pixels] (volumetric depth with phi = t_opt, Sec. 4.1 "Depth
  * Evaluation") and, if not NULL, tfinal [pixels]; pixels are packed view after view, row

@@ -134,3 +134,18 @@ def test_slices_under_graph_replay():
     assert r.status().error_bits == 0 and r.status().redo_warps > 0
     for a, b in zip(eager, out):
         assert torch.equal(a, b)
+
+
+def test_slices_keep_the_blend_traces():
+    """The per-pixel traces of the first blended ids: a warp rendered again over its whole list
+    rewrites its trace from the start, so nothing of the first pass's partial trace remains."""
+    sc, cams = _scene()
+    g = R.scene_to_device(sc)
+    out = {}
+    for k in (0, 1):
+        r = R.Renderer(sc.n, cams, I.RenderParams(slice_k=k), trace=True)
+        r.forward(g)
+        torch.cuda.synchronize()
+        assert r.status().error_bits == 0
+        out[k] = r.debug_trace().cpu().numpy()
+    assert (out[0] >= 0).any() and np.array_equal(out[1], out[0])
