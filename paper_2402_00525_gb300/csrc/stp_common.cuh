@@ -164,7 +164,6 @@ __device__ __forceinline__ float2 box_max_offset(const Rec& r, float x0, float x
     const float bx0 = off_x(r, x0), bx1 = off_x(r, x1), by0 = off_y(r, y0), by1 = off_y(r, y1);
     const bool inx = (bx0 <= 0.f) && (bx1 >= 0.f);
     const bool iny = (by0 <= 0.f) && (by1 >= 0.f);
-    if (inx && iny) return make_float2(0.f, 0.f);
     const float px = bx0 > 0.f ? bx0 : (bx1 < 0.f ? bx1 : (-bx0 <= bx1 ? bx0 : bx1));
     const float py = by0 > 0.f ? by0 : (by1 < 0.f ? by1 : (-by0 <= by1 ? by0 : by1));
     const float ex = __fsub_rn(px == bx0 ? bx1 : bx0, px);   // edge vector along x
@@ -175,18 +174,17 @@ __device__ __forceinline__ float2 box_max_offset(const Rec& r, float x0, float x
     const float se = __fmul_rn(r.r1.z, pe), sp = __fmul_rn(r.r1.w, pp);
     const float Apx = __fmaf_rn(se, r.r1.x, -__fmul_rn(sp, r.r1.y));
     const float Apy = __fmaf_rn(se, r.r1.y, __fmul_rn(sp, r.r1.x));
-    float tx = 0.f, ty = 0.f;
-    if (!inx) {     // search along the y-edge x = px: minimise q(p + t (0, ey))
-        const float Ayy = __fmaf_rn(r.r1.z, __fmul_rn(r.r1.y, r.r1.y), __fmul_rn(r.r1.w, __fmul_rn(r.r1.x, r.r1.x)));
-        const float den = __fmul_rn(ey, Ayy);
-        ty = den != 0.f ? fminf(1.f, fmaxf(0.f, __fdividef(-Apy, den))) : 0.f;
-    }
-    if (!iny) {     // search along the x-edge y = py
-        const float Axx = __fmaf_rn(r.r1.z, __fmul_rn(r.r1.x, r.r1.x), __fmul_rn(r.r1.w, __fmul_rn(r.r1.y, r.r1.y)));
-        const float den = __fmul_rn(ex, Axx);
-        tx = den != 0.f ? fminf(1.f, fmaxf(0.f, __fdividef(-Apx, den))) : 0.f;
-    }
-    return make_float2(__fmaf_rn(tx, ex, px), __fmaf_rn(ty, ey, py));
+    // both edge searches, selected (no divergent region; the same values as taking them only
+    // off the mean's row / column, and the mean itself when it lies in the box)
+    const float Ayy = __fmaf_rn(r.r1.z, __fmul_rn(r.r1.y, r.r1.y), __fmul_rn(r.r1.w, __fmul_rn(r.r1.x, r.r1.x)));
+    const float deny = __fmul_rn(ey, Ayy);
+    const float tyc = deny != 0.f ? fminf(1.f, fmaxf(0.f, __fdividef(-Apy, deny))) : 0.f;
+    const float Axx = __fmaf_rn(r.r1.z, __fmul_rn(r.r1.x, r.r1.x), __fmul_rn(r.r1.w, __fmul_rn(r.r1.y, r.r1.y)));
+    const float denx = __fmul_rn(ex, Axx);
+    const float txc = denx != 0.f ? fminf(1.f, fmaxf(0.f, __fdividef(-Apx, denx))) : 0.f;
+    const float tx = iny ? 0.f : txc, ty = inx ? 0.f : tyc;
+    const float2 o = make_float2(__fmaf_rn(tx, ex, px), __fmaf_rn(ty, ey, py));
+    return (inx && iny) ? make_float2(0.f, 0.f) : o;
 }
 
 // t_opt on the ray through camera-normalised coordinates (u, w) = ((x-cx)/fx, (y-cy)/fy),
