@@ -231,11 +231,13 @@ __device__ __forceinline__ bool box_keep_depth(const Rec& r, const Box& b, const
                                                float eps_o, bool centre_ray, float* t)
 {
     const float2 d = box_max_offset(r, b.x0, b.x1, b.y0, b.y1);
-    if (!(splat_at(r, d.x, d.y) >= eps_o)) return false;
+    const bool keep = splat_at(r, d.x, d.y) >= eps_o;
+    // the depth is taken for a culled box too (no divergent region; callers read *t only for a
+    // kept box, and a degenerate value there is never used)
     const float x = centre_ray ? __fmul_rn(0.5f, __fadd_rn(b.x0, b.x1)) : __fadd_rn(r.r0.x, __fadd_rn(r.r0.z, d.x));
     const float y = centre_ray ? __fmul_rn(0.5f, __fadd_rn(b.y0, b.y1)) : __fadd_rn(r.r0.y, __fadd_rn(r.r0.w, d.y));
     *t = depth_uv(r, to_u(V, x), to_w(V, y));
-    return true;
+    return keep;
 }
 
 // Raise a kernel's dynamic shared-memory limit once per device (host side). Later launches,
