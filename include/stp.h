@@ -86,7 +86,7 @@ typedef struct {
     const float* sh;             /* [N, (sh_degree+1)^2, 3] */
     int64_t n;                   /* number of Gaussians, 0 <= n < 2^31                        */
     int32_t sh_degree;           /* 0..3 */
-    int32_t reserved;
+    int32_t reserved;            /* padding to 8 bytes; ignored                              */
 } stp_gaussians;
 
 typedef struct {                 /* gradient outputs in the input layout, ACCUMULATED (+=)   */
@@ -218,7 +218,7 @@ typedef struct {                 /* byte offsets of workspace regions (for inspe
     int64_t capacity;            /* sort-entry capacity                                      */
     int64_t total_tiles, total_pixels;
     int32_t key_bits;            /* bits of the radix-sort key: 32 + bits(total tiles)       */
-    int32_t reserved;
+    int32_t reserved;            /* padding to 8 bytes; written 0                            */
 } stp_workspace_layout;
 
 /* Size of the workspace one stp_render call needs for `nviews` cameras of N Gaussians
