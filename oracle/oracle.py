@@ -53,7 +53,9 @@ def lib():
     global _lib
     if _lib is None:
         from oracle import build as _b  # noqa
-        path = _b.build()
+        # STP_ORACLE_LIB: load another build of the oracle (the tests that plant a mistake in
+        # a copy of its source run the pins against that build)
+        path = os.environ.get("STP_ORACLE_LIB") or _b.build()
         L = C.CDLL(path)
         dp = C.POINTER(C.c_double)
         vp = C.c_void_p

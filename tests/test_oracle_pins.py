@@ -176,7 +176,9 @@ def test_sh_basis_orthonormal_and_matches_textbook(oracle):
             y = oracle.sh_basis(d)
             Gm += np.outer(y, y) * w * (2 * math.pi / 48)
     assert np.allclose(Gm, np.eye(16), atol=1e-12)
-    # magnitudes against scipy's complex harmonics (real combination), index (l, m)
+    # against scipy's complex harmonics, which carry the Condon-Shortley phase: the real basis
+    # is sqrt(2) Re Y_l^m for m > 0, Y_l^0, and sqrt(2) Im Y_l^|m| for m < 0, signs included;
+    # index (l, m)
     rng = np.random.default_rng(14)
     lm = [(l, m) for l in range(4) for m in range(-l, l + 1)]
     for _ in range(20):
@@ -187,7 +189,7 @@ def test_sh_basis_orthonormal_and_matches_textbook(oracle):
         for k, (l, m) in enumerate(lm):
             Yc = sp.sph_harm_y(l, abs(m), theta, phi)
             ref = Yc.real if m == 0 else math.sqrt(2) * (Yc.real if m > 0 else Yc.imag)
-            assert abs(abs(y[k]) - abs(ref)) < 1e-12
+            assert abs(y[k] - ref) < 1e-12, (l, m)
 
 
 def test_sh_degree0_colour_is_view_independent(oracle):
