@@ -344,6 +344,29 @@ def test_resort_window_k(oracle, k):
     assert ok == [True, False]
 
 
+def test_equal_depths_keep_their_list_order(oracle):
+    """Reading of the queue merges (Sec. 3.4) and the per-pixel insertion (Sec. 3.3): entries of
+    equal depth leave every queue in list order (existing entries first, a new one after its
+    equals), so within the sorting window the blend order is the STABLE sort of the list; the
+    full per-ray sort (Sec. 3.2) breaks ties by list position too. Lists with many exact ties,
+    each entry displaced by at most 21 positions."""
+    rng = np.random.default_rng(31)
+    # a sorted list of runs of 6 equal depths: the order must stay the list order
+    t = np.arange(200) // 6 * 1.0
+    keep = (rng.random(200) < 0.7).astype(np.int32)
+    assert np.array_equal(oracle.schedule_synthetic(t, keep), np.nonzero(keep)[0])
+    for trial in range(120):
+        n = int(rng.integers(1, 300))
+        keep = (rng.random(n) < rng.uniform(0.3, 1.0)).astype(np.int32)
+        s = np.sort(rng.integers(0, max(1, n // 6), n)).astype(float)
+        t = s[np.argsort(np.arange(n) + rng.uniform(0, 20.999, n), kind="stable")]
+        surv = np.nonzero(keep)[0]
+        assert np.array_equal(oracle.schedule_synthetic(t, keep), surv[np.argsort(t[surv], kind="stable")])
+        stable = np.argsort(t, kind="stable")
+        assert np.array_equal(oracle.schedule_synthetic(t, None, mode=I.MODE_FULL), stable)
+        assert np.array_equal(oracle.schedule_synthetic(t, None, mode=I.MODE_WINDOW, head=24), stable)
+
+
 def test_layered_scene_all_orderings_agree(oracle):
     sc = I.layered_scene(6, 10, 7)
     cam = I.look_at((0.2, 0.1, -3), (0, 0, 0), (0, 1, 0), 160, 144, 60.0)
@@ -405,11 +428,14 @@ def _scene64(sc):
                    sc.sh.astype(np.float64), sc.sh_degree)
 
 
-def test_adjoint_matches_central_differences(oracle):
+@pytest.mark.parametrize("bg", [(0.0, 0.0, 0.0), (0.2, 0.5, 0.9)], ids=["black", "coloured"])
+def test_adjoint_matches_central_differences(oracle, bg):
     """Front-to-back adjoint with C - C_i and T_N / T_i (Sec. 3.5) chained through the
     preprocess, against FP64 central differences of L = <w, rgb> + <wz, depth>; parameters
-    whose +-h perturbation changes any blend decision are skipped."""
+    whose +-h perturbation changes any blend decision are skipped. A coloured background
+    brings in the T_N bg term of the colour gradient."""
     sc, _, cam, prm = I.fd_subcase()
+    prm = dataclasses.replace(prm, bg=bg)
     sc = _scene64(sc)
     rng = np.random.default_rng(18)
     H, W = cam.height, cam.width
