@@ -14,6 +14,12 @@ LIB = os.path.join(OUT_DIR, "libstp_oracle.so")
 SRC = os.path.join(HERE, "stp_oracle.c")
 
 
+def gcc_command(src: str, out: str) -> list:
+    """The compile line of the oracle library (FP64, no contraction, no fast math)."""
+    return ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+            "-fno-fast-math", "-Wall", "-o", out, src, "-lm"]
+
+
 def build(force: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     if (not force and os.path.exists(LIB)
@@ -21,9 +27,7 @@ def build(force: bool = False) -> str:
                                              os.path.getmtime(os.path.join(HERE, "stp_oracle.h")))):
         return LIB
     tmp = LIB + ".tmp.%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-           "-fno-fast-math", "-Wall", "-o", tmp, SRC, "-lm"]
-    subprocess.run(cmd, check=True)
+    subprocess.run(gcc_command(SRC, tmp), check=True)
     os.replace(tmp, LIB)
     return LIB
 
