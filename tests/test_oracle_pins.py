@@ -235,6 +235,70 @@ def test_projection_jacobian_is_finite_difference(oracle):
                            rtol=1e-6, atol=1e-8)
 
 
+def test_splat_shape_stops_changing_beyond_the_jacobian_clamp(oracle):
+    """The EWA Jacobian of the preprocess kept from 3DGS takes the view-space x/z and y/z
+    clamped to 1.3 times the half field of view (reading: kept). So beyond that limit the 2D
+    covariance no longer changes as the mean moves outward at a fixed depth; inside it does."""
+    cam = I.Camera(R=np.eye(3), t=np.zeros(3), fx=64.0, fy=64.0, cx=32.0, cy=24.0, width=64, height=48)
+    prm = I.RenderParams()
+    lim = (1.3 * 0.5 * 64 / 64, 1.3 * 0.5 * 48 / 64)
+    S = oracle.sigma(np.array([0.9, 0.2, -0.3, 0.25]), np.log([0.05, 0.2, 0.1]))
+    z = 2.0
+    for axis in (0, 1):
+        def cov(u):
+            mu = np.zeros(3)
+            mu[axis], mu[2] = u * z, z
+            return oracle.project(cam, prm, mu, S)[1]
+        outside = [cov(f * lim[axis]) for f in (1.2, 2.0, 5.0)]
+        for c in outside[1:]:
+            assert np.allclose(c, outside[0], rtol=1e-12, atol=0)
+        assert not np.allclose(cov(0.2 * lim[axis]), cov(0.8 * lim[axis]), rtol=1e-6, atol=0)
+        assert not np.allclose(cov(0.8 * lim[axis]), outside[0], rtol=1e-6, atol=0)
+
+
+def test_near_plane_culls_gaussians_in_front_of_znear(oracle):
+    """The preprocess kept from 3DGS culls Gaussians whose view-space depth is not above
+    znear = 0.2 (reading: kept as a parameter)."""
+    zs = [0.04, 0.1, 0.15, 0.199, 0.201, 0.3, 1.0, 5.0]
+    n = len(zs)
+    sh = np.zeros((n, 1, 3), np.float32)
+    sc = I.Scene(np.array([[0.0, 0.0, z] for z in zs], np.float32), np.full((n, 3), math.log(0.01), np.float32),
+                 np.tile(np.array([1, 0, 0, 0], np.float32), (n, 1)), np.full(n, 2.0, np.float32), sh, 0)
+    cam = I.Camera(R=np.eye(3), t=np.zeros(3), fx=16.0, fy=16.0, cx=8.0, cy=8.0, width=16, height=16)
+    with oracle.OracleRun(sc, cam, I.RenderParams()) as r:
+        vis = r.preprocess()["visible"]
+    assert list(vis) == [int(z > 0.2) for z in zs]
+
+
+def test_sh_colour_uses_the_direction_from_the_camera_to_the_mean(oracle):
+    """App. B.4: each Gaussian's colour is 0.5 + sum_lm Y_lm(d) c_lm, clamped at 0, with d the
+    unit vector from the camera centre to the mean. Y here from scipy's complex harmonics
+    (Condon-Shortley phase, real combinations), d from the float32 camera the renderer gets."""
+    sp = pytest.importorskip("scipy.special")
+    sc = I.uniform_scene(60, 41, extent=0.8, sh_degree=3)
+    sc.sh[:, 1:, :] *= 5.0                        # strong view dependence; some colours clamp
+    cam = I.look_at((1.0, -0.5, -3.0), (0, 0, 0), (0, 1, 0), 64, 64, 60.0)
+    with oracle.OracleRun(sc, cam, I.RenderParams()) as r:
+        pp = r.preprocess()
+    R = cam.R.astype(np.float32).astype(np.float64)
+    o = -R.T @ cam.t.astype(np.float32).astype(np.float64)
+    lm = [(l, m) for l in range(4) for m in range(-l, l + 1)]
+    checked = clamped = 0
+    for i in np.nonzero(pp["visible"])[0]:
+        d = sc.means[i].astype(np.float64) - o
+        d /= np.linalg.norm(d)
+        theta, phi = math.acos(d[2]), math.atan2(d[1], d[0])
+        Y = np.empty(16)
+        for k, (l, m) in enumerate(lm):
+            Yc = sp.sph_harm_y(l, abs(m), theta, phi)
+            Y[k] = Yc.real if m == 0 else math.sqrt(2) * (Yc.real if m > 0 else Yc.imag)
+        col = 0.5 + Y @ sc.sh[i].astype(np.float64)
+        assert np.allclose(pp["color"][i], np.maximum(col, 0.0), rtol=0, atol=1e-12), i
+        checked += 1
+        clamped += int((col < 0).any())
+    assert checked >= 40 and clamped >= 1
+
+
 # --------------------------------------------------------------------- culling exactness
 def _alpha_all_pixels(pp, cam):
     ys, xs = np.mgrid[0:cam.height, 0:cam.width]
