@@ -125,6 +125,68 @@ MUTANTS = [
     ("adjoint_ignores_the_colour_clamp", "App. B.4, Sec. 3.5",
      "double draw = G->raw[ch] > 0 ? gcol[3 * i + ch] : 0.0;", "double draw = gcol[3 * i + ch];",
      [PINS + "test_adjoint_matches_central_differences"]),
+    ("view_direction_reversed", "App. B.4 (SH colour)",
+     "for (int k = 0; k < 3; k++) g->u[k] = g->mu[k] - c->o[k];",
+     "for (int k = 0; k < 3; k++) g->u[k] = c->o[k] - g->mu[k];",
+     [PINS + "test_sh_colour_uses_the_direction_from_the_camera_to_the_mean"]),
+    ("colour_not_clamped_at_zero", "App. B.4 (SH colour)",
+     "g->color[ch] = s > 0 ? s : 0.0;", "g->color[ch] = s;",
+     [PINS + "test_sh_colour_uses_the_direction_from_the_camera_to_the_mean"]),
+    ("sh_without_the_half_offset", "App. B.4 (SH colour)",
+     "        double s = 0.5;\n", "        double s = 0.0;\n",
+     [PINS + "test_sh_degree0_colour_is_view_independent"]),
+    ("sigmoid_sign", "Sec. 2.1 (opacity)",
+     "g->opacity = 1.0 / (1.0 + exp(-sc->logits[i]));", "g->opacity = 1.0 / (1.0 + exp(sc->logits[i]));",
+     [COMP + "test_single_isotropic_gaussian_every_pixel"]),
+    ("rotation_from_the_raw_quaternion", "Sec. 2.1 (Sigma = R S S^T R^T)",
+     "    normalise_quat(quat, q, &l);\n    quat_to_rot(q, R);\n    for (int i = 0; i < 3; i++)\n"
+     "        for (int j = 0; j < 3; j++) {\n            double s = 0;\n"
+     "            for (int k = 0; k < 3; k++) s += R[3 * i + k] * exp(2",
+     "    normalise_quat(quat, q, &l);\n    quat_to_rot(quat, R);\n    for (int i = 0; i < 3; i++)\n"
+     "        for (int j = 0; j < 3; j++) {\n            double s = 0;\n"
+     "            for (int k = 0; k < 3; k++) s += R[3 * i + k] * exp(2",
+     [PINS + "test_sigma_inverse_and_clamp"]),
+    ("jacobian_not_clamped_outside_the_view", "Sec. 2.1 (EWA splat, clamp kept)",
+     "double cx = clampd(ux, -limx, limx), cy = clampd(uy, -limy, limy);", "double cx = ux, cy = uy;",
+     [PINS + "test_splat_shape_stops_changing_beyond_the_jacobian_clamp"]),
+    ("near_plane_at_zero", "preprocess (near plane kept)",
+     "g->visible = (g->p[2] > P->znear) && (g->opacity >= P->eps_o);",
+     "g->visible = (g->p[2] > 0) && (g->opacity >= P->eps_o);",
+     [PINS + "test_near_plane_culls_gaussians_in_front_of_znear"]),
+    ("radius_from_the_smaller_eigenvalue", "App. B.2",
+     "double lam = mid + sqrt(fmax(0.0, mid * mid - g->det));", "double lam = mid - sqrt(fmax(0.0, mid * mid - g->det));",
+     [PINS + "test_tile_culling_never_drops_a_contributor"]),
+    ("ray_direction_not_normalised", "Eq. dopt (unit ray)",
+     "    d[0] /= l; d[1] /= l; d[2] /= l;", "    (void)l;",
+     [COMP + "test_single_isotropic_gaussian_every_pixel"]),
+    ("pixel_ray_through_the_corner", "Sec. 3.4 (pixel centres)",
+     "    ps->x = X + 0.5;", "    ps->x = X;",
+     [COMP + "test_single_isotropic_gaussian_every_pixel"]),
+    ("tile_box_through_pixel_corners", "Sec. 3.4 (tile-based culling)",
+     "    box[0] = ox + 0.5; box[1] = xe + 0.5;", "    box[0] = ox; box[1] = xe;",
+     [PINS + "test_tile_culling_never_drops_a_contributor"]),
+    ("full_sort_by_the_tile_key", "Sec. 3.2 (full per-ray sort)",
+     "                    buf[k].t = pixel_depth(c, L->e[j].id, ps);", "                    buf[k].t = L->e[j].t;",
+     [COMP + "test_single_isotropic_gaussian_every_pixel",
+      PINS + "test_sort_error_full_is_zero_and_hier_beats_small_windows"]),
+    ("full_sort_skipped", "Sec. 3.2 (full per-ray sort)",
+     "qsort(buf, (size_t)k, sizeof(fent), cmp_fent);", "(void)cmp_fent;",
+     [PINS + "test_sort_error_full_is_zero_and_hier_beats_small_windows"]),
+    ("k_buffer_blends_its_farthest", "Sec. 3.3 (k-buffer)",
+     "        hent f = ps->head[0];\n        memmove(&ps->head[0], &ps->head[1], (size_t)(ps->nh - 1) * sizeof(hent));\n"
+     "        ps->nh--;\n        blend(c, ps, sk, f.t, f.id, f.a, cnt);\n    }\n}",
+     "        hent f = ps->head[ps->nh - 1];\n        ps->nh--;\n        blend(c, ps, sk, f.t, f.id, f.a, cnt);\n    }\n}",
+     [PINS + "test_resort_window_k"]),
+    ("pixel_alpha_threshold_doubled", "Sec. 3.4 (alpha >= eps_O)",
+     "            if (a < c->P.eps_o) continue;\n            hent h", "            if (a <= 2 * c->P.eps_o) continue;\n            hent h",
+     [PINS + "test_hier_blends_the_same_set_as_full_sort"]),
+    ("adjoint_mean2_wrong_conic_entry", "Sec. 3.5",
+     "gm2[2 * id + 0] += dG * G2 * (G->conic[0] * dx + G->conic[1] * dy);",
+     "gm2[2 * id + 0] += dG * G2 * (G->conic[0] * dx + G->conic[2] * dy);",
+     [PINS + "test_adjoint_matches_central_differences"]),
+    ("adjoint_log_scale_without_chain_factor", "Sec. 3.5",
+     "dls[k] += mb * G->Rq[3 * r + k] * G->s[k];", "dls[k] += mb * G->Rq[3 * r + k];",
+     [PINS + "test_adjoint_matches_central_differences"]),
     ("non_finite_sh_accepted", "invalid inputs (reading)",
      "        if (!isfinite(sc->sh[i * 3 * K + j])) return 0;", "        (void)0;",
      [COMP + "test_invalid_gaussians_are_dropped_and_counted"]),
