@@ -103,13 +103,15 @@ MUTANTS = [
      [PINS + "test_equal_depths_keep_their_list_order"]),
     ("adjoint_without_background_term", "Sec. 3.5",
      "            da -= gbg * Tf / (1.0 - a);\n", "",
-     [PINS + "test_adjoint_matches_central_differences"]),
+     [PINS + "test_adjoint_suffix_terms_equal_a_back_to_front_pass",
+      PINS + "test_adjoint_matches_central_differences"]),
     ("adjoint_conic_off_diagonal_halved", "Sec. 3.5",
      "gcon[3 * id + 1] += dG * G2 * (-dx * dy);", "gcon[3 * id + 1] += dG * G2 * (-0.5 * dx * dy);",
      [PINS + "test_adjoint_matches_central_differences"]),
     ("adjoint_depth_without_suffix", "Sec. 3.5, Sec. 4.1",
      "da += gz * (t * T - (Zf - Za) / (1.0 - a));", "da += gz * t * T;",
-     [PINS + "test_adjoint_matches_central_differences"]),
+     [PINS + "test_adjoint_suffix_terms_equal_a_back_to_front_pass",
+      PINS + "test_adjoint_matches_central_differences"]),
     ("adjoint_t_opt_wrong_vector", "Eq. dopt, Sec. 3.5",
      "gmu[3 * id + r] += dt * sd[r] / den;", "gmu[3 * id + r] += dt * sm[r] / den;",
      [PINS + "test_adjoint_matches_central_differences"]),

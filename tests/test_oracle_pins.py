@@ -540,6 +540,61 @@ def test_adjoint_matches_central_differences(oracle, bg):
     assert checked >= 60
 
 
+def test_adjoint_suffix_terms_equal_a_back_to_front_pass(oracle):
+    """Sec. 3.5: the adjoint walks the blend order front to back with the suffix colour C - C_i
+    (plus T_N bg) and the suffix transmittance T_N / T_i. A back-to-front pass, written here in
+    numpy from the blend order alone (3DGS's order of accumulation), must give the same
+    colour and opacity gradients, to rounding, with a coloured background and a depth term."""
+    sc, _, cam, prm = I.fd_subcase()
+    sc = _scene64(sc)
+    bg = np.array([0.2, 0.5, 0.9])
+    prm = dataclasses.replace(prm, bg=tuple(bg))
+    rng = np.random.default_rng(19)
+    H, W = cam.height, cam.width
+    w = rng.normal(size=(H, W, 3))
+    wz = rng.normal(size=(H, W)) * 0.1
+    with oracle.OracleRun(sc, cam, prm, record=True) as r:
+        pp = r.preprocess()
+        out = r.render(max_seq=512)
+        adj = r.backward(w, wz)
+    assert out["nblend"].max() < 512
+    Rc = cam.R.astype(np.float32).astype(np.float64)
+    f32 = lambda v: float(np.float32(v))  # noqa: E731
+    fx, fy, cx, cy = f32(cam.fx), f32(cam.fy), f32(cam.cx), f32(cam.cy)
+    s6 = pp["sinv6"]
+    sinv = np.stack([s6[:, [0, 1, 2]], s6[:, [1, 3, 4]], s6[:, [2, 4, 5]]], 1)
+    gcol, gop = np.zeros((sc.n, 3)), np.zeros(sc.n)
+    for y in range(H):
+        for x in range(W):
+            ids = out["seq"][y, x, :out["nblend"][y, x]]
+            if len(ids) == 0:
+                continue
+            px, py = x + 0.5, y + 0.5
+            d = Rc.T @ np.array([(px - cx) / fx, (py - cy) / fy, 1.0])
+            d /= np.linalg.norm(d)
+            dx, dy = px - pp["mean2"][ids, 0], py - pp["mean2"][ids, 1]
+            cn = pp["conic"][ids]
+            G2 = np.exp(-0.5 * (cn[:, 0] * dx * dx + 2 * cn[:, 1] * dx * dy + cn[:, 2] * dy * dy))
+            raw = pp["opacity"][ids] * G2
+            a = np.minimum(0.99, raw)
+            t = (pp["v"][ids] @ d) / np.einsum("i,kij,j->k", d, sinv[ids], d)
+            T = np.concatenate([[1.0], np.cumprod(1.0 - a)])
+            assert T[-1] == pytest.approx(out["tfinal"][y, x], rel=1e-12)
+            col = pp["color"][ids]
+            acc_c, acc_z = bg * T[-1], 0.0            # what lies behind: the background first
+            for k in range(len(ids) - 1, -1, -1):
+                i = ids[k]
+                gcol[i] += w[y, x] * a[k] * T[k]
+                da = w[y, x] @ (col[k] * T[k] - acc_c / (1.0 - a[k])) + wz[y, x] * (t[k] * T[k] - acc_z / (1.0 - a[k]))
+                if raw[k] < 0.99:
+                    gop[i] += da * G2[k]
+                acc_c = acc_c + col[k] * a[k] * T[k]
+                acc_z += t[k] * a[k] * T[k]
+    assert np.abs(gop).max() > 1e-3
+    assert np.allclose(adj["color"], gcol, rtol=1e-9, atol=1e-12 * np.abs(gcol).max())
+    assert np.allclose(adj["opacity"], gop, rtol=1e-9, atol=1e-12 * np.abs(gop).max())
+
+
 # --------------------------------------------------------------------- ablations D and E
 def test_without_tile_culling_lists_grow_but_per_pixel_orders_do_not_change(oracle):
     """Ablation D (Tab. performance_ablation): keeping every tile of a Gaussian's rectangle
