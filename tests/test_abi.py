@@ -1,6 +1,7 @@
 """C-ABI checks that need no GPU: the library loads, exports every function include/stp.h
 declares, sizes workspaces and rejects bad arguments on the host before any launch."""
 import ctypes as C
+import dataclasses
 import os
 import re
 
@@ -84,6 +85,12 @@ def test_workspace_layout_is_consistent(lib):
     ("eps_o", 0.0, N.STP_ERR_ARG), ("mode", 7, N.STP_ERR_ARG), ("mode", -1, N.STP_ERR_ARG), ("max_entries", -1, N.STP_ERR_ARG),
     ("blend_cap", -1, N.STP_ERR_ARG), ("blend_cap", 4097, N.STP_ERR_ARG), ("slice_k", -1, N.STP_ERR_ARG),
     ("full_max_passes", -1, N.STP_ERR_ARG),
+    ("head", 0, N.STP_ERR_NOT_SUPPORTED), ("head", 17, N.STP_ERR_NOT_SUPPORTED), ("tail", 288, N.STP_ERR_ARG),
+    ("mid", 24, N.STP_ERR_ARG), ("eps_o", 1.0, N.STP_ERR_ARG), ("eps_o", float("nan"), N.STP_ERR_ARG),
+    ("t_min", 1.0, N.STP_ERR_ARG), ("t_min", -0.1, N.STP_ERR_ARG), ("alpha_max", 1.0, N.STP_ERR_ARG),
+    ("alpha_max", 1.0 / 512, N.STP_ERR_ARG), ("inv_scale_max", 0.0, N.STP_ERR_ARG),
+    ("dilation", -0.1, N.STP_ERR_ARG), ("frustum_clamp", 0.0, N.STP_ERR_ARG), ("znear", 0.0, N.STP_ERR_ARG),
+    ("max_entries", 0xFFFFFFFF, N.STP_ERR_ARG),
 ])
 def test_bad_parameters_rejected_on_host(lib, field, value, code):
     sc, cams, prm = I.plain_forward_workload()
@@ -94,6 +101,45 @@ def test_bad_parameters_rejected_on_host(lib, field, value, code):
                                       C.byref(L))
     assert rc == code
     assert N.last_error()
+
+
+def _layout_rc(lib, n, cams, p):
+    L = N.Layout()
+    return lib.stp_workspace_layout_get(n, C.cast(N.cameras_array(cams), C.c_void_p), len(cams), C.byref(p),
+                                        C.byref(L))
+
+
+def test_window_k_is_checked_only_for_the_window_order(lib):
+    sc, cams, prm = I.plain_forward_workload()
+    p = N.params_struct(prm)
+    p.window_k = 5
+    assert _layout_rc(lib, sc.n, cams, p) == N.STP_OK
+    p.mode = I.MODE_WINDOW
+    assert _layout_rc(lib, sc.n, cams, p) == N.STP_ERR_NOT_SUPPORTED
+    p.window_k = 8
+    assert _layout_rc(lib, sc.n, cams, p) == N.STP_OK
+
+
+@pytest.mark.parametrize("field,value", [("width", 0), ("height", 0), ("width", 16385), ("height", 16385),
+                                         ("fx", 0.0), ("fy", -1.0), ("cx", float("inf")), ("cy", float("nan"))])
+def test_bad_cameras_rejected_on_host(lib, field, value):
+    sc, cams, prm = I.plain_forward_workload()
+    p = N.params_struct(prm)
+    cams = cams + [dataclasses.replace(cams[0], **{field: value})]
+    assert _layout_rc(lib, sc.n, cams, p) == N.STP_ERR_ARG
+    assert "view 1" in N.last_error()
+    ok = [dataclasses.replace(cams[0], width=16384, height=1)]
+    assert _layout_rc(lib, sc.n, ok, p) == N.STP_OK
+
+
+def test_view_count_range(lib):
+    sc, cams, prm = I.plain_forward_workload()
+    p = N.params_struct(prm)
+    assert _layout_rc(lib, sc.n, cams * 64, p) == N.STP_OK
+    assert _layout_rc(lib, sc.n, cams * 65, p) == N.STP_ERR_ARG
+    L = N.Layout()
+    rc = lib.stp_workspace_layout_get(sc.n, C.cast(N.cameras_array(cams), C.c_void_p), 0, C.byref(p), C.byref(L))
+    assert rc == N.STP_ERR_ARG
 
 
 def test_window_sizes_are_the_compiled_ones(lib):
