@@ -180,6 +180,33 @@ def test_render_rejects_bad_arguments_before_launch(lib):
     assert lib.stp_sort_temp_bytes(1000) > 12000
 
 
+def test_sort_entry_points_reject_bad_arguments_on_host(lib):
+    """Every case fails a host check before any device call (the dummy addresses are never
+    dereferenced)."""
+    fake = [C.c_void_p(256 * (k + 1)) for k in range(4)]
+    tmp = C.c_void_p(4096)
+    ok_temp = lib.stp_sort_temp_bytes(10)
+    cases = [
+        (-1, 40, fake, tmp, ok_temp, "n out of range"),
+        (0xFFFFFFFF, 40, fake, tmp, ok_temp, "n out of range"),
+        (10, 0, fake, tmp, ok_temp, "key_bits"),
+        (10, 65, fake, tmp, ok_temp, "key_bits"),
+        (10, 40, [None] + fake[1:], tmp, ok_temp, "null array"),
+        (10, 40, fake[:3] + [None], tmp, ok_temp, "null array"),
+        (10, 40, fake, None, ok_temp, "temp"),
+        (10, 40, fake, tmp, ok_temp - 1, "temp"),
+    ]
+    for n, bits, arrs, temp, tb, msg in cases:
+        assert lib.stp_sort_pairs(*arrs, n, None, bits, temp, tb, None) == N.STP_ERR_ARG, (n, bits, msg)
+        assert msg in N.last_error()
+    assert lib.stp_sort_temp_bytes(-1) == 0
+    assert lib.stp_sort_temp_bytes(2_000_000) > lib.stp_sort_temp_bytes(1000)
+    for n, bits, arrs, msg in [(-1, 40, fake, "exceeds"), ((1 << 20) + 1, 40, fake, "exceeds"), (10, 0, fake, "key_bits"),
+                               (10, 65, fake, "key_bits"), (10, 40, [None] + fake[1:], "null array")]:
+        assert lib.stp_sort_pairs_noalloc(*arrs, n, None, bits, None) == N.STP_ERR_ARG, (n, bits, msg)
+        assert msg in N.last_error()
+
+
 def test_batched_layout_adds_up_over_scenes(lib):
     cams = I.orbit_cameras(6, 15.0, 2.0, I.C4_SIZES, 50.0)
     p = N.params_struct(I.RenderParams(), N.FLAG_BACKWARD, max_entries=1 << 20)
