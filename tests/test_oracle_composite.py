@@ -278,3 +278,26 @@ def test_invalid_gaussians_are_dropped_and_counted(oracle):
         assert np.all(g1[k][bad] == 0) and np.all(np.isfinite(g1[k])), k
         keep = np.setdiff1d(np.arange(sc.n), bad)
         assert np.array_equal(g1[k][keep], g2[k][keep]), k
+
+
+def test_quaternion_length_threshold(oracle):
+    """Reading for invalid inputs: a quaternion whose squared length is below 1e-20 defines no
+    rotation, so the Gaussian is dropped and counted; just above it the quaternion is
+    normalised and the Gaussian renders like its unit-length twin."""
+    sc = I.uniform_scene(40, 94, scale_range=(0.05, 0.2))
+    cam = I.look_at((0.2, 0.1, -3), (0, 0, 0), (0, 1, 0), 48, 48, 60.0)
+    prm = I.RenderParams()
+    q = sc.quats.astype(np.float64)
+    tiny = I.Scene(sc.means, sc.log_scales, (q * 1e-11).astype(np.float32), sc.opacity_logits, sc.sh, 0)
+    small = I.Scene(sc.means, sc.log_scales, (q * 1e-9).astype(np.float32), sc.opacity_logits, sc.sh, 0)
+    with oracle.OracleRun(tiny, cam, prm) as r:
+        assert r.num_invalid == sc.n
+        assert r.render()["nblend"].sum() == 0
+    with oracle.OracleRun(small, cam, prm) as r1, oracle.OracleRun(sc, cam, prm) as r2:
+        assert r1.num_invalid == 0
+        a, b = r1.render(), r2.render()
+        assert a["nblend"].sum() > 0
+        assert np.array_equal(a["nblend"], b["nblend"]) and np.array_equal(a["hash"], b["hash"])
+        # the scaled quaternion rounds to float32 on its own, so its direction differs from the
+        # unit one by a few 1e-8; the colours by as much
+        assert np.allclose(a["rgb"], b["rgb"], rtol=0, atol=1e-6)

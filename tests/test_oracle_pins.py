@@ -353,6 +353,28 @@ def test_hier_blends_the_same_set_as_full_sort(oracle):
     assert np.array_equal(hs, fs)
 
 
+@pytest.mark.parametrize("flags", [0, I.FLAG_HEAD_EVICT_FIRST, I.FLAG_LEVEL_CENTRE_RAYS],
+                         ids=["default", "evict_first", "level_centre_rays"])
+def test_readings_change_the_order_never_the_set(oracle, flags):
+    """The two alternative readings (evict before insert in the per-pixel queue; 4x4 / 2x2 keys
+    from the level-centre ray) change only the order in which a pixel blends: culling does not
+    depend on keys, so without early termination every pixel still blends exactly the set the
+    full per-ray sort blends. On a clustered scene each reading reorders some pixels."""
+    sc = I.cluster_scene(3000, 33, nclusters=4, centre_range=0.5, scale_range=(0.01, 0.15))
+    cam = I.look_at((0, 0.5, -5), (0, 0, 0), (0, 1, 0), 64, 64, 50.0)
+    prm = I.RenderParams(t_min=1e-30)
+    f = oracle.render(sc, cam, dataclasses.replace(prm, mode=I.MODE_FULL), max_seq=600)
+    h = oracle.render(sc, cam, dataclasses.replace(prm, flags=flags), max_seq=600)
+    assert f["nblend"].max() < 600
+    assert np.array_equal(h["nblend"], f["nblend"])
+    hs = np.sort(np.where(h["seq"] < 0, 1 << 30, h["seq"]), axis=2)
+    fs = np.sort(np.where(f["seq"] < 0, 1 << 30, f["seq"]), axis=2)
+    assert np.array_equal(hs, fs)
+    if flags:
+        base = oracle.render(sc, cam, prm)
+        assert (h["hash"] != base["hash"]).mean() > 0.05
+
+
 # --------------------------------------------------------------------- Sec. 3.4 schedule
 def _late(n, src, D):
     order = list(range(n))
@@ -429,6 +451,26 @@ def test_equal_depths_keep_their_list_order(oracle):
         stable = np.argsort(t, kind="stable")
         assert np.array_equal(oracle.schedule_synthetic(t, None, mode=I.MODE_FULL), stable)
         assert np.array_equal(oracle.schedule_synthetic(t, None, mode=I.MODE_WINDOW, head=24), stable)
+
+
+def test_evict_first_reading_shrinks_every_window_by_one(oracle):
+    """Under the other reading of the full per-pixel queue (Sec. 3.4: blend the front before
+    inserting), a k-buffer handles an entry k - 1 positions late but not k, and the hierarchy's
+    worst-case window is 24 instead of 25."""
+    for k in (1, 2, 4, 8, 16, 24):
+        ok = [bool(np.all(np.diff(t[oracle.schedule_synthetic(t, None, mode=I.MODE_WINDOW, head=k,
+                                                               flags=I.FLAG_HEAD_EVICT_FIRST)]) >= 0))
+              for t in (_late(80, 30, d) for d in (k - 1, k))]
+        assert ok == [True, False], k
+
+    def case(disp):
+        xr = 49 - disp
+        loaded = [r for r in range(50) if r != xr]
+        t = np.array(loaded[:32] + loaded[32:49] + [1000 + k for k in range(15)] + [xr], float)
+        keep = np.array([1] * 49 + [0] * 15 + [1])
+        out = oracle.schedule_synthetic(t, keep, flags=I.FLAG_HEAD_EVICT_FIRST)
+        return bool(np.all(np.diff(t[out]) >= 0))
+    assert all(case(d) for d in range(0, 25)) and not case(25)
 
 
 def test_layered_scene_all_orderings_agree(oracle):
