@@ -189,6 +189,42 @@ MUTANTS = [
     ("adjoint_log_scale_without_chain_factor", "Sec. 3.5",
      "dls[k] += mb * G->Rq[3 * r + k] * G->s[k];", "dls[k] += mb * G->Rq[3 * r + k];",
      [PINS + "test_adjoint_matches_central_differences"]),
+    ("key_cut_ignored", "depth slices (prefix exactness)",
+     "            L->n = m;\n            batch_margins(L, key_cut);", "            (void)m;\n            batch_margins(L, key_cut);",
+     [PINS + "test_key_prefix_keeps_pixels_finished_inside_its_complete_batches"]),
+    ("global_order_through_a_k_buffer", "Sec. 3.2 (3DGS order)",
+     "                    if (P->mode == 2) blend(c, ps, sk, t, L->e[j].id, a, cnt);",
+     "                    if (P->mode == 99) blend(c, ps, sk, t, L->e[j].id, a, cnt);",
+     [PINS + "test_sort_error_full_is_zero_and_hier_beats_small_windows"]),
+    ("k_buffer_never_flushed", "Sec. 3.3 (k-buffer)",
+     "                if (P->mode == 3) head_flush(c, ps, sk, cnt);", "                (void)0;",
+     [COMP + "test_stack_on_one_ray_composites_front_to_back"]),
+    ("sort_error_counts_every_gap", "Sec. 3.3 (sort error)",
+     "if (ps->has_last && ps->last_t > t) ps->delta += ps->last_t - t;", "if (ps->has_last) ps->delta += fabs(ps->last_t - t);",
+     [PINS + "test_sort_error_full_is_zero_and_hier_beats_small_windows"]),
+    ("evict_first_reading_ignored", "Sec. 3.4 (full head queue, other reading)",
+     "if ((c->P.flags & 1) && ps->nh == hsize) {", "if ((c->P.flags & 1) && ps->nh == hsize + 1000) {",
+     [PINS + "test_evict_first_reading_shrinks_every_window_by_one"]),
+    ("level_centre_reading_ignored", "Sec. 3.4 (level rays, other reading)",
+     "    if (c->P.flags & 2) *t = depth_at(c, g, 0.5 * (box[0] + box[1]), 0.5 * (box[2] + box[3]));",
+     "    if (c->P.flags & 0) *t = depth_at(c, g, 0.5 * (box[0] + box[1]), 0.5 * (box[2] + box[3]));",
+     [PINS + "test_readings_change_the_order_never_the_set"]),
+    ("view_depth_ablation_ignored", "Tab. performance_ablation B",
+     "if (P->flags & 8) t = g->p[2];", "if (P->flags & 0) t = g->p[2];",
+     [PINS + "test_tile_depth_adjustment_reduces_sort_error"]),
+    ("tile_cull_ablation_ignored", "Tab. performance_ablation D",
+     "                if (P->flags & 512) {", "                if (P->flags & 0) {",
+     [PINS + "test_without_tile_culling_lists_grow_but_per_pixel_orders_do_not_change"]),
+    ("hierarchical_cull_ablation_ignored", "Tab. performance_ablation E",
+     "    if (c->P.flags & 1024) *margin = INFINITY;", "    if (c->P.flags & 0) *margin = INFINITY;",
+     [PINS + "test_without_hierarchical_culling_every_entry_reaches_the_pixels"]),
+    ("tiny_quaternion_accepted", "invalid inputs (reading)",
+     "if (!(q2 >= 1e-20) || !isfinite(sc->logits[i])) return 0;", "if (!(q2 > 0) || !isfinite(sc->logits[i])) return 0;",
+     [COMP + "test_quaternion_length_threshold"]),
+    ("non_finite_mean_accepted", "invalid inputs (reading)",
+     "if (!isfinite(sc->means[3 * i + k]) || !isfinite(sc->log_scales[3 * i + k])) return 0;",
+     "if (!isfinite(sc->log_scales[3 * i + k])) return 0;",
+     [COMP + "test_invalid_gaussians_are_dropped_and_counted"]),
     ("non_finite_sh_accepted", "invalid inputs (reading)",
      "        if (!isfinite(sc->sh[i * 3 * K + j])) return 0;", "        (void)0;",
      [COMP + "test_invalid_gaussians_are_dropped_and_counted"]),
