@@ -47,7 +47,9 @@ FLAG_NO_HIER_CULL = 1024       # ablation E: no culling at the 4x4 / 2x2 levels 
 
 @dataclasses.dataclass
 class RenderParams:
-    """Knobs of the renderer. Defaults are the paper's (64/8/4 queues, eps_O = 1/255)."""
+    """Knobs of the renderer. Defaults are the paper's (64/8/4 queues, eps_O = 1/255). The
+    library checks every value on the host (include/stp.h states the ranges) and rejects a bad
+    one before any launch."""
     tail: int = 64            # 4x4 tile-queue size, 32n+32 (Sec. 3.4)
     mid: int = 8              # 2x2 tile-queue size, 4m+4 (Sec. 3.4)
     head: int = 4             # per-pixel queue size (Sec. 3.4)
@@ -71,14 +73,6 @@ class RenderParams:
     # HIER with the partitioned sort: lists built in depth slices, about the slice_k nearest
     # entries of each tile first (0 = whole lists in one pass); the images are the same
     slice_k: int = 2048
-
-    def validate(self) -> None:
-        if self.tail < 64 or self.tail % 32 != 0:
-            raise ValueError("tail queue size must be 32n+32 with n >= 1")
-        if self.mid < 8 or self.mid % 4 != 0:
-            raise ValueError("mid queue size must be 4m+4 with m >= 1")
-        if self.head < 1:
-            raise ValueError("head queue size must be >= 1")
 
 
 @dataclasses.dataclass
@@ -126,9 +120,6 @@ class Scene:
         return Scene(self.means[perm].copy(), self.log_scales[perm].copy(),
                      self.quats[perm].copy(), self.opacity_logits[perm].copy(),
                      self.sh[perm].copy(), self.sh_degree)
-
-    def subset(self, idx: np.ndarray) -> "Scene":
-        return self.permuted(np.asarray(idx))
 
 
 # ----------------------------------------------------------------------------- cameras
