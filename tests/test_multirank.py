@@ -31,6 +31,17 @@ def test_views_shard_over_ranks_exactly_once():
     assert bench.job_mpix_per_s(1000, 4, 2.0) == pytest.approx(2.0)
 
 
+def test_view_sharding_edge_cases():
+    from paper_2402_00525_gb300 import distributed as D
+    cams = list(range(5))
+    assert [D.shard_views(cams, r, 3) for r in range(3)] == [[0, 3], [1, 4], [2]]
+    assert [D.shard_views(cams[:2], r, 4) for r in range(4)] == [[0], [1], [], []]
+    assert D.shard_views(cams, 0, 1) == cams
+    for rank, world in ((0, 0), (3, 3), (-1, 2)):
+        with pytest.raises(ValueError):
+            D.shard_views(cams, rank, world)
+
+
 def _rank_main(rank, world, port, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
     import torch.distributed as dist
