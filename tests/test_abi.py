@@ -277,3 +277,49 @@ def test_backward_before_forward_is_refused_on_the_host(lib):
     r2 = R.Renderer(sc.n, cams, prm, device="cpu")
     with pytest.raises(RuntimeError, match="backward=True"):
         r2.backward({}, torch.zeros(1), None, {})
+
+
+def test_binding_matches_the_header_layouts_and_constants(tmp_path):
+    """The ctypes structs of the binding have the C header's size and field offsets (a plain C
+    program built against include/stp.h prints them), and every constant the binding mirrors
+    has the header's value."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("needs gcc")
+    pairs = [(N.Gaussians, "stp_gaussians"), (N.GaussiansGrad, "stp_gaussians_grad"), (N.CameraS, "stp_camera"),
+             (N.Params, "stp_params"), (N.RunStatus, "stp_run_status"), (N.Layout, "stp_workspace_layout")]
+    consts = {"STP_OK": N.STP_OK, "STP_ERR_ARG": N.STP_ERR_ARG, "STP_ERR_CAPACITY": N.STP_ERR_CAPACITY,
+              "STP_ERR_TIMEOUT": N.STP_ERR_TIMEOUT, "STP_ERR_CUDA": N.STP_ERR_CUDA,
+              "STP_ERR_NOT_SUPPORTED": N.STP_ERR_NOT_SUPPORTED, "STP_ERR_INCONSISTENT": N.STP_ERR_INCONSISTENT,
+              "STP_MODE_HIER": I.MODE_HIER, "STP_MODE_FULL": I.MODE_FULL, "STP_MODE_GLOBAL": I.MODE_GLOBAL,
+              "STP_MODE_WINDOW": I.MODE_WINDOW, "STP_FLAG_HEAD_EVICT_FIRST": I.FLAG_HEAD_EVICT_FIRST,
+              "STP_FLAG_LEVEL_CENTRE_RAYS": I.FLAG_LEVEL_CENTRE_RAYS, "STP_FLAG_TILE_CENTRE_KEY": I.FLAG_TILE_CENTRE_KEY,
+              "STP_FLAG_VIEW_DEPTH_KEY": I.FLAG_VIEW_DEPTH_KEY, "STP_FLAG_NO_LOAD_BALANCE": I.FLAG_NO_LOAD_BALANCE,
+              "STP_FLAG_DEBUG_STATS": N.FLAG_DEBUG_STATS, "STP_FLAG_BACKWARD": N.FLAG_BACKWARD,
+              "STP_FLAG_DEBUG_TRACE": N.FLAG_DEBUG_TRACE, "STP_FLAG_GLOBAL_SORT": N.FLAG_GLOBAL_SORT,
+              "STP_FLAG_NO_TILE_CULL": N.FLAG_NO_TILE_CULL, "STP_FLAG_NO_HIER_CULL": N.FLAG_NO_HIER_CULL,
+              "STP_TRACE_LEN": N.TRACE_LEN, "STP_MAX_SCENES": N.MAX_SCENES, "STP_MAX_VIEWS": N.MAX_VIEWS,
+              "STP_SORT_STATIC_MAX_N": N.SORT_STATIC_MAX_N, "STP_NUM_STAGES": N.NUM_STAGES}
+    assert I.FLAG_GLOBAL_SORT == N.FLAG_GLOBAL_SORT and I.FLAG_NO_TILE_CULL == N.FLAG_NO_TILE_CULL
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "stp.h"', "int main(void) {"]
+    expect = {}
+    for cls, cname in pairs:
+        lines.append('printf("%%s %%zu\\n", "%s", sizeof(%s));' % (cname, cname))
+        expect[cname] = C.sizeof(cls)
+        for f, _ in cls._fields_:
+            key = "%s.%s" % (cname, f)
+            lines.append('printf("%%s %%zu\\n", "%s", offsetof(%s, %s));' % (key, cname, f))
+            expect[key] = getattr(cls, f).offset
+    for k, v in consts.items():
+        lines.append('printf("%%s %%lld\\n", "%s", (long long)(%s));' % (k, k))
+        expect[k] = v
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layouts.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layouts"
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    got = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                          text=True).stdout.splitlines())
+    assert {k: int(v) for k, v in got.items()} == expect
